@@ -1,0 +1,182 @@
+/*
+ * qdd.h -- C ABI of the GB300 Wilson-clover quark solver with the restricted
+ * additive Schwarz (RAS) preconditioner.
+ *
+ * Method: Osaki & Ishikawa, "Domain Decomposition method on GPU cluster",
+ * Lattice 2010.  The library solves the quark equation D phi = eta (Eq. 1)
+ * for the O(a)-improved Wilson (Wilson-clover) operator
+ *
+ *     D = A - kappa H,
+ *     (H psi)(x) = sum_mu [ b (1 - gamma_mu) U_mu(x) psi(x+mu)
+ *                         + b (1 + gamma_mu) U_mu(x-mu)^dag psi(x-mu) ],
+ *     A(x) = 1 + i kappa c_sw sum_{mu<nu} sigma_{mu nu} Fhat_{mu nu}(x),
+ *
+ * (kappa and c_SW as in Sec. 5; gamma matrices in the DeGrand-Rossi basis,
+ * b = the boundary sign of a hop that wraps around the lattice), with the
+ * mixed-precision nested BiCGStab of Sec. 3 whose inner solve is right-
+ * preconditioned (Eq. 3) by the RAS iteration of Alg. 1 / Eq. 2.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: dims = (Lx, Ly, Lz, Lt), site index i = x + Lx(y + Ly(z + Lz t)),
+ * mu = 0..3 <-> x, y, z, t.  bc[mu] = +1 periodic, -1 antiperiodic; the sign
+ * multiplies fermion hops that wrap around direction mu.  Gauge links are
+ * always periodic.
+ *
+ * Canonical layouts (all FP64, interleaved complex: re, im):
+ *   spinor  double[V][4 spin][3 colour][2]       (24 doubles per site)
+ *   gauge   double[V][4 mu][3 row][3 col][2]     (72 doubles per site)
+ * Every double* argument may be a DEVICE pointer (cudaMalloc, torch CUDA
+ * tensor) or a HOST pointer (pinned or pageable); the library detects which.
+ * Host buffers are copied to and from the device inside the call, on the
+ * lattice's stream, and a call that writes a host buffer returns only after
+ * the data has arrived.  Calls with device buffers are stream-ordered on the
+ * stream given to qdd_create_lattice and may return before the GPU is done,
+ * except qdd_solve / qdd_solve_batch, which read residual norms on the host
+ * and so return after the solve completes.
+ *
+ * Ownership: the caller owns every buffer it passes; the library never keeps
+ * a caller pointer after a call returns.  The library owns the lattice, its
+ * internal copies of the links (FP64, FP32 and FP16, 12-real compressed for
+ * the reduced precisions), the clover cache keyed by (kappa, c_sw), the
+ * solver work vectors and the reduction scratch.
+ *
+ * Errors: every call returns a qdd_status and never aborts the process.
+ * qdd_last_error() returns a description of the last failure on the calling
+ * thread.  A call that fails leaves the lattice usable.
+ *
+ * Threading: a lattice may be used by one host thread at a time.
+ */
+#ifndef QDD_H
+#define QDD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    QDD_OK = 0,
+    QDD_ERR_ARG = 1,            /* invalid argument (sizes, blocking, null pointer, non-SU(3) link) */
+    QDD_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    QDD_ERR_NOMEM = 3,          /* device allocation failed */
+    QDD_ERR_NOT_CONVERGED = 4,  /* iteration budget exhausted; phi holds the best iterate */
+    QDD_ERR_BREAKDOWN = 5,      /* BiCGStab broke down twice (after one restart) */
+    QDD_ERR_NONFINITE = 6,      /* NaN or Inf in a residual norm */
+    QDD_ERR_TIMEOUT = 7,        /* reserved: a bounded device-side wait gave up */
+    QDD_ERR_STATE = 8           /* call out of order (e.g. no gauge field loaded) */
+} qdd_status;
+
+typedef enum { QDD_F64 = 0, QDD_F32 = 1, QDD_F16 = 2 } qdd_prec;
+
+/* Opaque lattice: geometry, boundary signs, links, clover cache, stream. */
+typedef struct qdd_lattice qdd_lattice;
+
+/* Opaque spinor field in the library's internal GPU layout (for repeated
+ * application without layout conversion, e.g. throughput measurement). */
+typedef struct qdd_field qdd_field;
+
+/* Solver parameters (Sec. 2 and Sec. 5 name block shape, overlap depth
+ * d = 2 s, N_dominv and NRAS). */
+typedef struct {
+    int block[4];       /* bulk block Omega_i (each divides the lattice), default 4,4,4,4 */
+    int overlap;        /* s: extension of Omega'_i on each side, d = 2 s; default 0 */
+    int n_dominv;       /* MR iterations per domain solve, default 4 */
+    int n_ras;          /* NRAS sweeps per preconditioner application, default 3 */
+    int inner_prec;     /* qdd_prec of the inner solve: QDD_F32 (default) or QDD_F16;
+                           QDD_F64 runs the plain FP64 BiCGStab (no nesting, no RAS) */
+    double inner_tol;   /* relative residual of each inner solve, default 1e-3 */
+    int max_inner;      /* inner BiCGStab iterations per outer step, default 2000 */
+    int max_outer;      /* outer defect-correction steps, default 50 */
+    int use_ras;        /* 1: right-precondition the inner solve with K_RAS (default 1) */
+    int outer_mode;     /* 0: FP64 defect correction (the only mode so far) */
+    int autotune;       /* reserved, 0 */
+} qdd_solver_params;
+
+typedef struct {
+    int outer_iters;            /* defect-correction steps */
+    int inner_iters;            /* inner BiCGStab iterations, summed */
+    int dv_count;               /* global D applications (the paper's "Dv count", Table 1) */
+    int ras_sweeps;             /* RAS block-solve sweeps */
+    int status;                 /* qdd_status of the solve */
+    double true_rel_residual;   /* |eta - D phi| / |eta| with the FP64 D */
+    double t_total_ms;          /* wall time of the call */
+    double t_outer_ms;          /* FP64 residuals, conversions and accumulation */
+    double t_inner_ms;          /* inner solves */
+} qdd_solve_info;
+
+/* Library version string. */
+const char *qdd_version(void);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char *qdd_last_error(void);
+
+/* Fills *p with the defaults listed in qdd_solver_params. */
+void qdd_default_params(qdd_solver_params *p);
+
+/* Creates a lattice of dims[4] = (Lx, Ly, Lz, Lt) sites with boundary signs
+ * bc[4] (+1 / -1) on the current CUDA device.  n_rhs must be 1.
+ * cuda_stream is a cudaStream_t (NULL: the legacy default stream); every
+ * kernel of this lattice runs on it.  Allocates the lattice's device memory
+ * (about 1.6 KB per site).  Errors: QDD_ERR_ARG for non-positive or odd-sized
+ * nonsense dims, bc not +-1, n_rhs != 1; QDD_ERR_NOMEM. */
+qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc[4], int n_rhs,
+                              void *cuda_stream);
+
+/* Frees the lattice and everything it owns (fields created from it must be
+ * destroyed first).  NULL is accepted. */
+qdd_status qdd_destroy_lattice(qdd_lattice *lat);
+
+/* Loads the gauge field U (canonical FP64, host or device) and derives the
+ * internal FP64 (18-real), FP32 and FP16 (12-real, third row rebuilt as the
+ * conjugated cross product of the first two) copies; invalidates the clover
+ * cache.  The links enter D through the hopping term of Eq. 1 and the clover
+ * leaves.  Rejects with QDD_ERR_ARG a field with any max|U^dag U - 1| or
+ * |det U - 1| above 1e-10 (the compression needs SU(3)). */
+qdd_status qdd_load_gauge(qdd_lattice *lat, const double *U);
+
+/* out = D in (Eq. 1), computed in precision prec (QDD_F64: FP64 throughout;
+ * QDD_F32: FP32 fields and arithmetic; QDD_F16: FP16 storage with per-site
+ * norms, FP32 arithmetic).  in/out canonical FP64 spinors, host or device,
+ * must not overlap.  Builds the clover term for (kappa, c_sw) on first use. */
+qdd_status qdd_dslash(qdd_lattice *lat, double *out, const double *in, double kappa, double c_sw,
+                      qdd_prec prec);
+
+/* out = K_RAS in (Alg. 1): NRAS sweeps of projection onto every extended
+ * domain Omega'_i, n_dominv MR iterations of the Dirichlet-restricted D on
+ * it, restriction to the bulk block and summation, then phi += v,
+ * r -= D v.  Uses params->block, overlap, n_dominv, n_ras and inner_prec
+ * (QDD_F32 or QDD_F16).  in/out canonical FP64 spinors, host or device.
+ * Errors: QDD_ERR_ARG if a block does not divide the lattice or
+ * block + 2*overlap exceeds it. */
+qdd_status qdd_ras_apply(qdd_lattice *lat, double *out, const double *in, double kappa, double c_sw,
+                         const qdd_solver_params *params);
+
+/* Solves D phi = eta to |eta - D phi| / |eta| <= tol (the stopping rule of
+ * Sec. 5), with the FP64 outer defect correction around the right-
+ * preconditioned inner BiCGStab (Sec. 3, Eq. 3), or with the plain FP64
+ * BiCGStab when params->inner_prec == QDD_F64.  params NULL: defaults.
+ * phi is overwritten (no initial guess).  info may be NULL.  Returns QDD_OK,
+ * QDD_ERR_NOT_CONVERGED (phi = best iterate), QDD_ERR_BREAKDOWN or
+ * QDD_ERR_NONFINITE. */
+qdd_status qdd_solve(qdd_lattice *lat, double *phi, const double *eta, double kappa, double c_sw,
+                     double tol, const qdd_solver_params *params, qdd_solve_info *info);
+
+/* -- internal-layout fields ------------------------------------------------ */
+
+/* Creates a spinor field of precision prec in the internal layout. */
+qdd_status qdd_field_create(qdd_lattice *lat, qdd_prec prec, qdd_field **out);
+qdd_status qdd_field_destroy(qdd_field *f);
+/* Canonical FP64 spinor (host or device) -> field (rounded to its precision). */
+qdd_status qdd_field_import(qdd_field *f, const double *src);
+/* Field -> canonical FP64 spinor (host or device). */
+qdd_status qdd_field_export(const qdd_field *f, double *dst);
+/* out = D in on internal fields of one precision (the dslash kernel alone:
+ * one launch, stream-ordered, nothing else). */
+qdd_status qdd_dslash_field(qdd_lattice *lat, qdd_field *out, const qdd_field *in, double kappa,
+                            double c_sw);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QDD_H */

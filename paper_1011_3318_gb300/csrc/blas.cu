@@ -1,0 +1,306 @@
+// blas.cu -- fused vector kernels of the right-preconditioned BiCGStab
+// (Eq. 3) and of the FP64 defect correction around it (Sec. 3).
+//
+// The solver scalars (rho, alpha, omega, beta, |r|^2) live on the device.
+// Each reduction ends with the last-block pattern of grid_sum, whose final
+// block derives the next scalar (so no kernel recomputes it per thread and
+// no host round trip is needed inside an iteration).  Kernels of a solver
+// iteration return at once when the status is no longer "running", which
+// lets the host enqueue several iterations ahead of the convergence check.
+#include "device.cuh"
+#include "lib.h"
+
+namespace qdd {
+
+constexpr int BLAS_NT = 256;
+
+template <typename T>
+__device__ __forceinline__ void zero12(C<T> (&a)[12])
+{
+#pragma unroll
+    for (int k = 0; k < 12; k++) a[k] = {0, 0};
+}
+
+template <int P, int OP>
+__global__ void __launch_bounds__(BLAS_NT) blas_kernel(const BlasArgs a)
+{
+    typedef typename RealOf<P>::T T;
+    constexpr int NRED = (OP == B_INIT || OP == B_NORM || OP == B_RESTART) ? 1 : 0;
+    if constexpr (OP == B_P || OP == B_S) {
+        if (a.sc->status != S_RUN) return;
+    }
+    const long long V = a.V;
+    double red[NRED > 0 ? NRED : 1];
+#pragma unroll
+    for (int k = 0; k < (NRED > 0 ? NRED : 1); k++) red[k] = 0.0;
+
+    // coefficients read once per thread from the device scalars
+    C<T> c1 = {0, 0}, c2 = {0, 0};
+    if constexpr (OP == B_P) {
+        c1 = {(T)a.sc->beta.x, (T)a.sc->beta.y};
+        c2 = {(T)a.sc->omega.x, (T)a.sc->omega.y};
+    } else if constexpr (OP == B_S) {
+        c1 = {(T)a.sc->alpha.x, (T)a.sc->alpha.y};
+    }
+
+    for (long long x = (long long)blockIdx.x * BLAS_NT + threadIdx.x; x < V; x += (long long)gridDim.x * BLAS_NT) {
+        if constexpr (OP == B_INIT) {
+            C<T> b[12], z[12];
+            load_spinor<P>(a.f[0], V, x, b);
+            zero12(z);
+            store_spinor<P>(a.f[1], V, x, b);
+            store_spinor<P>(a.f[2], V, x, b);
+            store_spinor<P>(a.f[3], V, x, z);
+            store_spinor<P>(a.f[4], V, x, z);
+            store_spinor<P>(a.f[5], V, x, z);
+            T n2 = 0;
+#pragma unroll
+            for (int k = 0; k < 12; k++) n2 += b[k].r * b[k].r + b[k].i * b[k].i;
+            red[0] += (double)n2;
+        } else if constexpr (OP == B_P) {
+            C<T> p[12], r[12], v[12];
+            load_spinor<P>(a.f[0], V, x, p);
+            load_spinor<P>(a.f[1], V, x, r);
+            load_spinor<P>(a.f[2], V, x, v);
+#pragma unroll
+            for (int k = 0; k < 12; k++) p[k] = cadd(r[k], cmul(c1, csub(p[k], cmul(c2, v[k]))));
+            store_spinor<P>(a.f[0], V, x, p);
+        } else if constexpr (OP == B_S) {
+            C<T> r[12], v[12];
+            load_spinor<P>(a.f[1], V, x, r);
+            load_spinor<P>(a.f[2], V, x, v);
+#pragma unroll
+            for (int k = 0; k < 12; k++) r[k] = csub(r[k], cmul(c1, v[k]));
+            store_spinor<P>(a.f[0], V, x, r);
+        } else if constexpr (OP == B_NORM) {
+            C<T> f[12];
+            load_spinor<P>(a.f[0], V, x, f);
+            T n2 = 0;
+#pragma unroll
+            for (int k = 0; k < 12; k++) n2 += f[k].r * f[k].r + f[k].i * f[k].i;
+            red[0] += (double)n2;
+        } else if constexpr (OP == B_COPY) {
+            C<T> f[12];
+            load_spinor<P>(a.f[1], V, x, f);
+            store_spinor<P>(a.f[0], V, x, f);
+        } else if constexpr (OP == B_ZERO) {
+            C<T> z[12];
+            zero12(z);
+            store_spinor<P>(a.f[0], V, x, z);
+        } else if constexpr (OP == B_RESTART) {
+            C<T> r[12], z[12];
+            load_spinor<P>(a.f[1], V, x, r);
+            zero12(z);
+            store_spinor<P>(a.f[0], V, x, r);
+            store_spinor<P>(a.f[2], V, x, z);
+            store_spinor<P>(a.f[3], V, x, z);
+            T n2 = 0;
+#pragma unroll
+            for (int k = 0; k < 12; k++) n2 += r[k].r * r[k].r + r[k].i * r[k].i;
+            red[0] += (double)n2;
+        }
+    }
+
+    if constexpr (NRED > 0) {
+        if (grid_sum<NRED>(red, a.rs)) {
+            Scalars *sc = a.sc;
+            if constexpr (OP == B_INIT) {
+                sc->rho = make_double2(red[0], 0.0);
+                sc->alpha = sc->omega = sc->beta = make_double2(1.0, 0.0);
+                sc->rr = red[0];
+                sc->rhat2 = red[0];
+                sc->tol2 = a.tol2_rel * red[0];
+                sc->iter = 0;
+                sc->status = isfinite(red[0]) ? (red[0] <= sc->tol2 ? S_CONVERGED : S_RUN) : S_NONFINITE;
+            } else if constexpr (OP == B_NORM) {
+                sc->aux[a.aux_slot] = red[0];
+            } else if constexpr (OP == B_RESTART) {
+                sc->rho = make_double2(red[0], 0.0);
+                sc->alpha = sc->omega = sc->beta = make_double2(1.0, 0.0);
+                sc->rhat2 = red[0];
+                sc->status = isfinite(red[0]) ? S_RUN : S_NONFINITE;
+            }
+        }
+    }
+}
+
+// x += alpha phat + omega shat ; r = s - omega t ; then rho' = <rhat, r>,
+// |r|^2 and beta = (rho'/rho)(alpha/omega).  f = {x, phat, shat, r, s, t, rhat}.
+template <int P>
+__global__ void __launch_bounds__(BLAS_NT) bicg_xr_kernel(const BlasArgs a)
+{
+    typedef typename RealOf<P>::T T;
+    if (a.sc->status != S_RUN) return;
+    const long long V = a.V;
+    const C<T> al = {(T)a.sc->alpha.x, (T)a.sc->alpha.y};
+    const C<T> om = {(T)a.sc->omega.x, (T)a.sc->omega.y};
+    double red[3] = {0.0, 0.0, 0.0};
+    for (long long x = (long long)blockIdx.x * BLAS_NT + threadIdx.x; x < V; x += (long long)gridDim.x * BLAS_NT) {
+        C<T> xx[12], ph[12], sh[12];
+        load_spinor<P>(a.f[0], V, x, xx);
+        load_spinor<P>(a.f[1], V, x, ph);
+        load_spinor<P>(a.f[2], V, x, sh);
+#pragma unroll
+        for (int k = 0; k < 12; k++) xx[k] = cadd(xx[k], cadd(cmul(al, ph[k]), cmul(om, sh[k])));
+        store_spinor<P>(a.f[0], V, x, xx);
+        C<T> s[12], t[12], rh[12];
+        load_spinor<P>(a.f[4], V, x, s);
+        load_spinor<P>(a.f[5], V, x, t);
+        load_spinor<P>(a.f[6], V, x, rh);
+        T dr = 0, di = 0, n2 = 0;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            s[k] = csub(s[k], cmul(om, t[k]));
+            C<T> p = cmulc(rh[k], s[k]);
+            dr += p.r;
+            di += p.i;
+            n2 += s[k].r * s[k].r + s[k].i * s[k].i;
+        }
+        store_spinor<P>(a.f[3], V, x, s);
+        red[0] += (double)dr;
+        red[1] += (double)di;
+        red[2] += (double)n2;
+    }
+    if (grid_sum<3>(red, a.rs)) {
+        Scalars *sc = a.sc;
+        const double2 rn = make_double2(red[0], red[1]);
+        if (!isfinite(red[0]) || !isfinite(red[1]) || !isfinite(red[2])) {
+            sc->status = S_NONFINITE;
+            return;
+        }
+        sc->beta = zmul(zdiv(rn, sc->rho), zdiv(sc->alpha, sc->omega));
+        sc->rho = rn;
+        sc->rr = red[2];
+        sc->iter += 1;
+        if (red[2] <= sc->tol2) sc->status = S_CONVERGED;
+    }
+}
+
+static int blas_blocks(long long V, int max_blocks)
+{
+    long long nb = (V + BLAS_NT - 1) / BLAS_NT;
+    long long cap = 152LL * 8;  // 8 resident blocks of 256 threads on each of the 152 SMs
+    if (nb > cap) nb = cap;
+    if (nb > max_blocks) nb = max_blocks;
+    return (int)(nb < 1 ? 1 : nb);
+}
+
+template <int P>
+static cudaError_t launch_blas_p(int op, const BlasArgs &a, cudaStream_t st)
+{
+    const int nb = blas_blocks(a.V, a.rs.max_blocks);
+    switch (op) {
+    case B_INIT: blas_kernel<P, B_INIT><<<nb, BLAS_NT, 0, st>>>(a); break;
+    case B_P: blas_kernel<P, B_P><<<nb, BLAS_NT, 0, st>>>(a); break;
+    case B_S: blas_kernel<P, B_S><<<nb, BLAS_NT, 0, st>>>(a); break;
+    case B_XR: bicg_xr_kernel<P><<<nb, BLAS_NT, 0, st>>>(a); break;
+    case B_NORM: blas_kernel<P, B_NORM><<<nb, BLAS_NT, 0, st>>>(a); break;
+    case B_COPY: blas_kernel<P, B_COPY><<<nb, BLAS_NT, 0, st>>>(a); break;
+    case B_ZERO: blas_kernel<P, B_ZERO><<<nb, BLAS_NT, 0, st>>>(a); break;
+    case B_RESTART: blas_kernel<P, B_RESTART><<<nb, BLAS_NT, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blas(int prec, int op, const BlasArgs &a, cudaStream_t st)
+{
+    switch (prec) {
+    case P64: return launch_blas_p<P64>(op, a, st);
+    case P32: return launch_blas_p<P32>(op, a, st);
+    case P16: return launch_blas_p<P16>(op, a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- precision changes
+template <int PD>
+__global__ void __launch_bounds__(BLAS_NT) convert_scaled_kernel(long long V, SpinorView dst, SpinorView src64,
+                                                                 const Scalars *sc, int slot)
+{
+    typedef typename RealOf<PD>::T T;
+    const double n2 = sc->aux[slot];
+    const double inv = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
+    for (long long x = (long long)blockIdx.x * BLAS_NT + threadIdx.x; x < V; x += (long long)gridDim.x * BLAS_NT) {
+        C<double> s[12];
+        load_spinor<P64>(src64, V, x, s);
+        C<T> d[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) d[k] = {(T)(s[k].r * inv), (T)(s[k].i * inv)};
+        store_spinor<PD>(dst, V, x, d);
+    }
+}
+
+template <int PS>
+__global__ void __launch_bounds__(BLAS_NT) accum_scaled_kernel(long long V, SpinorView phi64, SpinorView xs,
+                                                               const Scalars *sc, int slot)
+{
+    typedef typename RealOf<PS>::T T;
+    const double sc_ = sqrt(sc->aux[slot]);
+    for (long long x = (long long)blockIdx.x * BLAS_NT + threadIdx.x; x < V; x += (long long)gridDim.x * BLAS_NT) {
+        C<double> p[12];
+        C<T> e[12];
+        load_spinor<P64>(phi64, V, x, p);
+        load_spinor<PS>(xs, V, x, e);
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            p[k].r += sc_ * (double)e[k].r;
+            p[k].i += sc_ * (double)e[k].i;
+        }
+        store_spinor<P64>(phi64, V, x, p);
+    }
+}
+
+template <int PD, int PS>
+__global__ void __launch_bounds__(BLAS_NT) convert_kernel(long long V, SpinorView dst, SpinorView src)
+{
+    typedef typename RealOf<PS>::T TS;
+    typedef typename RealOf<PD>::T TD;
+    for (long long x = (long long)blockIdx.x * BLAS_NT + threadIdx.x; x < V; x += (long long)gridDim.x * BLAS_NT) {
+        C<TS> s[12];
+        load_spinor<PS>(src, V, x, s);
+        C<TD> d[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) d[k] = {(TD)s[k].r, (TD)s[k].i};
+        store_spinor<PD>(dst, V, x, d);
+    }
+}
+
+cudaError_t launch_convert_scaled(long long V, int prec, SpinorView dst, SpinorView src64, const Scalars *sc,
+                                  int slot, cudaStream_t st)
+{
+    const int nb = blas_blocks(V, 1 << 30);
+    if (prec == P64) convert_scaled_kernel<P64><<<nb, BLAS_NT, 0, st>>>(V, dst, src64, sc, slot);
+    else if (prec == P32) convert_scaled_kernel<P32><<<nb, BLAS_NT, 0, st>>>(V, dst, src64, sc, slot);
+    else convert_scaled_kernel<P16><<<nb, BLAS_NT, 0, st>>>(V, dst, src64, sc, slot);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_accum_scaled(long long V, int prec, SpinorView phi64, SpinorView x, const Scalars *sc, int slot,
+                                cudaStream_t st)
+{
+    const int nb = blas_blocks(V, 1 << 30);
+    if (prec == P64) accum_scaled_kernel<P64><<<nb, BLAS_NT, 0, st>>>(V, phi64, x, sc, slot);
+    else if (prec == P32) accum_scaled_kernel<P32><<<nb, BLAS_NT, 0, st>>>(V, phi64, x, sc, slot);
+    else accum_scaled_kernel<P16><<<nb, BLAS_NT, 0, st>>>(V, phi64, x, sc, slot);
+    return cudaGetLastError();
+}
+
+template <int PD>
+static cudaError_t convert_from(long long V, SpinorView dst, int ps, SpinorView src, int nb, cudaStream_t st)
+{
+    if (ps == P64) convert_kernel<PD, P64><<<nb, BLAS_NT, 0, st>>>(V, dst, src);
+    else if (ps == P32) convert_kernel<PD, P32><<<nb, BLAS_NT, 0, st>>>(V, dst, src);
+    else convert_kernel<PD, P16><<<nb, BLAS_NT, 0, st>>>(V, dst, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert(long long V, int pd, SpinorView dst, int ps, SpinorView src, cudaStream_t st)
+{
+    const int nb = blas_blocks(V, 1 << 30);
+    if (pd == P64) return convert_from<P64>(V, dst, ps, src, nb, st);
+    if (pd == P32) return convert_from<P32>(V, dst, ps, src, nb, st);
+    return convert_from<P16>(V, dst, ps, src, nb, st);
+}
+
+}  // namespace qdd

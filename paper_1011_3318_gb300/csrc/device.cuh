@@ -1,0 +1,378 @@
+// device.cuh -- device building blocks of the Wilson-clover operator.
+//
+// The operator (Eq. 1 of Osaki & Ishikawa, Lattice 2010, with the O(a)
+// improvement of Sec. 5) is D = A - kappa H, where the hop in direction mu
+// carries the spin projector (1 - gamma_mu) forward and (1 + gamma_mu)
+// backward.  In the DeGrand-Rossi basis every gamma_mu is off-diagonal in
+// chirality, gamma_mu = [[0, X_mu], [X_mu^dag, 0]] on (upper spins 0,1 ;
+// lower spins 2,3), with
+//     X_x = [[0, i], [i, 0]],   X_y = [[0, -1], [1, 0]],
+//     X_z = [[i, 0], [0, -i]],  X_t = 1.
+// Hence (1 -+ gamma_mu) psi = [h ; -+ X_mu^dag h] with h = up -+ X_mu dn: only
+// the two-spin half spinor h is multiplied by the link, and the lower half
+// is rebuilt from it.  This file derives its constants from that structure
+// alone.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "qdd_internal.h"
+
+namespace qdd {
+
+template <int P> struct RealOf { typedef float T; };
+template <> struct RealOf<P64> { typedef double T; };
+
+template <typename T> struct C { T r, i; };
+
+template <typename T> __device__ __forceinline__ C<T> cadd(C<T> a, C<T> b) { return {a.r + b.r, a.i + b.i}; }
+template <typename T> __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) { return {a.r - b.r, a.i - b.i}; }
+template <typename T> __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b)
+{
+    return {a.r * b.r - a.i * b.i, a.r * b.i + a.i * b.r};
+}
+// conj(a) * b
+template <typename T> __device__ __forceinline__ C<T> cmulc(C<T> a, C<T> b)
+{
+    return {a.r * b.r + a.i * b.i, a.r * b.i - a.i * b.r};
+}
+template <typename T> __device__ __forceinline__ C<T> cscale(C<T> a, T s) { return {a.r * s, a.i * s}; }
+template <typename T> __device__ __forceinline__ C<T> ci(C<T> a) { return {-a.i, a.r}; }    // i a
+template <typename T> __device__ __forceinline__ C<T> cmi(C<T> a) { return {a.i, -a.r}; }   // -i a
+template <typename T> __device__ __forceinline__ C<T> cneg(C<T> a) { return {-a.r, -a.i}; }
+template <typename T> __device__ __forceinline__ C<T> cconj(C<T> a) { return {a.r, -a.i}; }
+
+// ---------------------------------------------------------------- geometry
+__device__ __forceinline__ void site_coords(const Geom &g, long long x, int c[4])
+{
+    long long r = x;
+    c[0] = (int)(r % g.L[0]); r /= g.L[0];
+    c[1] = (int)(r % g.L[1]); r /= g.L[1];
+    c[2] = (int)(r % g.L[2]); r /= g.L[2];
+    c[3] = (int)r;
+}
+
+__device__ __forceinline__ long long fwd_site(const Geom &g, long long x, const int c[4], int mu)
+{
+    return c[mu] == g.L[mu] - 1 ? x - (long long)(g.L[mu] - 1) * g.stride[mu] : x + g.stride[mu];
+}
+
+__device__ __forceinline__ long long bwd_site(const Geom &g, long long x, const int c[4], int mu)
+{
+    return c[mu] == 0 ? x + (long long)(g.L[mu] - 1) * g.stride[mu] : x - g.stride[mu];
+}
+
+// ---------------------------------------------------------------- spinors
+template <int P, typename T>
+__device__ __forceinline__ void load_spinor(const SpinorView &f, long long V, long long x, C<T> (&s)[12])
+{
+    if constexpr (P == P64) {
+        const double2 *p = (const double2 *)f.d;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            double2 a = p[k * V + x];
+            s[k] = {(T)a.x, (T)a.y};
+        }
+    } else if constexpr (P == P32) {
+        const float4 *p = (const float4 *)f.d;
+#pragma unroll
+        for (int q = 0; q < 6; q++) {
+            float4 a = p[q * V + x];
+            s[2 * q] = {(T)a.x, (T)a.y};
+            s[2 * q + 1] = {(T)a.z, (T)a.w};
+        }
+    } else {
+        const uint4 *p = (const uint4 *)f.d;
+        float n = f.n[x];
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            uint4 a = p[q * V + x];
+            unsigned w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                __half2 h = *reinterpret_cast<__half2 *>(&w[j]);
+                float2 f2 = __half22float2(h);
+                s[4 * q + j] = {(T)(f2.x * n), (T)(f2.y * n)};
+            }
+        }
+    }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void store_spinor(const SpinorView &f, long long V, long long x, const C<T> (&s)[12])
+{
+    if constexpr (P == P64) {
+        double2 *p = (double2 *)f.d;
+#pragma unroll
+        for (int k = 0; k < 12; k++) p[k * V + x] = make_double2((double)s[k].r, (double)s[k].i);
+    } else if constexpr (P == P32) {
+        float4 *p = (float4 *)f.d;
+#pragma unroll
+        for (int q = 0; q < 6; q++)
+            p[q * V + x] = make_float4((float)s[2 * q].r, (float)s[2 * q].i, (float)s[2 * q + 1].r,
+                                       (float)s[2 * q + 1].i);
+    } else {
+        float m = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf((float)s[k].r), fabsf((float)s[k].i)));
+        float inv = m > 0.f ? 1.0f / m : 0.f;
+        uint4 *p = (uint4 *)f.d;
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            unsigned w[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                __half2 h = __floats2half2_rn((float)s[4 * q + j].r * inv, (float)s[4 * q + j].i * inv);
+                w[j] = *reinterpret_cast<unsigned *>(&h);
+            }
+            p[q * V + x] = make_uint4(w[0], w[1], w[2], w[3]);
+        }
+        f.n[x] = m;
+    }
+}
+
+// ---------------------------------------------------------------- links
+template <typename T>
+__device__ __forceinline__ void rebuild_row2(C<T> (&U)[9])
+{
+    // row2 = conj(row0 x row1) for an SU(3) matrix
+    U[6] = cconj(csub(cmul(U[1], U[5]), cmul(U[2], U[4])));
+    U[7] = cconj(csub(cmul(U[2], U[3]), cmul(U[0], U[5])));
+    U[8] = cconj(csub(cmul(U[0], U[4]), cmul(U[1], U[3])));
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void load_link(const LinkView &u, long long V, int mu, long long x, C<T> (&U)[9])
+{
+    if constexpr (P == P64) {
+        const double2 *p = (const double2 *)u.d + (long long)mu * 9 * V;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            double2 a = p[k * V + x];
+            U[k] = {(T)a.x, (T)a.y};
+        }
+    } else if constexpr (P == P32) {
+        const float4 *p = (const float4 *)u.d + (long long)mu * 3 * V;
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            float4 a = p[q * V + x];
+            U[2 * q] = {(T)a.x, (T)a.y};
+            U[2 * q + 1] = {(T)a.z, (T)a.w};
+        }
+        rebuild_row2(U);
+    } else {
+        const uint2 *p = (const uint2 *)u.d + (long long)mu * 3 * V;
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            uint2 a = p[q * V + x];
+            unsigned w[2] = {a.x, a.y};
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                float2 f2 = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
+                U[2 * q + j] = {(T)f2.x, (T)f2.y};
+            }
+        }
+        rebuild_row2(U);
+    }
+}
+
+// ---------------------------------------------------------------- hopping
+// acc += c * (1 -+ gamma_mu) (x) M psi, with M = U (forward, minus sign)
+// or M = U^dag (backward, plus sign), psi the neighbour's spinor.
+template <int MU, bool FWD, typename T>
+__device__ __forceinline__ void hop(C<T> (&acc)[12], const C<T> (&s)[12], const C<T> (&U)[9], T c)
+{
+    C<T> h0[3], h1[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        C<T> u0 = s[a], u1 = s[3 + a], d0 = s[6 + a], d1 = s[9 + a];
+        C<T> x0, x1;  // X_mu dn
+        if constexpr (MU == 0) { x0 = ci(d1); x1 = ci(d0); }
+        else if constexpr (MU == 1) { x0 = cneg(d1); x1 = d0; }
+        else if constexpr (MU == 2) { x0 = ci(d0); x1 = cmi(d1); }
+        else { x0 = d0; x1 = d1; }
+        if constexpr (FWD) { h0[a] = csub(u0, x0); h1[a] = csub(u1, x1); }
+        else { h0[a] = cadd(u0, x0); h1[a] = cadd(u1, x1); }
+    }
+    C<T> w0[3], w1[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        C<T> p = {0, 0}, q = {0, 0};
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            if constexpr (FWD) {
+                p = cadd(p, cmul(U[a * 3 + b], h0[b]));
+                q = cadd(q, cmul(U[a * 3 + b], h1[b]));
+            } else {
+                p = cadd(p, cmulc(U[b * 3 + a], h0[b]));
+                q = cadd(q, cmulc(U[b * 3 + a], h1[b]));
+            }
+        }
+        w0[a] = p;
+        w1[a] = q;
+    }
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        C<T> l0, l1;  // X_mu^dag w
+        if constexpr (MU == 0) { l0 = cmi(w1[a]); l1 = cmi(w0[a]); }
+        else if constexpr (MU == 1) { l0 = w1[a]; l1 = cneg(w0[a]); }
+        else if constexpr (MU == 2) { l0 = cmi(w0[a]); l1 = ci(w1[a]); }
+        else { l0 = w0[a]; l1 = w1[a]; }
+        if constexpr (FWD) { l0 = cneg(l0); l1 = cneg(l1); }
+        acc[a] = cadd(acc[a], cscale(w0[a], c));
+        acc[3 + a] = cadd(acc[3 + a], cscale(w1[a], c));
+        acc[6 + a] = cadd(acc[6 + a], cscale(l0, c));
+        acc[9 + a] = cadd(acc[9 + a], cscale(l1, c));
+    }
+}
+
+// ---------------------------------------------------------------- clover
+template <int P, typename T>
+__device__ __forceinline__ void load_clover(const CloverView &A, long long V, long long x, T (&a)[72])
+{
+    if constexpr (P == P64) {
+        const double2 *p = (const double2 *)A.d;
+#pragma unroll
+        for (int k = 0; k < 36; k++) {
+            double2 v = p[k * V + x];
+            a[2 * k] = (T)v.x;
+            a[2 * k + 1] = (T)v.y;
+        }
+    } else if constexpr (P == P32) {
+        const float4 *p = (const float4 *)A.d;
+#pragma unroll
+        for (int k = 0; k < 18; k++) {
+            float4 v = p[k * V + x];
+            a[4 * k] = (T)v.x; a[4 * k + 1] = (T)v.y; a[4 * k + 2] = (T)v.z; a[4 * k + 3] = (T)v.w;
+        }
+    } else {
+        const uint4 *p = (const uint4 *)A.d;
+        float n = A.n[x];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            uint4 v = p[k * V + x];
+            unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                float2 f2 = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
+                a[8 * k + 2 * j] = (T)(f2.x * n);
+                a[8 * k + 2 * j + 1] = (T)(f2.y * n);
+            }
+        }
+    }
+}
+
+// Position of the lower off-diagonal element (i > j) of a packed 6x6 block.
+__host__ __device__ constexpr int cl_off(int i, int j) { return 6 + 2 * (i * (i - 1) / 2 + j); }
+
+// out = A psi with A the two packed Hermitian 6x6 chiral blocks.
+template <typename T>
+__device__ __forceinline__ void clover_apply(const T (&a)[72], const C<T> (&s)[12], C<T> (&o)[12])
+{
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int base = 36 * h;
+#pragma unroll
+        for (int i = 0; i < 6; i++) {
+            C<T> acc = cscale(s[6 * h + i], a[base + i]);
+#pragma unroll
+            for (int j = 0; j < 6; j++) {
+                if (j < i) {
+                    C<T> l = {a[base + cl_off(i, j)], a[base + cl_off(i, j) + 1]};
+                    acc = cadd(acc, cmul(l, s[6 * h + j]));
+                } else if (j > i) {
+                    C<T> l = {a[base + cl_off(j, i)], a[base + cl_off(j, i) + 1]};
+                    acc = cadd(acc, cmulc(l, s[6 * h + j]));
+                }
+            }
+            o[6 * h + i] = acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- reductions
+// Sum of N doubles over the block; the total ends up in every lane of warp 0
+// (thread 0 in particular).  All threads of the block must call it.
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N], double *sm /* N * 32 */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < N; k++)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+    __syncthreads();  // sm may be in use by a previous call
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < N; k++) sm[k * 32 + warp] = v[k];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int k = 0; k < N; k++) {
+            v[k] = lane < nw ? sm[k * 32 + lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        }
+    }
+}
+
+// Block sum that leaves the total in every thread of the block.
+template <int N>
+__device__ __forceinline__ void block_allsum(double (&v)[N], double *sm /* N * 32 + N */)
+{
+    block_sum<N>(v, sm);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int k = 0; k < N; k++) sm[N * 32 + k] = v[k];
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < N; k++) v[k] = sm[N * 32 + k];
+}
+
+// Grid-wide sum by the last-block pattern: every block stores its partial
+// sums, and the block that arrives last adds them in block order (so the
+// result does not depend on scheduling) and returns true in thread 0 with
+// the totals in v.  No block waits for another.
+template <int N>
+__device__ __forceinline__ bool grid_sum(double (&v)[N], const ReduceScratch &rs)
+{
+    __shared__ double sm[N * 32];
+    __shared__ int last;
+    block_sum<N>(v, sm);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < N; k++) rs.partials[(long long)blockIdx.x * N + k] = v[k];
+        __threadfence();
+        unsigned t = atomicAdd(rs.counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    double acc[N];
+#pragma unroll
+    for (int k = 0; k < N; k++) acc[k] = 0.0;
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < N; k++) acc[k] += __ldcg(rs.partials + (long long)b * N + k);
+    block_sum<N>(acc, sm);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < N; k++) v[k] = acc[k];
+        *rs.counter = 0u;
+    }
+    return threadIdx.x == 0;
+}
+
+// ---------------------------------------------------------------- scalars
+__device__ __forceinline__ double2 zdiv(double2 a, double2 b)
+{
+    double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 zmul(double2 a, double2 b)
+{
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+}  // namespace qdd

@@ -1,0 +1,166 @@
+// dslash.cu -- the Wilson-clover operator D = A - kappa H on the whole
+// lattice (Eq. 1; the global "Dv" of Alg. 1 line 9 and of Eq. 3).
+//
+// One thread per site.  Each thread reads its own spinor and clover, then
+// for each of the 8 hops the neighbour's spinor and the link, spin-projects
+// the neighbour to a two-spin half spinor, multiplies it by U (forward) or
+// U^dag (backward) and rebuilds the four-spin result.  All fields are planar
+// so that every load of a warp is one contiguous, fully used segment; the
+// 8-fold re-reads of neighbour spinors and the 2-fold re-reads of links are
+// served by L1/L2, leaving the compulsory traffic (spinor in, links, clover,
+// spinor out) for HBM.  Epilogues fuse the residual update and the dot
+// products of BiCGStab, so those need no separate pass over memory.
+#include "device.cuh"
+#include "lib.h"
+
+namespace qdd {
+
+template <int P, int MU, typename T>
+__device__ __forceinline__ void hop_pair(const DslashArgs &a, long long x, const int c[4], C<T> (&acc)[12], T mk)
+{
+    const long long V = a.g.V;
+    {
+        const long long xf = fwd_site(a.g, x, c, MU);
+        const T sf = (c[MU] == a.g.L[MU] - 1 && a.g.bc[MU] < 0) ? -mk : mk;
+        C<T> s[12], U[9];
+        load_spinor<P>(a.in, V, xf, s);
+        load_link<P>(a.U, V, MU, x, U);
+        hop<MU, true>(acc, s, U, sf);
+    }
+    {
+        const long long xb = bwd_site(a.g, x, c, MU);
+        const T sb = (c[MU] == 0 && a.g.bc[MU] < 0) ? -mk : mk;
+        C<T> s[12], U[9];
+        load_spinor<P>(a.in, V, xb, s);
+        load_link<P>(a.U, V, MU, xb, U);
+        hop<MU, false>(acc, s, U, sb);
+    }
+}
+
+template <int P, int EPI, int NT>
+__global__ void __launch_bounds__(NT) dslash_kernel(const DslashArgs a)
+{
+    typedef typename RealOf<P>::T T;
+    constexpr int NRED = (EPI == EPI_XMY_NORM) ? 1 : (EPI == EPI_RV || EPI == EPI_TS) ? 3 : 0;
+    if constexpr (EPI == EPI_RV || EPI == EPI_TS) {
+        if (a.sc->status != S_RUN) return;
+    }
+    const long long V = a.g.V;
+    const long long x = (long long)blockIdx.x * NT + threadIdx.x;
+    const bool active = x < V;
+    double red[NRED > 0 ? NRED : 1] = {0.0};
+
+    if (active) {
+        int c[4];
+        site_coords(a.g, x, c);
+        C<T> acc[12];
+        {
+            T av[72];
+            C<T> s[12];
+            load_clover<P>(a.A, V, x, av);
+            load_spinor<P>(a.in, V, x, s);
+            clover_apply(av, s, acc);
+        }
+        const T mk = (T)(-a.kappa);
+        hop_pair<P, 0>(a, x, c, acc, mk);
+        hop_pair<P, 1>(a, x, c, acc, mk);
+        hop_pair<P, 2>(a, x, c, acc, mk);
+        hop_pair<P, 3>(a, x, c, acc, mk);
+
+        if constexpr (EPI == EPI_XMY || EPI == EPI_XMY_NORM) {
+            C<T> y[12];
+            load_spinor<P>(a.y, V, x, y);
+#pragma unroll
+            for (int k = 0; k < 12; k++) acc[k] = csub(y[k], acc[k]);
+        }
+        store_spinor<P>(a.out, V, x, acc);
+
+        if constexpr (EPI == EPI_XMY_NORM) {
+            T n2 = 0;
+#pragma unroll
+            for (int k = 0; k < 12; k++) n2 += acc[k].r * acc[k].r + acc[k].i * acc[k].i;
+            red[0] = (double)n2;
+        } else if constexpr (EPI == EPI_RV || EPI == EPI_TS) {
+            C<T> y[12];
+            load_spinor<P>(a.y, V, x, y);
+            T dr = 0, di = 0, n2 = 0;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                // EPI_RV: <y, out> = sum conj(y) out ; EPI_TS: <out, y> = sum conj(out) y
+                C<T> p = (EPI == EPI_RV) ? cmulc(y[k], acc[k]) : cmulc(acc[k], y[k]);
+                dr += p.r;
+                di += p.i;
+                n2 += acc[k].r * acc[k].r + acc[k].i * acc[k].i;
+            }
+            red[0] = (double)dr;
+            red[1] = (double)di;
+            red[2] = (double)n2;
+        }
+    }
+
+    if constexpr (NRED > 0) {
+        if (grid_sum<NRED>(red, a.rs)) {
+            Scalars *sc = a.sc;
+            if constexpr (EPI == EPI_XMY_NORM) {
+                sc->aux[a.aux_slot] = red[0];
+            } else if constexpr (EPI == EPI_RV) {
+                const double2 rv = make_double2(red[0], red[1]);
+                const double mag2 = rv.x * rv.x + rv.y * rv.y;
+                if (!isfinite(mag2) || !isfinite(red[2])) {
+                    sc->status = S_NONFINITE;
+                } else if (mag2 <= 1e-60 * sc->rhat2 * red[2]) {
+                    sc->status = S_BREAK_RV;
+                } else {
+                    sc->alpha = zdiv(sc->rho, rv);
+                }
+            } else {
+                const double tt = red[2];
+                if (!isfinite(tt) || !isfinite(red[0]) || !isfinite(red[1])) {
+                    sc->status = S_NONFINITE;
+                } else if (tt == 0.0) {
+                    sc->status = S_BREAK_TT;
+                } else {
+                    sc->omega = make_double2(red[0] / tt, red[1] / tt);
+                }
+            }
+        }
+    }
+}
+
+template <int P, int EPI>
+static cudaError_t launch_one(const DslashArgs &a, cudaStream_t st)
+{
+    constexpr int NT = (P == P64) ? 128 : 256;
+    const long long nb = (a.g.V + NT - 1) / NT;
+    if (EPI == EPI_XMY_NORM || EPI == EPI_RV || EPI == EPI_TS) {
+        if (nb > a.rs.max_blocks) return cudaErrorInvalidConfiguration;
+    }
+    dslash_kernel<P, EPI, NT><<<(unsigned)nb, NT, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t launch_prec(int epi, const DslashArgs &a, cudaStream_t st)
+{
+    switch (epi) {
+    case EPI_D: return launch_one<P, EPI_D>(a, st);
+    case EPI_XMY: return launch_one<P, EPI_XMY>(a, st);
+    case EPI_XMY_NORM: return launch_one<P, EPI_XMY_NORM>(a, st);
+    case EPI_RV: return launch_one<P, EPI_RV>(a, st);
+    case EPI_TS: return launch_one<P, EPI_TS>(a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_dslash(int prec, int epi, const DslashArgs &a, cudaStream_t st)
+{
+    if (a.g.V <= 0) return cudaSuccess;
+    switch (prec) {
+    case P64: return launch_prec<P64>(epi, a, st);
+    case P32: return launch_prec<P32>(epi, a, st);
+    case P16: return launch_prec<P16>(epi, a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace qdd

@@ -1,0 +1,347 @@
+// lattice.cu -- layout conversions, gauge-field import and the clover term.
+//
+// The clover term is the O(a) improvement of the Wilson quark named in
+// Sec. 1 and Sec. 5 (coefficient c_SW):
+//     A(x) = 1 + i kappa c_sw sum_{mu<nu} sigma_{mu nu} Fhat_{mu nu}(x),
+//     Fhat_{mu nu} = (Q_{mu nu} - Q_{mu nu}^dag) / 8,
+// Q the sum of the four plaquette leaves at x in the (mu, nu) plane.  In the
+// DeGrand-Rossi basis sigma_{mu nu} = (i/2)[gamma_mu, gamma_nu] is block
+// diagonal in chirality; writing its 2x2 blocks with Pauli matrices
+// (s_x, s_y, s_z) gives, for the upper (spins 0,1) and lower (spins 2,3)
+// blocks,
+//     upper: s_z (F_xy - F_zt) + s_y (F_xz + F_yt) + s_x (F_yz - F_xt)
+//     lower: s_z (F_xy + F_zt) + s_y (F_xz - F_yt) + s_x (F_yz + F_xt)
+// so each 6x6 block is 1 + i kappa c_sw [[Gz, Gx - i Gy], [Gx + i Gy, -Gz]].
+// The build runs once per (gauge field, kappa, c_sw) in FP64 and stores the
+// result in all three working precisions.
+#include "device.cuh"
+#include "lib.h"
+
+namespace qdd {
+
+// ---------------------------------------------------------------- spinors
+template <int P>
+__global__ void import_spinor_kernel(Geom g, SpinorView dst, const double *src)
+{
+    typedef typename RealOf<P>::T T;
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.V) return;
+    const double2 *s2 = reinterpret_cast<const double2 *>(src) + x * 12;
+    C<T> s[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        double2 v = s2[k];
+        s[k] = {(T)v.x, (T)v.y};
+    }
+    store_spinor<P>(dst, g.V, x, s);
+}
+
+template <int P>
+__global__ void export_spinor_kernel(Geom g, double *dst, SpinorView src)
+{
+    typedef typename RealOf<P>::T T;
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.V) return;
+    C<T> s[12];
+    load_spinor<P>(src, g.V, x, s);
+    double2 *d2 = reinterpret_cast<double2 *>(dst) + x * 12;
+#pragma unroll
+    for (int k = 0; k < 12; k++) d2[k] = make_double2((double)s[k].r, (double)s[k].i);
+}
+
+cudaError_t launch_import_spinor(const Geom &g, int prec, SpinorView dst, const double *src, cudaStream_t st)
+{
+    const unsigned nb = (unsigned)((g.V + 255) / 256);
+    if (prec == P64) import_spinor_kernel<P64><<<nb, 256, 0, st>>>(g, dst, src);
+    else if (prec == P32) import_spinor_kernel<P32><<<nb, 256, 0, st>>>(g, dst, src);
+    else import_spinor_kernel<P16><<<nb, 256, 0, st>>>(g, dst, src);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorView src, cudaStream_t st)
+{
+    const unsigned nb = (unsigned)((g.V + 255) / 256);
+    if (prec == P64) export_spinor_kernel<P64><<<nb, 256, 0, st>>>(g, dst, src);
+    else if (prec == P32) export_spinor_kernel<P32><<<nb, 256, 0, st>>>(g, dst, src);
+    else export_spinor_kernel<P16><<<nb, 256, 0, st>>>(g, dst, src);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- gauge
+__global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, float4 *U32, uint2 *U16,
+                                     unsigned long long *maxdev)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double dev = 0.0;
+    if (t < g.V * 4) {
+        const long long x = t >> 2;
+        const int mu = (int)(t & 3);
+        const double2 *u2 = reinterpret_cast<const double2 *>(U) + t * 9;
+        C<double> m[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            double2 v = u2[k];
+            m[k] = {v.x, v.y};
+        }
+        // unitarity: max |(U^dag U - 1)_{ab}|
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+#pragma unroll
+            for (int b = 0; b < 3; b++) {
+                C<double> s = {a == b ? -1.0 : 0.0, 0.0};
+#pragma unroll
+                for (int k = 0; k < 3; k++) s = cadd(s, cmulc(m[k * 3 + a], m[k * 3 + b]));
+                dev = fmax(dev, sqrt(s.r * s.r + s.i * s.i));
+            }
+        // determinant
+        C<double> det = cmul(m[0], csub(cmul(m[4], m[8]), cmul(m[5], m[7])));
+        det = csub(det, cmul(m[1], csub(cmul(m[3], m[8]), cmul(m[5], m[6]))));
+        det = cadd(det, cmul(m[2], csub(cmul(m[3], m[7]), cmul(m[4], m[6]))));
+        dev = fmax(dev, sqrt((det.r - 1.0) * (det.r - 1.0) + det.i * det.i));
+        if (!isfinite(dev)) dev = 1e300;
+
+        const long long V = g.V;
+#pragma unroll
+        for (int k = 0; k < 9; k++) U64[((long long)mu * 9 + k) * V + x] = make_double2(m[k].r, m[k].i);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            U32[((long long)mu * 3 + q) * V + x] =
+                make_float4((float)m[2 * q].r, (float)m[2 * q].i, (float)m[2 * q + 1].r, (float)m[2 * q + 1].i);
+            __half2 h0 = __floats2half2_rn((float)m[2 * q].r, (float)m[2 * q].i);
+            __half2 h1 = __floats2half2_rn((float)m[2 * q + 1].r, (float)m[2 * q + 1].i);
+            U16[((long long)mu * 3 + q) * V + x] =
+                make_uint2(*reinterpret_cast<unsigned *>(&h0), *reinterpret_cast<unsigned *>(&h1));
+        }
+    }
+    // block max, then one atomic per block on the bit pattern (non-negative
+    // doubles order like their bit patterns)
+    for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(maxdev, (unsigned long long)__double_as_longlong(dev));
+}
+
+cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void *U32, void *U16,
+                                 unsigned long long *maxdev, cudaStream_t st)
+{
+    const long long n = g.V * 4;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    gauge_convert_kernel<<<nb, 256, 0, st>>>(g, U, (double2 *)U64, (float4 *)U32, (uint2 *)U16, maxdev);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- clover
+typedef C<double> Z;
+
+struct M3 {
+    Z e[9];
+};
+
+__device__ __forceinline__ M3 m3_load(const double2 *U64, long long V, int mu, long long x)
+{
+    M3 m;
+    const double2 *p = U64 + (long long)mu * 9 * V;
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        double2 v = p[k * V + x];
+        m.e[k] = {v.x, v.y};
+    }
+    return m;
+}
+
+__device__ __forceinline__ M3 m3_mul(const M3 &a, const M3 &b)
+{
+    M3 c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            Z s = {0, 0};
+#pragma unroll
+            for (int k = 0; k < 3; k++) s = cadd(s, cmul(a.e[i * 3 + k], b.e[k * 3 + j]));
+            c.e[i * 3 + j] = s;
+        }
+    return c;
+}
+
+__device__ __forceinline__ M3 m3_dag(const M3 &a)
+{
+    M3 c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) c.e[i * 3 + j] = cconj(a.e[j * 3 + i]);
+    return c;
+}
+
+// a * b^dag
+__device__ __forceinline__ M3 m3_mul_d(const M3 &a, const M3 &b)
+{
+    M3 c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            Z s = {0, 0};
+#pragma unroll
+            for (int k = 0; k < 3; k++) s = cadd(s, cmul(a.e[i * 3 + k], cconj(b.e[j * 3 + k])));
+            c.e[i * 3 + j] = s;
+        }
+    return c;
+}
+
+// a^dag * b
+__device__ __forceinline__ M3 m3_dmul(const M3 &a, const M3 &b)
+{
+    M3 c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            Z s = {0, 0};
+#pragma unroll
+            for (int k = 0; k < 3; k++) s = cadd(s, cmulc(a.e[k * 3 + i], b.e[k * 3 + j]));
+            c.e[i * 3 + j] = s;
+        }
+    return c;
+}
+
+__device__ __forceinline__ long long shifted(const Geom &g, const int c[4], int mu, int dm, int nu, int dn)
+{
+    int d[4] = {c[0], c[1], c[2], c[3]};
+    d[mu] = (d[mu] + dm + g.L[mu]) % g.L[mu];
+    d[nu] = (d[nu] + dn + g.L[nu]) % g.L[nu];
+    return d[0] + g.stride[1] * d[1] + g.stride[2] * d[2] + g.stride[3] * d[3];
+}
+
+// Fhat_{mu nu}(x) = (Q - Q^dag) / 8 from the four counter-clockwise leaves.
+__device__ M3 field_strength(const Geom &g, const double2 *U64, long long x, const int c[4], int mu, int nu)
+{
+    const long long V = g.V;
+    const long long xpm = shifted(g, c, mu, 1, nu, 0), xpn = shifted(g, c, mu, 0, nu, 1);
+    const long long xmm = shifted(g, c, mu, -1, nu, 0), xmn = shifted(g, c, mu, 0, nu, -1);
+    const long long xmm_pn = shifted(g, c, mu, -1, nu, 1), xmm_mn = shifted(g, c, mu, -1, nu, -1);
+    const long long xpm_mn = shifted(g, c, mu, 1, nu, -1);
+    M3 Q;
+    // x -> x+mu -> x+mu+nu -> x+nu -> x
+    M3 l = m3_mul(m3_load(U64, V, mu, x), m3_load(U64, V, nu, xpm));
+    l = m3_mul_d(l, m3_load(U64, V, mu, xpn));
+    l = m3_mul_d(l, m3_load(U64, V, nu, x));
+    Q = l;
+    // x -> x+nu -> x-mu+nu -> x-mu -> x
+    l = m3_mul_d(m3_load(U64, V, nu, x), m3_load(U64, V, mu, xmm_pn));
+    l = m3_mul_d(l, m3_load(U64, V, nu, xmm));
+    l = m3_mul(l, m3_load(U64, V, mu, xmm));
+#pragma unroll
+    for (int k = 0; k < 9; k++) Q.e[k] = cadd(Q.e[k], l.e[k]);
+    // x -> x-mu -> x-mu-nu -> x-nu -> x:  U_mu(x-mu)^dag U_nu(x-mu-nu)^dag = (U_nu(x-mu-nu) U_mu(x-mu))^dag
+    l = m3_dag(m3_mul(m3_load(U64, V, nu, xmm_mn), m3_load(U64, V, mu, xmm)));
+    l = m3_mul(l, m3_load(U64, V, mu, xmm_mn));
+    l = m3_mul(l, m3_load(U64, V, nu, xmn));
+#pragma unroll
+    for (int k = 0; k < 9; k++) Q.e[k] = cadd(Q.e[k], l.e[k]);
+    // x -> x-nu -> x+mu-nu -> x+mu -> x
+    l = m3_dmul(m3_load(U64, V, nu, xmn), m3_load(U64, V, mu, xmn));
+    l = m3_mul(l, m3_load(U64, V, nu, xpm_mn));
+    l = m3_mul_d(l, m3_load(U64, V, mu, x));
+#pragma unroll
+    for (int k = 0; k < 9; k++) Q.e[k] = cadd(Q.e[k], l.e[k]);
+    M3 F;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            Z q = Q.e[i * 3 + j], qd = cconj(Q.e[j * 3 + i]);
+            F.e[i * 3 + j] = cscale(csub(q, qd), 0.125);
+        }
+    return F;
+}
+
+__global__ void __launch_bounds__(128) clover_build_kernel(Geom g, const double2 *U64, double kappa, double csw,
+                                                           double2 *A64, float4 *A32, uint4 *A16, float *A16n)
+{
+    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.V) return;
+    int c[4];
+    site_coords(g, x, c);
+    // planes in the order (x,y) (x,z) (x,t) (y,z) (y,t) (z,t)
+    M3 F01 = field_strength(g, U64, x, c, 0, 1);
+    M3 F02 = field_strength(g, U64, x, c, 0, 2);
+    M3 F03 = field_strength(g, U64, x, c, 0, 3);
+    M3 F12 = field_strength(g, U64, x, c, 1, 2);
+    M3 F13 = field_strength(g, U64, x, c, 1, 3);
+    M3 F23 = field_strength(g, U64, x, c, 2, 3);
+    double pk[72];
+    const double kc = kappa * csw;
+#pragma unroll 1
+    for (int h = 0; h < 2; h++) {
+        const double sg = h == 0 ? -1.0 : 1.0;
+        Z Gz[9], Gy[9], Gx[9];
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            Gz[k] = cadd(F01.e[k], cscale(F23.e[k], sg));
+            Gy[k] = csub(F02.e[k], cscale(F13.e[k], sg));
+            Gx[k] = cadd(F12.e[k], cscale(F03.e[k], sg));
+        }
+        // 6x6 block M = 1 + i kc B, B = [[Gz, Gx - i Gy], [Gx + i Gy, -Gz]]
+        Z M[36];
+#pragma unroll
+        for (int s = 0; s < 2; s++)
+#pragma unroll
+            for (int t = 0; t < 2; t++)
+#pragma unroll
+                for (int a = 0; a < 3; a++)
+#pragma unroll
+                    for (int b = 0; b < 3; b++) {
+                        const int k = a * 3 + b;
+                        Z bst;
+                        if (s == 0 && t == 0) bst = Gz[k];
+                        else if (s == 1 && t == 1) bst = cneg(Gz[k]);
+                        else if (s == 0) bst = csub(Gx[k], ci(Gy[k]));
+                        else bst = cadd(Gx[k], ci(Gy[k]));
+                        Z m = cscale(ci(bst), kc);
+                        if (s == t && a == b) m.r += 1.0;
+                        M[(s * 3 + a) * 6 + (t * 3 + b)] = m;
+                    }
+        const int base = 36 * h;
+#pragma unroll
+        for (int i = 0; i < 6; i++) pk[base + i] = M[i * 6 + i].r;
+#pragma unroll
+        for (int i = 1; i < 6; i++)
+#pragma unroll
+            for (int j = 0; j < i; j++) {
+                pk[base + cl_off(i, j)] = M[i * 6 + j].r;
+                pk[base + cl_off(i, j) + 1] = M[i * 6 + j].i;
+            }
+    }
+    const long long V = g.V;
+    double nrm = 0.0;
+#pragma unroll
+    for (int k = 0; k < 72; k++) nrm = fmax(nrm, fabs(pk[k]));
+    const double inv = nrm > 0 ? 1.0 / nrm : 0.0;
+#pragma unroll
+    for (int k = 0; k < 36; k++) A64[k * V + x] = make_double2(pk[2 * k], pk[2 * k + 1]);
+#pragma unroll
+    for (int k = 0; k < 18; k++)
+        A32[k * V + x] = make_float4((float)pk[4 * k], (float)pk[4 * k + 1], (float)pk[4 * k + 2], (float)pk[4 * k + 3]);
+#pragma unroll
+    for (int k = 0; k < 9; k++) {
+        unsigned w[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            __half2 hh = __floats2half2_rn((float)(pk[8 * k + 2 * j] * inv), (float)(pk[8 * k + 2 * j + 1] * inv));
+            w[j] = *reinterpret_cast<unsigned *>(&hh);
+        }
+        A16[k * V + x] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    A16n[x] = (float)nrm;
+}
+
+cudaError_t launch_clover_build(const Geom &g, const void *U64, double kappa, double csw, void *A64, void *A32,
+                                void *A16, float *A16n, cudaStream_t st)
+{
+    const unsigned nb = (unsigned)((g.V + 127) / 128);
+    clover_build_kernel<<<nb, 128, 0, st>>>(g, (const double2 *)U64, kappa, csw, (double2 *)A64, (float4 *)A32,
+                                            (uint4 *)A16, A16n);
+    return cudaGetLastError();
+}
+
+}  // namespace qdd

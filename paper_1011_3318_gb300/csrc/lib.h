@@ -1,0 +1,165 @@
+// lib.h -- host-side structures and kernel launchers of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "qdd_internal.h"
+
+namespace qdd {
+
+// Dslash epilogues.
+enum Epi {
+    EPI_D = 0,         // out = D in
+    EPI_XMY = 1,       // out = y - D in
+    EPI_XMY_NORM = 2,  // out = y - D in, |out|^2 -> sc->aux[aux_slot]
+    EPI_RV = 3,        // out = D in, alpha = rho / <y, out>   (BiCGStab, y = rhat)
+    EPI_TS = 4,        // out = D in, omega = <out, y> / |out|^2 (BiCGStab, y = s)
+};
+
+struct DslashArgs {
+    Geom g;
+    SpinorView out, in, y;
+    LinkView U;
+    CloverView A;
+    double kappa;
+    ReduceScratch rs;
+    Scalars *sc;
+    int aux_slot;
+};
+
+cudaError_t launch_dslash(int prec, int epi, const DslashArgs &a, cudaStream_t st);
+
+// Field conversions between the canonical FP64 layout and internal layouts.
+cudaError_t launch_import_spinor(const Geom &g, int prec, SpinorView dst, const double *src, cudaStream_t st);
+cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorView src, cudaStream_t st);
+
+// Gauge conversion; writes max(|U^dag U - 1|, |det U - 1|) as the bit
+// pattern of a non-negative double into *maxdev (device, zeroed first).
+cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void *U32, void *U16,
+                                 unsigned long long *maxdev, cudaStream_t st);
+
+// Clover term from the FP64 links, stored in all three precisions.
+cudaError_t launch_clover_build(const Geom &g, const void *U64, double kappa, double csw, void *A64, void *A32,
+                                void *A16, float *A16n, cudaStream_t st);
+
+// BLAS of the Krylov solvers (K-B4 in the design notes).
+struct BlasArgs {
+    long long V;
+    SpinorView f[8];
+    Scalars *sc;
+    ReduceScratch rs;
+    int aux_slot;
+    double tol2_rel;   // bicg_init: tol^2
+};
+
+enum BlasOp {
+    B_INIT = 0,       // f0 = b: r(f1) = b, rhat(f2) = b, x(f3) = p(f4) = v(f5) = 0; scalars reset
+    B_P = 1,          // p(f0) = r(f1) + beta (p - omega v(f2))
+    B_S = 2,          // s(f0) = r(f1) - alpha v(f2)
+    B_XR = 3,         // x(f0) += alpha phat(f1) + omega shat(f2); r(f3) = s(f4) - omega t(f5); <rhat(f6), r>, |r|^2
+    B_NORM = 4,       // |f0|^2 -> aux[aux_slot]
+    B_COPY = 5,       // f0 = f1 (same precision)
+    B_ZERO = 6,       // f0 = 0
+    B_RESTART = 7,    // rhat(f0) = r(f1); p(f2) = v(f3) = 0; rho = <r, r>; alpha = omega = 1
+};
+
+cudaError_t launch_blas(int prec, int op, const BlasArgs &a, cudaStream_t st);
+
+// Precision changes around the inner solve (outer defect correction).
+// dst(prec) = src64 / sqrt(aux[slot])
+cudaError_t launch_convert_scaled(long long V, int prec, SpinorView dst, SpinorView src64, const Scalars *sc,
+                                  int slot, cudaStream_t st);
+// phi64 += sqrt(aux[slot]) * x(prec)
+cudaError_t launch_accum_scaled(long long V, int prec, SpinorView phi64, SpinorView x, const Scalars *sc, int slot,
+                                cudaStream_t st);
+// dst(pd) = src(ps)
+cudaError_t launch_convert(long long V, int pd, SpinorView dst, int ps, SpinorView src, cudaStream_t st);
+
+// RAS block solve (Alg. 1 lines 4-8) over every domain.
+struct RasArgs {
+    Geom g;
+    DomainGeom dg;
+    SpinorView in;     // residual rho (projected per domain)
+    SpinorView vout;   // v on bulk sites (d == nullptr: not written)
+    SpinorView acc;    // phi: acc = v (accumulate = 0) or acc += v (accumulate = 1)
+    int accumulate;
+    LinkView U;
+    CloverView A;
+    float kappa;
+    int n_iter;
+    const Scalars *sc;  // may be null; a non-running solver status skips the work
+    float2 *scratch;    // general kernel: per-slot rho, q, v
+    int slots;
+};
+
+// Sites of an extended domain up to which the shared-memory kernel is used.
+constexpr int RAS_SMEM_MAX_SITES = 512;
+
+cudaError_t launch_ras_block(int prec, const RasArgs &a, cudaStream_t st);
+size_t ras_scratch_bytes(const DomainGeom &dg, int slots);
+int ras_default_slots();
+
+bool domain_geom(const Geom &g, const int block[4], int s, DomainGeom *dg, std::string *why);
+
+}  // namespace qdd
+
+struct qdd_field {
+    qdd_lattice *lat;
+    int prec;
+    void *d;
+    float *n;
+    qdd::SpinorView view() const { return qdd::SpinorView{d, n}; }
+};
+
+// Solver workspace (allocated on first use, kept with the lattice).
+struct qdd_work;
+
+struct qdd_lattice {
+    qdd::Geom g;
+    int device;
+    cudaStream_t stream;
+    // links
+    void *U64, *U32, *U16;
+    bool has_gauge;
+    // clover cache
+    bool clover_valid;
+    double kappa_c, csw_c;
+    void *A64, *A32, *A16;
+    float *A16n;
+    // reductions and device scalars
+    qdd::ReduceScratch rs;
+    qdd::Scalars *sc;       // device
+    qdd::Scalars *sc_host;  // pinned mirror
+    unsigned long long *maxdev;
+    // canonical staging buffers for host pointers
+    double *stage_a, *stage_b;
+    // RAS scratch
+    float2 *ras_scratch;
+    size_t ras_scratch_bytes;
+    // in/out fields of the canonical-layout entry points, per precision
+    void *io_d[3][2];
+    float *io_n[3][2];
+    qdd_work *work;
+};
+
+// Helpers shared by api.cu and solver.cu.
+namespace qdd {
+void set_error(const std::string &msg);
+qdd_status cuda_fail(cudaError_t e, const char *what);
+qdd_status ensure_clover(qdd_lattice *lat, double kappa, double csw);
+size_t spinor_bytes(long long V, int prec);
+qdd_status field_alloc(long long V, int prec, void **d, float **n);
+void field_free(void *d, float *n);
+LinkView links_of(const qdd_lattice *lat, int prec);
+CloverView clover_of(const qdd_lattice *lat, int prec);
+qdd_status run_dslash(qdd_lattice *lat, int prec, int epi, SpinorView out, SpinorView in, SpinorView y, double kappa,
+                      int aux_slot);
+qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params *p, const DomainGeom &dg,
+                            SpinorView out, SpinorView in, SpinorView rho, SpinorView v, double kappa, int *dv,
+                            const Scalars *sc);
+qdd_status solve_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, double kappa, double csw, double tol,
+                      const qdd_solver_params *p, qdd_solve_info *info);
+void work_free(qdd_work *w);
+}  // namespace qdd

@@ -1,0 +1,355 @@
+// ras.cu -- one sweep of the restricted additive Schwarz iteration (Alg. 1
+// lines 3-8, Sec. 2) over every domain of the lattice in one launch.
+//
+// For each domain i (one CTA): the residual is projected onto the extended
+// domain Omega'_i (line 4), D_{Omega'_i} v = r is solved approximately with
+// the Dirichlet boundary (line 5) by n_dominv minimal-residual iterations
+// from zero,
+//     q = D rho,  alpha = <q, rho> / <q, q>,  v += alpha rho,  rho -= alpha q,
+// and v is restricted to the bulk block Omega_i (line 6) and written there;
+// bulk blocks tile the lattice, so the writes of all CTAs form the sum of
+// line 8.  Domains are independent (the paper runs one per GPU; here one per
+// CTA), so a sweep needs no grid-wide synchronisation.
+//
+// The Dirichlet operator keeps the clover term on every site of Omega'_i and
+// drops every hop whose target lies outside Omega'_i; a direction in which
+// the block spans the whole lattice is not decomposed and its hops wrap
+// around inside the domain with the boundary sign.  The domain arithmetic is
+// FP32 whatever the storage precision of the fields.
+//
+// Two kernels:
+//  * ras_smem_kernel: extended domains of at most RAS_SMEM_MAX_SITES sites.
+//    One thread per site; the MR residual rho lives in shared memory (read
+//    by the neighbours' hops), q and v in registers; links and clover come
+//    through L1.
+//  * ras_gmem_kernel: any domain size.  A persistent grid of `slots` CTAs
+//    loops over the domains; rho, q and v of the current domain live in a
+//    per-CTA slot of global scratch (L2-resident for moderate domains).
+#include "device.cuh"
+#include "lib.h"
+
+namespace qdd {
+
+struct DomSite {
+    long long x;      // global site
+    bool act, bulk;
+    int nf[4], nb[4]; // local neighbour index, -1 when the hop leaves the domain
+    long long xb[4];  // global backward neighbour (its link is U_mu(x - mu))
+    float cf[4], cb[4];
+};
+
+__device__ __forceinline__ void dom_site(const Geom &g, const DomainGeom &dg, int dom, int l, float kappa,
+                                         DomSite &s)
+{
+    s.act = l < dg.nloc;
+    const int ll = s.act ? l : 0;
+    int k[4], lc[4], gc[4];
+    {
+        int r = dom;
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) { k[mu] = r % dg.nb[mu]; r /= dg.nb[mu]; }
+        r = ll;
+#pragma unroll
+        for (int mu = 0; mu < 4; mu++) { lc[mu] = r % dg.e[mu]; r /= dg.e[mu]; }
+    }
+    s.x = 0;
+    s.bulk = s.act;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        int v = (k[mu] * dg.b[mu] - dg.sh[mu] + lc[mu]) % g.L[mu];
+        if (v < 0) v += g.L[mu];
+        gc[mu] = v;
+        s.x += (long long)v * g.stride[mu];
+        if (lc[mu] < dg.sh[mu] || lc[mu] >= dg.sh[mu] + dg.b[mu]) s.bulk = false;
+    }
+    int lstride = 1;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        const int e = dg.e[mu];
+        const bool whole = dg.b[mu] == g.L[mu];
+        if (whole) {
+            s.nf[mu] = lc[mu] == e - 1 ? ll - (e - 1) * lstride : ll + lstride;
+            s.nb[mu] = lc[mu] == 0 ? ll + (e - 1) * lstride : ll - lstride;
+        } else {
+            s.nf[mu] = lc[mu] + 1 < e ? ll + lstride : -1;
+            s.nb[mu] = lc[mu] > 0 ? ll - lstride : -1;
+        }
+        s.cf[mu] = (gc[mu] == g.L[mu] - 1 && g.bc[mu] < 0) ? kappa : -kappa;
+        s.cb[mu] = (gc[mu] == 0 && g.bc[mu] < 0) ? kappa : -kappa;
+        s.xb[mu] = bwd_site(g, s.x, gc, mu);
+        lstride *= e;
+    }
+}
+
+// Local spinor from a planar float2 [12][stride] array (shared or global).
+__device__ __forceinline__ void ld_local(const float2 *base, int stride, int l, C<float> (&s)[12])
+{
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        float2 v = base[k * stride + l];
+        s[k] = {v.x, v.y};
+    }
+}
+
+__device__ __forceinline__ void st_local(float2 *base, int stride, int l, const C<float> (&s)[12])
+{
+#pragma unroll
+    for (int k = 0; k < 12; k++) base[k * stride + l] = make_float2(s[k].r, s[k].i);
+}
+
+template <int P, int MU>
+__device__ __forceinline__ void dom_hops(const RasArgs &a, const DomSite &ds, const float2 *rho, int stride,
+                                         C<float> (&q)[12])
+{
+    const long long V = a.g.V;
+    if (ds.nf[MU] >= 0) {
+        C<float> s[12], U[9];
+        ld_local(rho, stride, ds.nf[MU], s);
+        load_link<P>(a.U, V, MU, ds.x, U);
+        hop<MU, true>(q, s, U, ds.cf[MU]);
+    }
+    if (ds.nb[MU] >= 0) {
+        C<float> s[12], U[9];
+        ld_local(rho, stride, ds.nb[MU], s);
+        load_link<P>(a.U, V, MU, ds.xb[MU], U);
+        hop<MU, false>(q, s, U, ds.cb[MU]);
+    }
+}
+
+// q = D_{Omega'} rho at one local site.
+template <int P>
+__device__ __forceinline__ void dom_apply(const RasArgs &a, const DomSite &ds, const C<float> (&own)[12],
+                                          const float2 *rho, int stride, C<float> (&q)[12])
+{
+    float av[72];
+    load_clover<P>(a.A, a.g.V, ds.x, av);
+    clover_apply(av, own, q);
+    dom_hops<P, 0>(a, ds, rho, stride, q);
+    dom_hops<P, 1>(a, ds, rho, stride, q);
+    dom_hops<P, 2>(a, ds, rho, stride, q);
+    dom_hops<P, 3>(a, ds, rho, stride, q);
+}
+
+template <int P>
+__device__ __forceinline__ void write_outputs(const RasArgs &a, long long x, const C<float> (&v)[12])
+{
+    typedef typename RealOf<P>::T T;
+    const long long V = a.g.V;
+    if (a.vout.d) store_spinor<P>(a.vout, V, x, v);
+    if (a.accumulate) {
+        C<T> o[12];
+        load_spinor<P>(a.acc, V, x, o);
+#pragma unroll
+        for (int k = 0; k < 12; k++) o[k] = cadd(o[k], C<T>{(T)v[k].r, (T)v[k].i});
+        store_spinor<P>(a.acc, V, x, o);
+    } else {
+        store_spinor<P>(a.acc, V, x, v);
+    }
+}
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT) ras_smem_kernel(const RasArgs a)
+{
+    if (a.sc && a.sc->status != S_RUN) return;
+    extern __shared__ float2 srho[];  // [12][NT]
+    __shared__ double red_sm[3 * 32 + 3];
+    const int l = threadIdx.x;
+    DomSite ds;
+    dom_site(a.g, a.dg, blockIdx.x, l, a.kappa, ds);
+
+    C<float> rho[12], v[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) { rho[k] = {0.f, 0.f}; v[k] = {0.f, 0.f}; }
+    if (ds.act) load_spinor<P>(a.in, a.g.V, ds.x, rho);   // projection P_{Omega'}
+    st_local(srho, NT, l, rho);
+
+    for (int it = 0; it < a.n_iter; it++) {
+        __syncthreads();
+        C<float> q[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) q[k] = {0.f, 0.f};
+        if (ds.act) dom_apply<P>(a, ds, rho, srho, NT, q);
+        float qr = 0.f, qi = 0.f, qq = 0.f;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            C<float> t = cmulc(q[k], rho[k]);
+            qr += t.r;
+            qi += t.i;
+            qq += q[k].r * q[k].r + q[k].i * q[k].i;
+        }
+        double red[3] = {qr, qi, qq};
+        block_allsum<3>(red, red_sm);
+        if (red[2] > 0.0) {
+            const C<float> al = {(float)(red[0] / red[2]), (float)(red[1] / red[2])};
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                v[k] = cadd(v[k], cmul(al, rho[k]));
+                rho[k] = csub(rho[k], cmul(al, q[k]));
+            }
+        }
+        // every thread is past the barriers of block_allsum, so all reads of
+        // srho for this iteration are done
+        st_local(srho, NT, l, rho);
+    }
+    if (ds.bulk) write_outputs<P>(a, ds.x, v);  // restriction R_{Omega}
+}
+
+constexpr int RAS_GMEM_NT = 256;
+
+template <int P>
+__global__ void __launch_bounds__(RAS_GMEM_NT) ras_gmem_kernel(const RasArgs a)
+{
+    if (a.sc && a.sc->status != S_RUN) return;
+    __shared__ double red_sm[3 * 32 + 3];
+    const int n = a.dg.nloc;
+    float2 *rho = a.scratch + (size_t)blockIdx.x * 36 * n;
+    float2 *q = rho + 12 * (size_t)n;
+    float2 *vv = q + 12 * (size_t)n;
+    for (int dom = blockIdx.x; dom < a.dg.ndom; dom += gridDim.x) {
+        for (int l = threadIdx.x; l < n; l += RAS_GMEM_NT) {
+            DomSite ds;
+            dom_site(a.g, a.dg, dom, l, a.kappa, ds);
+            C<float> r[12], z[12];
+            load_spinor<P>(a.in, a.g.V, ds.x, r);
+#pragma unroll
+            for (int k = 0; k < 12; k++) z[k] = {0.f, 0.f};
+            st_local(rho, n, l, r);
+            st_local(vv, n, l, z);
+        }
+        for (int it = 0; it < a.n_iter; it++) {
+            __syncthreads();
+            double red[3] = {0.0, 0.0, 0.0};
+            for (int l = threadIdx.x; l < n; l += RAS_GMEM_NT) {
+                DomSite ds;
+                dom_site(a.g, a.dg, dom, l, a.kappa, ds);
+                C<float> own[12], qq[12];
+                ld_local(rho, n, l, own);
+                dom_apply<P>(a, ds, own, rho, n, qq);
+                st_local(q, n, l, qq);
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 12; k++) {
+                    C<float> t = cmulc(qq[k], own[k]);
+                    s0 += t.r;
+                    s1 += t.i;
+                    s2 += qq[k].r * qq[k].r + qq[k].i * qq[k].i;
+                }
+                red[0] += s0;
+                red[1] += s1;
+                red[2] += s2;
+            }
+            block_allsum<3>(red, red_sm);
+            if (red[2] > 0.0) {
+                const C<float> al = {(float)(red[0] / red[2]), (float)(red[1] / red[2])};
+                for (int l = threadIdx.x; l < n; l += RAS_GMEM_NT) {
+#pragma unroll
+                    for (int k = 0; k < 12; k++) {
+                        float2 r2 = rho[k * n + l], q2 = q[k * n + l], v2 = vv[k * n + l];
+                        C<float> r = {r2.x, r2.y}, qc = {q2.x, q2.y}, vc = {v2.x, v2.y};
+                        vc = cadd(vc, cmul(al, r));
+                        r = csub(r, cmul(al, qc));
+                        rho[k * n + l] = make_float2(r.r, r.i);
+                        vv[k * n + l] = make_float2(vc.r, vc.i);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        for (int l = threadIdx.x; l < n; l += RAS_GMEM_NT) {
+            DomSite ds;
+            dom_site(a.g, a.dg, dom, l, a.kappa, ds);
+            if (ds.bulk) {
+                C<float> v[12];
+                ld_local(vv, n, l, v);
+                write_outputs<P>(a, ds.x, v);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int P, int NT>
+static cudaError_t launch_smem(const RasArgs &a, cudaStream_t st)
+{
+    const size_t smem = (size_t)12 * NT * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(ras_smem_kernel<P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    ras_smem_kernel<P, NT><<<a.dg.ndom, NT, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int P>
+static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
+{
+    const int n = a.dg.nloc;
+    if (n <= 64) return launch_smem<P, 64>(a, st);
+    if (n <= 128) return launch_smem<P, 128>(a, st);
+    if (n <= 256) return launch_smem<P, 256>(a, st);
+    if (n <= RAS_SMEM_MAX_SITES) return launch_smem<P, 512>(a, st);
+    if (!a.scratch || a.slots < 1) return cudaErrorInvalidValue;
+    const int grid = a.slots < a.dg.ndom ? a.slots : a.dg.ndom;
+    ras_gmem_kernel<P><<<grid, RAS_GMEM_NT, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ras_block(int prec, const RasArgs &a, cudaStream_t st)
+{
+    if (a.dg.ndom <= 0) return cudaSuccess;
+    switch (prec) {
+    case P64: return launch_p<P64>(a, st);
+    case P32: return launch_p<P32>(a, st);
+    case P16: return launch_p<P16>(a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+int ras_default_slots() { return 2 * 152; }
+
+size_t ras_scratch_bytes(const DomainGeom &dg, int slots)
+{
+    if (dg.nloc <= RAS_SMEM_MAX_SITES) return 0;
+    const int s = slots < dg.ndom ? slots : dg.ndom;
+    return (size_t)s * 36 * (size_t)dg.nloc * sizeof(float2);
+}
+
+bool domain_geom(const Geom &g, const int block[4], int s, DomainGeom *dg, std::string *why)
+{
+    if (s < 0) {
+        if (why) *why = "overlap must be >= 0";
+        return false;
+    }
+    dg->ndom = 1;
+    long long nloc = 1;
+    for (int mu = 0; mu < 4; mu++) {
+        const int b = block[mu], L = g.L[mu];
+        if (b <= 0 || L % b != 0) {
+            if (why) *why = "block[" + std::to_string(mu) + "] = " + std::to_string(b) + " does not divide L = " +
+                            std::to_string(L);
+            return false;
+        }
+        dg->b[mu] = b;
+        if (b == L) {
+            dg->e[mu] = L;
+            dg->sh[mu] = 0;
+        } else {
+            if (b + 2 * s > L) {
+                if (why) *why = "block + 2*overlap exceeds the lattice in direction " + std::to_string(mu);
+                return false;
+            }
+            dg->e[mu] = b + 2 * s;
+            dg->sh[mu] = s;
+        }
+        dg->nb[mu] = L / b;
+        dg->ndom *= dg->nb[mu];
+        nloc *= dg->e[mu];
+    }
+    if (nloc > (1LL << 30)) {
+        if (why) *why = "extended domain too large";
+        return false;
+    }
+    dg->nloc = (int)nloc;
+    return true;
+}
+
+}  // namespace qdd

@@ -1,0 +1,78 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/qdd.h declares; host-side argument checks answer without a GPU."""
+
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "qdd.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qdd_[a-z_0-9]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1011_3318_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("qdd_create_lattice", "qdd_load_gauge", "qdd_dslash", "qdd_ras_apply", "qdd_solve"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (qdd_[a-z_0-9]+)", out))
+    missing = [n for n in declared_functions() if n not in exported]
+    assert not missing, missing
+    lib = ctypes.CDLL(libpath)
+    for n in declared_functions():
+        getattr(lib, n)
+
+
+def test_binding_lists_the_abi(libpath):
+    from paper_1011_3318_gb300 import qdd
+    assert sorted(qdd.ABI) == declared_functions()
+
+
+def test_host_side_calls_without_gpu(libpath):
+    from paper_1011_3318_gb300 import qdd
+    assert "sm_103a" in qdd.version()
+    p = qdd.default_params()
+    assert list(p.block) == [4, 4, 4, 4] and p.n_ras == 3 and p.n_dominv == 4 and p.inner_tol == 1e-3
+    lib = qdd.lib()
+    h = ctypes.c_void_p()
+    bad_dims = (ctypes.c_int * 4)(8, 0, 8, 8)
+    bc = (ctypes.c_int * 4)(1, 1, 1, -1)
+    assert lib.qdd_create_lattice(ctypes.byref(h), bad_dims, bc, 1, None) == qdd.QDD_ERR_ARG
+    assert "extents" in qdd.last_error()
+    dims = (ctypes.c_int * 4)(8, 8, 8, 8)
+    bad_bc = (ctypes.c_int * 4)(1, 1, 1, 0)
+    assert lib.qdd_create_lattice(ctypes.byref(h), dims, bad_bc, 1, None) == qdd.QDD_ERR_ARG
+    assert lib.qdd_create_lattice(ctypes.byref(h), dims, bc, 2, None) == qdd.QDD_ERR_ARG
+    assert lib.qdd_destroy_lattice(None) == qdd.QDD_OK
+
+
+def test_oracle_and_library_share_no_code():
+    """The oracle and the CUDA path are independent: no file of one includes,
+    imports or links the other."""
+    pkg = os.path.join(ROOT, "paper_1011_3318_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "oracle" not in re.sub(r"#.*|//.*", "", text).lower() or f.endswith(".md"), f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".py", ".c")):
+            text = open(os.path.join(ROOT, "oracle", f)).read()
+            assert "paper_1011_3318_gb300" not in text and "qdd.h" not in text
