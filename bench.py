@@ -1,0 +1,422 @@
+#!/usr/bin/env python
+"""Benchmark: time to solve the 32^4 Wilson-clover quark equation D phi = eta
+to |eta - D phi| / |eta| <= 1e-10 on one GB300.
+
+Workload (the paper's lattice size, Sec. 5, with synthetic seeded inputs in
+place of the authors' configuration): 32^4 sites, antiperiodic time, random
+SU(3) links U = exp(i 0.3 H) (gauge seed 1), kappa = 0.125, c_sw = 1, complex
+Gaussian source (seed 2).  One step = one whole pass of the hot path: gauge
+import and clover build, then the mixed-precision nested solve (FP64 defect
+correction around the FP16-storage / FP32-arithmetic inner BiCGStab, right-
+preconditioned by RAS).  The plain FP64 BiCGStab on the same GPU is timed
+beside it (the comparison the metric names), and the CPU oracle on a bounded
+sample of the same workload.
+
+Prints one JSON line on stdout (rank 0).  Usage:
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank solves its own replica of the workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "32^4 solve time to 1e-10 FP64 residual (RAS FP16/32 vs plain FP64); dslash GB/s/HBM"
+DIMS = (32, 32, 32, 32)
+BC = (1, 1, 1, -1)
+EPS, KAPPA, CSW, GSEED, SSEED, TOL = 0.3, 0.125, 1.0, 1, 2, 1e-10
+WORKLOAD = "32^4 lattice, eps=0.3 links (seed 1), kappa=0.125, c_sw=1.0, Gaussian source (seed 2), tol 1e-10"
+BYTES_PER_SITE = {"f64": 1536, "f32": 672, "f16": 348}   # compulsory D traffic: spinor in/out, links, clover
+FLOPS_PER_SITE_D = 1872                                    # spin-projected hop 1320 + clover 504 + combine 48
+NOMINAL = {"hbm_gbs": 7900.0, "sms": 152, "fp32_lanes": 128, "sm_max_mhz": 2070.0, "fp64_tflops": 1.25}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid):
+        self.uuid = uuid
+        self.proc = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ helpers
+def kernel_source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1011_3318_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel_class):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel_class)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def oracle_counts():
+    d = json.load(open(os.path.join(ROOT, "oracle", "counts.json")))
+    return d["32^4 eps=0.3 kappa=0.125"]["plain_bicgstab"]
+
+
+def cpu_baseline(U, eta, budget_s=15.0):
+    """The oracle (plain FP64 C, OpenMP on all host cores) on a bounded sample
+    of the workload: its clover build plus k plain-BiCGStab iterations at 32^4,
+    scaled to the iteration count of its own full solve."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    op = oracle.Op(DIMS, BC, U, KAPPA, CSW)
+    t_clover = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    op.bicgstab(eta, 1e-30, maxit=1)
+    t1 = time.perf_counter() - t0
+    k = int(max(2, min(20, budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    op.bicgstab(eta, 1e-30, maxit=k)
+    t_it = (time.perf_counter() - t0) / k
+    t0 = time.perf_counter()
+    op.dslash(eta)
+    t_d = time.perf_counter() - t0
+    n_it = oracle_counts()["inner_iters"]
+    value = t_clover + n_it * t_it + t_d
+    sample = (f"oracle clover build + {k} plain-BiCGStab iterations at 32^4 ({t_it:.2f} s each) + one D, "
+              f"scaled to the {n_it} iterations of the oracle's own full solve (oracle/counts.json)")
+    return {"value": round(value, 3), "unit": "s", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": sample}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    import synth
+    log("reference arm: the FP64 CPU oracle on this box's host cores")
+    U = synth.gauge_field(DIMS, EPS, GSEED)
+    eta = synth.gaussian_source(DIMS, SSEED)
+    import oracle
+    oracle.build()
+    op = oracle.Op(DIMS, BC, U, KAPPA, CSW)
+    n_it = oracle_counts()["inner_iters"]
+    k = 2
+    vals = []
+    for step in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        op.bicgstab(eta, 1e-30, maxit=k)
+        v = (time.perf_counter() - t0) / k * n_it
+        if step >= args.warmup:
+            vals.append(v)
+    value = sum(vals) / len(vals)
+    sample = f"{k} plain-BiCGStab iterations of the oracle at 32^4 per step, scaled to its {n_it}-iteration solve"
+    cb = {"value": round(value, 3), "unit": "s", "cores": oracle.get_threads(), "kind": "oracle", "sample": sample}
+    print(json.dumps({"impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "s",
+                      "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": round(value * 1e3, 1), "higher_is_better": False, "scaling": "weak",
+                      "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": WORKLOAD, "method": "plain FP64 BiCGStab (oracle)"},
+                      "cpu_baseline": cb, "e2e": {"value": round(value, 3), "unit": "s", "h2d_bytes_per_step": 0,
+                                                  "d2h_bytes_per_step": 0}}), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def time_steps(torch, stream, fn, steps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    stream.synchronize()
+    e0.record(stream)
+    infos = [fn() for _ in range(steps)]
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps, infos
+
+
+def dslash_roofline(torch, qdd, lat, stream, deta, prec, pk, reps=50):
+    a = qdd.field_create(lat, prec)
+    b = qdd.field_create(lat, prec)
+    qdd.field_import(a, deta)
+    for _ in range(3):
+        qdd.dslash_field(lat, b, a, KAPPA, CSW)
+    ms, _ = time_steps(torch, stream, lambda: qdd.dslash_field(lat, b, a, KAPPA, CSW), reps)
+    V = lat.V
+    gbs = BYTES_PER_SITE[prec] * V / (ms * 1e-3) / 1e9
+    qdd.field_destroy(a)
+    qdd.field_destroy(b)
+    return {"us_per_launch": round(ms * 1e3, 1), "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / pk, 3),
+            "D_per_s": round(1e3 / ms, 1), "bytes_per_site": BYTES_PER_SITE[prec]}
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1011_3318_gb300 import qdd
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    pk, pk_kind = peaks()
+    hbm = float(pk["hbm_gbs"])
+
+    log(f"rank {rank}: generating the 32^4 workload")
+    U = synth.gauge_field(DIMS, EPS, GSEED)
+    eta = synth.gaussian_source(DIMS, SSEED)
+    V = int(np.prod(DIMS))
+    stream = torch.cuda.Stream()
+    lat = qdd.create_lattice(DIMS, BC, stream=stream)
+    dU = torch.from_numpy(U).cuda()
+    deta = torch.from_numpy(eta).cuda()
+    dphi = torch.empty_like(deta)
+    params = qdd.default_params(inner_prec=args.prec, use_ras=1, block=args.block, overlap=args.overlap,
+                                n_dominv=args.n_dominv, n_ras=args.n_ras, inner_tol=args.inner_tol)
+    plain = qdd.default_params(inner_prec="f64", use_ras=0)
+
+    def step():
+        qdd.load_gauge(lat, dU)           # gauge import + invalidates the clover: rebuilt inside the solve
+        return qdd.solve(lat, dphi, deta, KAPPA, CSW, TOL, params)
+
+    for _ in range(args.warmup):
+        step()
+    uuid = None
+    try:
+        uuid = str(torch.cuda.get_device_properties(local).uuid)
+        uuid = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    qdd.set_profiling(lat, True)
+    qdd.profile_read(lat, reset=True)
+    n0 = qdd.kernel_launches()
+    sampler.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ms, infos = time_steps(torch, stream, step, args.steps)
+    torch.cuda.synchronize()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(t.item())
+    launches = qdd.kernel_launches() - n0
+    clocks = sampler.stop()
+    prof = qdd.profile_read(lat, reset=True)
+    qdd.set_profiling(lat, False)
+    ok = all(i["status"] == 0 and i["true_rel_residual"] <= TOL for i in infos)
+    info = infos[-1]
+
+    # plain FP64 BiCGStab on the same GPU (the comparison of the metric)
+    qdd.solve(lat, dphi, deta, KAPPA, CSW, TOL, plain)
+    ms_plain, pinfos = time_steps(torch, stream, lambda: qdd.solve(lat, dphi, deta, KAPPA, CSW, TOL, plain),
+                                  max(1, min(3, args.steps)))
+    # mixed precision without RAS (context)
+    nor = qdd.default_params(inner_prec=args.prec, use_ras=0, inner_tol=args.inner_tol)
+    qdd.solve(lat, dphi, deta, KAPPA, CSW, TOL, nor)
+    ms_nor, ninfos = time_steps(torch, stream, lambda: qdd.solve(lat, dphi, deta, KAPPA, CSW, TOL, nor),
+                                max(1, min(3, args.steps)))
+
+    # the dslash kernel alone, same launch configuration as inside the solve
+    dsl = {p: dslash_roofline(torch, qdd, lat, stream, deta, p, hbm) for p in ("f16", "f32", "f64")}
+
+    # roofline of the dominant kernel class inside the timed solves
+    total = sum(v[0] for v in prof.values())
+    dom = max(prof, key=lambda k: prof[k][0])
+    sm_mhz = clocks.get("sm_mhz") or NOMINAL["sm_max_mhz"]
+    fp32_alu_peak = NOMINAL["sms"] * NOMINAL["fp32_lanes"] * 2 * NOMINAL["sm_max_mhz"] * 1e6 / 1e12
+    if dom == "ras":
+        ms_l = prof["ras"][0] / max(1, prof["ras"][1])
+        nloc = 1
+        for b, L in zip(args.block, DIMS):
+            nloc *= b if b == L else b + 2 * args.overlap
+        ndom = 1
+        for b, L in zip(args.block, DIMS):
+            ndom *= L // b
+        flops = ndom * nloc * args.n_dominv * (FLOPS_PER_SITE_D + 96 + 48)
+        ach = flops / (ms_l * 1e-3) / 1e12
+        roof = {"kernel": "ras_smem_kernel (RAS sweep)", "bound": "alu", "achieved": round(ach, 2),
+                "peak": round(fp32_alu_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_alu_peak, 3),
+                "traffic": ncu_traffic("ras"), "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "us_per_launch": round(ms_l * 1e3, 1), "share": round(prof["ras"][0] / total, 3)}
+    else:
+        cls = dom if dom in ("dslash", "dslash_f64") else "dslash"
+        ms_l = prof[cls][0] / max(1, prof[cls][1])
+        prec = "f64" if cls == "dslash_f64" else args.prec
+        ach = BYTES_PER_SITE[prec] * V / (ms_l * 1e-3) / 1e9
+        roof = {"kernel": f"dslash_kernel ({prec})", "bound": "hbm", "achieved": round(ach, 1), "peak": hbm,
+                "unit": "GB/s", "frac": round(ach / hbm, 3), "traffic": ncu_traffic(cls),
+                "peak_kind": f"{pk_kind} (MEASURED_PEAKS.json hbm_gbs)", "us_per_launch": round(ms_l * 1e3, 1),
+                "share": round(prof[cls][0] / total, 3)}
+    # the inner-precision dslash inside the solves (fused epilogues included)
+    ms_d = prof["dslash"][0] / max(1, prof["dslash"][1])
+    ach_d = BYTES_PER_SITE[args.prec] * V / (ms_d * 1e-3) / 1e9
+    roof_dslash = {"kernel": f"dslash_kernel ({args.prec}, in the solve)", "bound": "hbm", "achieved": round(ach_d, 1),
+                   "peak": hbm, "unit": "GB/s", "frac": round(ach_d / hbm, 3), "traffic": ncu_traffic("dslash"),
+                   "us_per_launch": round(ms_d * 1e3, 1)}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    hU = torch.from_numpy(U).pin_memory()
+    heta = torch.from_numpy(eta).pin_memory()
+    hphi = torch.empty_like(heta).pin_memory()
+
+    def e2e_step():
+        qdd.load_gauge(lat, hU)
+        return qdd.solve(lat, hphi, heta, KAPPA, CSW, TOL, params)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_infos = [e2e_step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    e_ok = all(i["status"] == 0 for i in e_infos)
+
+    # the oracle's check of the last answer (FP64 true residual with the oracle's D)
+    oracle_res = None
+    cb = None
+    if rank == 0:
+        import oracle
+        oracle.build()
+        op = oracle.Op(DIMS, BC, U, KAPPA, CSW, store_clover=False)
+        oracle_res = op.true_residual(eta, hphi.numpy())
+        if world == 1 and not args.no_cpu_baseline:
+            cb = cpu_baseline(U, eta)
+
+    if rank == 0:
+        nrep = world
+        value = ms / 1e3 / nrep
+        rec = {
+            "metric": METRIC, "value": round(value, 5), "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": list(DIMS),
+                       "method": f"FP64 defect correction + {args.prec}-storage/FP32 inner BiCGStab, RAS "
+                                 f"block {'x'.join(map(str, args.block))} s={args.overlap} "
+                                 f"N_dominv={args.n_dominv} NRAS={args.n_ras}, inner tol {args.inner_tol}",
+                       "l2": "inputs larger than L2 (links 604 MB, source 201 MB FP64 per replica)",
+                       "parallelism": f"{world} independent replica(s)"},
+            "solve": {k: info[k] for k in ("outer_iters", "inner_iters", "dv_count", "ras_sweeps",
+                                            "true_rel_residual")},
+            "all_timed_solves_converged": ok,
+            "oracle_true_rel_residual": oracle_res,
+            "plain_fp64": {"s": round(ms_plain / 1e3, 4), "inner_iters": pinfos[-1]["inner_iters"],
+                           "true_rel_residual": pinfos[-1]["true_rel_residual"],
+                           "speedup_of_value": round(ms_plain / ms, 2)},
+            "mixed_no_ras": {"s": round(ms_nor / 1e3, 4), "inner_iters": ninfos[-1]["inner_iters"],
+                             "outer_iters": ninfos[-1]["outer_iters"]},
+            "kernel_time_ms_per_step": {k: round(v[0] / args.steps, 3) for k, v in prof.items()},
+            "kernel_launches_per_step": {k: v[1] / args.steps for k, v in prof.items()},
+            "roofline": roof, "roofline_dslash": roof_dslash, "dslash_alone": dsl,
+            "e2e": {"value": round(e2e_s, 5), "unit": "s",
+                    "h2d_bytes_per_step": int(U.nbytes + eta.nbytes), "d2h_bytes_per_step": int(eta.nbytes),
+                    "converged": e_ok},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+            "cpu_baseline": cb,
+            "kernel_source_hash": kernel_source_hash(),
+        }
+        print(json.dumps(rec), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--prec", choices=("f16", "f32"), default="f16")
+    ap.add_argument("--block", type=lambda s: tuple(int(x) for x in s.split(",")), default=(4, 4, 4, 4))
+    ap.add_argument("--overlap", type=int, default=0)
+    ap.add_argument("--n-dominv", dest="n_dominv", type=int, default=4)
+    ap.add_argument("--n-ras", dest="n_ras", type=int, default=3)
+    ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=1e-3)
+    ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        return run_reference(args, rank)
+    return run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -175,6 +175,41 @@ qdd_status qdd_field_export(const qdd_field *f, double *dst);
 qdd_status qdd_dslash_field(qdd_lattice *lat, qdd_field *out, const qdd_field *in, double kappa,
                             double c_sw);
 
+/* -- measurement ------------------------------------------------------------ */
+
+/* Kernel classes of the per-class GPU timers. */
+enum {
+    QDD_K_DSLASH = 0,      /* D in FP32 / FP16 (inner solve, RAS residual updates) */
+    QDD_K_DSLASH_F64 = 1,  /* D in FP64 (plain solver, outer true residual) */
+    QDD_K_RAS = 2,         /* RAS sweeps (projection + domain solves + restriction) */
+    QDD_K_BLAS = 3,        /* Krylov vector kernels and reductions */
+    QDD_K_CONVERT = 4,     /* layout and precision conversions */
+    QDD_K_CLOVER = 5,      /* clover-term build and gauge conversion */
+    QDD_NKCLASS = 6
+};
+
+typedef struct {
+    double ms[QDD_NKCLASS];            /* summed GPU time of each class */
+    long long launches[QDD_NKCLASS];   /* timed launches of each class */
+} qdd_profile;
+
+/* Process-wide count of kernel launches made by this library. */
+unsigned long long qdd_kernel_launches(void);
+
+/* Turns per-class GPU timing on or off for this lattice: while on, every
+ * launch is bracketed by CUDA events on the lattice's stream (about a
+ * microsecond of overhead each). */
+qdd_status qdd_set_profiling(qdd_lattice *lat, int on);
+
+/* Synchronises the lattice's stream and returns the per-class totals since
+ * the last reset; reset != 0 clears them. */
+qdd_status qdd_profile_read(qdd_lattice *lat, qdd_profile *out, int reset);
+
+/* Measures the FMA throughput of the current device in TFLOP/s (2 flops per
+ * FMA): fp64 != 0 for FP64, else FP32.  Runs a few short kernels on the
+ * legacy default stream. */
+qdd_status qdd_measure_fma_peak(int fp64, double *tflops);
+
 #ifdef __cplusplus
 }
 #endif

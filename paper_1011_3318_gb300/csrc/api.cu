@@ -64,6 +64,7 @@ qdd_status ensure_clover(qdd_lattice *lat, double kappa, double csw)
         return QDD_ERR_STATE;
     }
     if (lat->clover_valid && lat->kappa_c == kappa && lat->csw_c == csw) return QDD_OK;
+    ProfScope ps(lat, QDD_K_CLOVER);
     cudaError_t e = launch_clover_build(lat->g, lat->U64, kappa, csw, lat->A64, lat->A32, lat->A16, lat->A16n,
                                         lat->stream);
     if (e != cudaSuccess) return cuda_fail(e, "clover build");
@@ -261,6 +262,7 @@ qdd_status qdd_destroy_lattice(qdd_lattice *lat)
     work_free(lat->work);
     for (int p = 0; p < 3; p++)
         for (int k = 0; k < 2; k++) field_free(lat->io_d[p][k], lat->io_n[p][k]);
+    delete lat->prof;
     delete lat;
     return QDD_OK;
 }
@@ -287,7 +289,10 @@ qdd_status qdd_load_gauge(qdd_lattice *lat, const double *U)
         src = tmp;
     }
     e = cudaMemsetAsync(lat->maxdev, 0, sizeof(unsigned long long), lat->stream);
-    if (e == cudaSuccess) e = launch_gauge_convert(lat->g, src, lat->U64, lat->U32, lat->U16, lat->maxdev, lat->stream);
+    if (e == cudaSuccess) {
+        ProfScope ps(lat, QDD_K_CLOVER);
+        e = launch_gauge_convert(lat->g, src, lat->U64, lat->U32, lat->U16, lat->maxdev, lat->stream);
+    }
     unsigned long long bits = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, lat->maxdev, sizeof(bits), cudaMemcpyDeviceToHost, lat->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);

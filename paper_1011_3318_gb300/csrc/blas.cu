@@ -200,6 +200,7 @@ static cudaError_t launch_blas_p(int op, const BlasArgs &a, cudaStream_t st)
     case B_RESTART: blas_kernel<P, B_RESTART><<<nb, BLAS_NT, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -273,6 +274,7 @@ cudaError_t launch_convert_scaled(long long V, int prec, SpinorView dst, SpinorV
     if (prec == P64) convert_scaled_kernel<P64><<<nb, BLAS_NT, 0, st>>>(V, dst, src64, sc, slot);
     else if (prec == P32) convert_scaled_kernel<P32><<<nb, BLAS_NT, 0, st>>>(V, dst, src64, sc, slot);
     else convert_scaled_kernel<P16><<<nb, BLAS_NT, 0, st>>>(V, dst, src64, sc, slot);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -283,6 +285,7 @@ cudaError_t launch_accum_scaled(long long V, int prec, SpinorView phi64, SpinorV
     if (prec == P64) accum_scaled_kernel<P64><<<nb, BLAS_NT, 0, st>>>(V, phi64, x, sc, slot);
     else if (prec == P32) accum_scaled_kernel<P32><<<nb, BLAS_NT, 0, st>>>(V, phi64, x, sc, slot);
     else accum_scaled_kernel<P16><<<nb, BLAS_NT, 0, st>>>(V, phi64, x, sc, slot);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -292,6 +295,7 @@ static cudaError_t convert_from(long long V, SpinorView dst, int ps, SpinorView 
     if (ps == P64) convert_kernel<PD, P64><<<nb, BLAS_NT, 0, st>>>(V, dst, src);
     else if (ps == P32) convert_kernel<PD, P32><<<nb, BLAS_NT, 0, st>>>(V, dst, src);
     else convert_kernel<PD, P16><<<nb, BLAS_NT, 0, st>>>(V, dst, src);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -136,6 +136,7 @@ static cudaError_t launch_one(const DslashArgs &a, cudaStream_t st)
         if (nb > a.rs.max_blocks) return cudaErrorInvalidConfiguration;
     }
     dslash_kernel<P, EPI, NT><<<(unsigned)nb, NT, 0, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -55,6 +55,7 @@ cudaError_t launch_import_spinor(const Geom &g, int prec, SpinorView dst, const 
     if (prec == P64) import_spinor_kernel<P64><<<nb, 256, 0, st>>>(g, dst, src);
     else if (prec == P32) import_spinor_kernel<P32><<<nb, 256, 0, st>>>(g, dst, src);
     else import_spinor_kernel<P16><<<nb, 256, 0, st>>>(g, dst, src);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -64,6 +65,7 @@ cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorVie
     if (prec == P64) export_spinor_kernel<P64><<<nb, 256, 0, st>>>(g, dst, src);
     else if (prec == P32) export_spinor_kernel<P32><<<nb, 256, 0, st>>>(g, dst, src);
     else export_spinor_kernel<P16><<<nb, 256, 0, st>>>(g, dst, src);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -125,6 +127,7 @@ cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void
     const long long n = g.V * 4;
     const unsigned nb = (unsigned)((n + 255) / 256);
     gauge_convert_kernel<<<nb, 256, 0, st>>>(g, U, (double2 *)U64, (float4 *)U32, (uint2 *)U16, maxdev);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -341,6 +344,7 @@ cudaError_t launch_clover_build(const Geom &g, const void *U64, double kappa, do
     const unsigned nb = (unsigned)((g.V + 127) / 128);
     clover_build_kernel<<<nb, 128, 0, st>>>(g, (const double2 *)U64, kappa, csw, (double2 *)A64, (float4 *)A32,
                                             (uint4 *)A16, A16n);
+    note_launch();
     return cudaGetLastError();
 }
 

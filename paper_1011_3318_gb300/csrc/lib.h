@@ -4,10 +4,31 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "qdd_internal.h"
 
 namespace qdd {
+
+// Counts kernel launches of this library (qdd_kernel_launches()).
+void note_launch(unsigned n = 1);
+
+// Per-kernel-class GPU time, measured with CUDA events on the lattice stream
+// around every launch while profiling is on (qdd_set_profiling).
+struct Profiler {
+    struct Pair {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    std::vector<Pair> pending;
+    double ms[QDD_NKCLASS] = {};
+    long long n[QDD_NKCLASS] = {};
+    ~Profiler();
+    cudaEvent_t get();
+    void drain();  // after the stream has passed every pending event
+};
 
 // Dslash epilogues.
 enum Epi {
@@ -142,10 +163,20 @@ struct qdd_lattice {
     void *io_d[3][2];
     float *io_n[3][2];
     qdd_work *work;
+    qdd::Profiler *prof;
 };
 
 // Helpers shared by api.cu and solver.cu.
 namespace qdd {
+// Records events around the launches in its lifetime when profiling is on.
+struct ProfScope {
+    Profiler *prof;
+    int cls;
+    cudaStream_t st;
+    cudaEvent_t a;
+    ProfScope(qdd_lattice *lat, int cls);
+    ~ProfScope();
+};
 void set_error(const std::string &msg);
 qdd_status cuda_fail(cudaError_t e, const char *what);
 qdd_status ensure_clover(qdd_lattice *lat, double kappa, double csw);

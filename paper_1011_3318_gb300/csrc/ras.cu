@@ -276,6 +276,7 @@ static cudaError_t launch_smem(const RasArgs &a, cudaStream_t st)
                                          (int)smem);
     if (e != cudaSuccess) return e;
     ras_smem_kernel<P, NT><<<a.dg.ndom, NT, smem, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 
@@ -290,6 +291,7 @@ static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
     if (!a.scratch || a.slots < 1) return cudaErrorInvalidValue;
     const int grid = a.slots < a.dg.ndom ? a.slots : a.dg.ndom;
     ras_gmem_kernel<P><<<grid, RAS_GMEM_NT, 0, st>>>(a);
+    note_launch();
     return cudaGetLastError();
 }
 

@@ -79,6 +79,7 @@ static qdd_status blas(qdd_lattice *lat, int prec, int op, std::initializer_list
     a.rs = lat->rs;
     a.aux_slot = aux_slot;
     a.tol2_rel = tol2;
+    ProfScope ps(lat, QDD_K_BLAS);
     cudaError_t e = launch_blas(prec, op, a, lat->stream);
     return e == cudaSuccess ? QDD_OK : cuda_fail(e, "blas kernel");
 }
@@ -87,6 +88,7 @@ static qdd_status read_scalars(qdd_lattice *lat)
 {
     cudaError_t e = cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, lat->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
+    if (e == cudaSuccess && lat->prof) lat->prof->drain();
     return e == cudaSuccess ? QDD_OK : cuda_fail(e, "reading solver scalars");
 }
 
@@ -105,6 +107,7 @@ qdd_status run_dslash(qdd_lattice *lat, int prec, int epi, SpinorView out, Spino
     a.rs = lat->rs;
     a.sc = lat->sc;
     a.aux_slot = aux_slot;
+    ProfScope ps(lat, prec == P64 ? QDD_K_DSLASH_F64 : QDD_K_DSLASH);
     cudaError_t e = launch_dslash(prec, epi, a, lat->stream);
     return e == cudaSuccess ? QDD_OK : cuda_fail(e, "dslash kernel");
 }
@@ -152,7 +155,11 @@ qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params 
         ra.vout = last ? SpinorView{nullptr, nullptr} : v;
         ra.acc = out;
         ra.accumulate = j > 0;
-        cudaError_t e = launch_ras_block(prec, ra, lat->stream);
+        cudaError_t e;
+        {
+            ProfScope ps(lat, QDD_K_RAS);
+            e = launch_ras_block(prec, ra, lat->stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "RAS block kernel");
         if (!last) {
             st = run_dslash(lat, prec, EPI_XMY, rho, v, ra.in, kappa, 0);
@@ -243,7 +250,11 @@ qdd_status solve_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, 
 
     const Geom &g = lat->g;
     SpinorView eta = outer(lat, 0), phi = outer(lat, 1), r = outer(lat, 2);
-    cudaError_t e = launch_import_spinor(g, P64, eta, eta_dev, lat->stream);
+    cudaError_t e;
+    {
+        ProfScope ps(lat, QDD_K_CONVERT);
+        e = launch_import_spinor(g, P64, eta, eta_dev, lat->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "import");
     if ((st = blas(lat, P64, B_NORM, {eta}, 0)) != QDD_OK) return st;   // |eta|^2 -> aux[0]
     if ((st = blas(lat, P64, B_COPY, {r, eta})) != QDD_OK) return st;
@@ -271,7 +282,10 @@ qdd_status solve_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, 
         double tol_in = 0.5 * tol * std::sqrt(eta2 / rr);
         if (!plain && p->inner_tol > tol_in) tol_in = p->inner_tol;
         const auto ti = clk::now();
-        e = launch_convert_scaled(g.V, prec, inner(lat, prec, W_B), r, lat->sc, 1, lat->stream);
+        {
+            ProfScope ps(lat, QDD_K_CONVERT);
+            e = launch_convert_scaled(g.V, prec, inner(lat, prec, W_B), r, lat->sc, 1, lat->stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "convert");
         InnerResult ir;
         if ((st = inner_bicgstab(lat, prec, p, use_ras ? &dg : nullptr, kappa, tol_in, p->max_inner, &ir)) !=
@@ -284,7 +298,10 @@ qdd_status solve_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, 
         inf.outer_iters++;
         if (ir.status == S_NONFINITE) { result = QDD_ERR_NONFINITE; break; }
         // phi += |r| x ; r = eta - D phi ; |r|^2 -> aux[1]
-        e = launch_accum_scaled(g.V, prec, phi, inner(lat, prec, W_X), lat->sc, 1, lat->stream);
+        {
+            ProfScope ps(lat, QDD_K_CONVERT);
+            e = launch_accum_scaled(g.V, prec, phi, inner(lat, prec, W_X), lat->sc, 1, lat->stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "accumulate");
         if ((st = run_dslash(lat, P64, EPI_XMY_NORM, r, phi, eta, kappa, 1)) != QDD_OK) return st;
         if ((st = read_scalars(lat)) != QDD_OK) return st;
@@ -296,7 +313,10 @@ qdd_status solve_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, 
             break;
         }
     }
-    e = launch_export_spinor(g, P64, phi_dev, phi, lat->stream);
+    {
+        ProfScope ps(lat, QDD_K_CONVERT);
+        e = launch_export_spinor(g, P64, phi_dev, phi, lat->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(e, "export");
     e = cudaStreamSynchronize(lat->stream);
     if (e != cudaSuccess) return cuda_fail(e, "solve");

@@ -40,7 +40,11 @@ PREC = {"f64": QDD_F64, "f32": QDD_F32, "f16": QDD_F16, QDD_F64: QDD_F64, QDD_F3
 # Every function the header declares (checked by the tests against the library's exports).
 ABI = ("qdd_version", "qdd_last_error", "qdd_default_params", "qdd_create_lattice", "qdd_destroy_lattice",
        "qdd_load_gauge", "qdd_dslash", "qdd_ras_apply", "qdd_solve", "qdd_field_create", "qdd_field_destroy",
-       "qdd_field_import", "qdd_field_export", "qdd_dslash_field")
+       "qdd_field_import", "qdd_field_export", "qdd_dslash_field", "qdd_kernel_launches", "qdd_set_profiling",
+       "qdd_profile_read", "qdd_measure_fma_peak")
+
+# Kernel classes of the per-class GPU timers (qdd_profile).
+KCLASS = ("dslash", "dslash_f64", "ras", "blas", "convert", "clover")
 
 
 class QddError(RuntimeError):
@@ -54,6 +58,10 @@ class SolverParams(ctypes.Structure):
                 ("n_ras", ctypes.c_int), ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_inner", ctypes.c_int), ("max_outer", ctypes.c_int), ("use_ras", ctypes.c_int),
                 ("outer_mode", ctypes.c_int), ("autotune", ctypes.c_int)]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_longlong * 6)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -85,8 +93,12 @@ def _load():
     lib.qdd_field_import.argtypes = [P, P]
     lib.qdd_field_export.argtypes = [P, P]
     lib.qdd_dslash_field.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double]
+    lib.qdd_kernel_launches.restype = ctypes.c_ulonglong
+    lib.qdd_set_profiling.argtypes = [P, ctypes.c_int]
+    lib.qdd_profile_read.argtypes = [P, ctypes.POINTER(Profile), ctypes.c_int]
+    lib.qdd_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     for name in ABI:
-        if name not in ("qdd_version", "qdd_last_error", "qdd_default_params"):
+        if name not in ("qdd_version", "qdd_last_error", "qdd_default_params", "qdd_kernel_launches"):
             getattr(lib, name).restype = st
     return lib
 
@@ -252,3 +264,26 @@ def field_export(f: Field, dst) -> None:
 
 def dslash_field(lat: Lattice, out: Field, inp: Field, kappa: float, c_sw: float) -> None:
     _check(_lib.qdd_dslash_field(lat.handle, out.handle, inp.handle, float(kappa), float(c_sw)), "qdd_dslash_field")
+
+
+def kernel_launches() -> int:
+    """Process-wide number of kernel launches made by the library."""
+    return int(_lib.qdd_kernel_launches())
+
+
+def set_profiling(lat: Lattice, on: bool) -> None:
+    _check(_lib.qdd_set_profiling(lat.handle, int(bool(on))), "qdd_set_profiling")
+
+
+def profile_read(lat: Lattice, reset: bool = True) -> dict:
+    """{class: (ms, launches)} of GPU time per kernel class since the last reset."""
+    p = Profile()
+    _check(_lib.qdd_profile_read(lat.handle, ctypes.byref(p), int(bool(reset))), "qdd_profile_read")
+    return {k: (p.ms[i], p.launches[i]) for i, k in enumerate(KCLASS)}
+
+
+def measure_fma_peak(fp64: bool) -> float:
+    """FMA throughput of the current GPU in TFLOP/s (FP64 or FP32)."""
+    v = ctypes.c_double()
+    _check(_lib.qdd_measure_fma_peak(int(bool(fp64)), ctypes.byref(v)), "qdd_measure_fma_peak")
+    return v.value
