@@ -175,6 +175,27 @@ qdd_status qdd_field_export(const qdd_field *f, double *dst);
 qdd_status qdd_dslash_field(qdd_lattice *lat, qdd_field *out, const qdd_field *in, double kappa,
                             double c_sw);
 
+/* K_RAS of qdd_ras_apply on caller-owned fields, with no device allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot let the library call cudaMalloc when the preconditioner runs --
+ * code inside a CUDA stream capture, programs that own all device memory
+ * through their own pool, and loops where an allocation would stall the GPU.
+ * out = K_RAS in with params->block, overlap, n_dominv, n_ras; out, in, rho
+ * and v are four different fields of this lattice in one precision (QDD_F32
+ * or QDD_F16); rho and v are work vectors whose contents are overwritten.
+ * Every sweep runs the general domain kernel, whose scratch is a fixed
+ * 16 MiB device array inside the library (present on every GPU that loads
+ * it, until the process exits): an extended domain may have at most 58254
+ * sites (36 * 8 bytes each), and larger ones are rejected with QDD_ERR_ARG.
+ * The first call on a device looks up that array's device address
+ * (cudaGetSymbolAddress); make it before any stream capture begins.  All
+ * calls share the array, so calls whose kernels overlap on the GPU race and
+ * give wrong results.  Stream-ordered on the lattice's stream; needs a gauge
+ * field (QDD_ERR_STATE otherwise); builds the clover term for (kappa, c_sw)
+ * if it is not cached, which launches a kernel but allocates nothing. */
+qdd_status qdd_ras_field_noalloc(qdd_lattice *lat, qdd_field *out, const qdd_field *in, qdd_field *rho,
+                                 qdd_field *v, double kappa, double c_sw, const qdd_solver_params *params);
+
 /* -- measurement ------------------------------------------------------------ */
 
 /* Kernel classes of the per-class GPU timers. */

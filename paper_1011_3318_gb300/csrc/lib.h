@@ -119,6 +119,9 @@ struct RasArgs {
 constexpr int RAS_SMEM_MAX_SITES = 512;
 
 cudaError_t launch_ras_block(int prec, const RasArgs &a, cudaStream_t st);
+// The general (global-scratch) sweep kernel for any domain size, with the
+// scratch and slot count given in a (FP32 and FP16 only).
+cudaError_t launch_ras_block_gmem(int prec, const RasArgs &a, cudaStream_t st);
 size_t ras_scratch_bytes(const DomainGeom &dg, int slots);
 int ras_default_slots();
 

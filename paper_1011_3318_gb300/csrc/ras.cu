@@ -306,6 +306,26 @@ cudaError_t launch_ras_block(int prec, const RasArgs &a, cudaStream_t st)
     return cudaErrorInvalidValue;
 }
 
+template <int P>
+static cudaError_t launch_gmem_p(const RasArgs &a, cudaStream_t st)
+{
+    if (!a.scratch || a.slots < 1) return cudaErrorInvalidValue;
+    const int grid = a.slots < a.dg.ndom ? a.slots : a.dg.ndom;
+    ras_gmem_kernel<P><<<grid, RAS_GMEM_NT, 0, st>>>(a);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ras_block_gmem(int prec, const RasArgs &a, cudaStream_t st)
+{
+    if (a.dg.ndom <= 0) return cudaSuccess;
+    switch (prec) {
+    case P32: return launch_gmem_p<P32>(a, st);
+    case P16: return launch_gmem_p<P16>(a, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 int ras_default_slots() { return 2 * 152; }
 
 size_t ras_scratch_bytes(const DomainGeom &dg, int slots)

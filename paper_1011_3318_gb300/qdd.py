@@ -41,7 +41,7 @@ PREC = {"f64": QDD_F64, "f32": QDD_F32, "f16": QDD_F16, QDD_F64: QDD_F64, QDD_F3
 ABI = ("qdd_version", "qdd_last_error", "qdd_default_params", "qdd_create_lattice", "qdd_destroy_lattice",
        "qdd_load_gauge", "qdd_dslash", "qdd_ras_apply", "qdd_solve", "qdd_field_create", "qdd_field_destroy",
        "qdd_field_import", "qdd_field_export", "qdd_dslash_field", "qdd_kernel_launches", "qdd_set_profiling",
-       "qdd_profile_read", "qdd_measure_fma_peak")
+       "qdd_profile_read", "qdd_measure_fma_peak", "qdd_ras_field_noalloc")
 
 # Kernel classes of the per-class GPU timers (qdd_profile).
 KCLASS = ("dslash", "dslash_f64", "ras", "blas", "convert", "clover")
@@ -97,6 +97,8 @@ def _load():
     lib.qdd_set_profiling.argtypes = [P, ctypes.c_int]
     lib.qdd_profile_read.argtypes = [P, ctypes.POINTER(Profile), ctypes.c_int]
     lib.qdd_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.qdd_ras_field_noalloc.argtypes = [P, P, P, P, P, ctypes.c_double, ctypes.c_double,
+                                          ctypes.POINTER(SolverParams)]
     for name in ABI:
         if name not in ("qdd_version", "qdd_last_error", "qdd_default_params", "qdd_kernel_launches"):
             getattr(lib, name).restype = st
@@ -287,3 +289,11 @@ def measure_fma_peak(fp64: bool) -> float:
     v = ctypes.c_double()
     _check(_lib.qdd_measure_fma_peak(int(bool(fp64)), ctypes.byref(v)), "qdd_measure_fma_peak")
     return v.value
+
+
+def ras_field_noalloc(lat: Lattice, out: Field, inp: Field, rho: Field, v: Field, kappa: float, c_sw: float,
+                      params: SolverParams) -> None:
+    """out = K_RAS inp on internal fields without any device allocation (the
+    scratch is a fixed array inside the library; see include/qdd.h)."""
+    _check(_lib.qdd_ras_field_noalloc(lat.handle, out.handle, inp.handle, rho.handle, v.handle, float(kappa),
+                                      float(c_sw), ctypes.byref(params)), "qdd_ras_field_noalloc")
