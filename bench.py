@@ -396,6 +396,41 @@ def run_ours(args, rank, world):
     return 0
 
 
+def run_kernels(spec):
+    """Kernel microbenchmark for profilers: builds the 32^4 workload and runs
+    one kernel a few times -- dslash:<prec>, ras:<prec> (one RAS sweep of 4^4
+    blocks, N_dominv = 4) or clover (the clover build)."""
+    import torch
+
+    import synth
+    from paper_1011_3318_gb300 import qdd
+    kind, _, prec = spec.partition(":")
+    U = synth.gauge_field(DIMS, EPS, GSEED)
+    eta = synth.gaussian_source(DIMS, SSEED)
+    lat = qdd.create_lattice(DIMS, BC)
+    qdd.load_gauge(lat, torch.from_numpy(U).cuda())
+    deta = torch.from_numpy(eta).cuda()
+    out = torch.empty_like(deta)
+    if kind == "dslash":
+        a = qdd.field_create(lat, prec)
+        b = qdd.field_create(lat, prec)
+        qdd.field_import(a, deta)
+        for _ in range(3):
+            qdd.dslash_field(lat, b, a, KAPPA, CSW)
+    elif kind == "ras":
+        p = qdd.default_params(inner_prec=prec, n_ras=1, n_dominv=4)
+        for _ in range(3):
+            qdd.ras_apply(lat, out, deta, KAPPA, CSW, p)
+    elif kind == "clover":
+        for k in range(3):
+            qdd.dslash(lat, out, deta, KAPPA + 0.001 * k, CSW, "f32")
+    else:
+        raise SystemExit(f"unknown kernel {spec}")
+    torch.cuda.synchronize()
+    log(f"ran {spec}")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -409,7 +444,11 @@ def main():
     ap.add_argument("--n-ras", dest="n_ras", type=int, default=3)
     ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=1e-3)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    ap.add_argument("--kernels", default=None,
+                    help="profiler workload: dslash:f16|f32|f64, ras:f16|f32 or clover, three launches at 32^4")
     args = ap.parse_args()
+    if args.kernels:
+        return run_kernels(args.kernels)
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

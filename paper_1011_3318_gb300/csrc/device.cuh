@@ -98,6 +98,30 @@ __device__ __forceinline__ void load_spinor(const SpinorView &f, long long V, lo
     }
 }
 
+// As load_spinor, but FP16 values are left unscaled and the site norm is
+// returned (1 for FP32/FP64), so that callers fold it into a coefficient.
+template <int P, typename T>
+__device__ __forceinline__ T load_spinor_u(const SpinorView &f, long long V, long long x, C<T> (&s)[12])
+{
+    if constexpr (P == P16) {
+        const uint4 *p = (const uint4 *)f.d;
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            uint4 a = p[q * V + x];
+            unsigned w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                float2 f2 = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
+                s[4 * q + j] = {(T)f2.x, (T)f2.y};
+            }
+        }
+        return (T)f.n[x];
+    } else {
+        load_spinor<P>(f, V, x, s);
+        return (T)1;
+    }
+}
+
 template <int P, typename T>
 __device__ __forceinline__ void store_spinor(const SpinorView &f, long long V, long long x, const C<T> (&s)[12])
 {
@@ -259,6 +283,30 @@ __device__ __forceinline__ void load_clover(const CloverView &A, long long V, lo
                 a[8 * k + 2 * j + 1] = (T)(f2.y * n);
             }
         }
+    }
+}
+
+// As load_clover, but FP16 values are left unscaled and the norm returned.
+template <int P, typename T>
+__device__ __forceinline__ T load_clover_u(const CloverView &A, long long V, long long x, T (&a)[72])
+{
+    if constexpr (P == P16) {
+        const uint4 *p = (const uint4 *)A.d;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            uint4 v = p[k * V + x];
+            unsigned w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                float2 f2 = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
+                a[8 * k + 2 * j] = (T)f2.x;
+                a[8 * k + 2 * j + 1] = (T)f2.y;
+            }
+        }
+        return (T)A.n[x];
+    } else {
+        load_clover<P>(A, V, x, a);
+        return (T)1;
     }
 }
 

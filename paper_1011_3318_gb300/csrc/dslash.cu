@@ -23,17 +23,17 @@ __device__ __forceinline__ void hop_pair(const DslashArgs &a, long long x, const
         const long long xf = fwd_site(a.g, x, c, MU);
         const T sf = (c[MU] == a.g.L[MU] - 1 && a.g.bc[MU] < 0) ? -mk : mk;
         C<T> s[12], U[9];
-        load_spinor<P>(a.in, V, xf, s);
+        const T nf = load_spinor_u<P>(a.in, V, xf, s);
         load_link<P>(a.U, V, MU, x, U);
-        hop<MU, true>(acc, s, U, sf);
+        hop<MU, true>(acc, s, U, sf * nf);
     }
     {
         const long long xb = bwd_site(a.g, x, c, MU);
         const T sb = (c[MU] == 0 && a.g.bc[MU] < 0) ? -mk : mk;
         C<T> s[12], U[9];
-        load_spinor<P>(a.in, V, xb, s);
+        const T nb = load_spinor_u<P>(a.in, V, xb, s);
         load_link<P>(a.U, V, MU, xb, U);
-        hop<MU, false>(acc, s, U, sb);
+        hop<MU, false>(acc, s, U, sb * nb);
     }
 }
 
@@ -57,9 +57,14 @@ __global__ void __launch_bounds__(NT) dslash_kernel(const DslashArgs a)
         {
             T av[72];
             C<T> s[12];
-            load_clover<P>(a.A, V, x, av);
-            load_spinor<P>(a.in, V, x, s);
+            const T na = load_clover_u<P>(a.A, V, x, av);
+            const T ns = load_spinor_u<P>(a.in, V, x, s);
             clover_apply(av, s, acc);
+            if constexpr (P == P16) {
+                const T sc = na * ns;
+#pragma unroll
+                for (int k = 0; k < 12; k++) acc[k] = cscale(acc[k], sc);
+            }
         }
         const T mk = (T)(-a.kappa);
         hop_pair<P, 0>(a, x, c, acc, mk);

@@ -258,91 +258,113 @@ __device__ M3 field_strength(const Geom &g, const double2 *U64, long long x, con
     return F;
 }
 
-__global__ void __launch_bounds__(128) clover_build_kernel(Geom g, const double2 *U64, double kappa, double csw,
-                                                           double2 *A64, float4 *A32, uint4 *A16, float *A16n)
+// One CTA builds the clover of 32 consecutive sites in three phases:
+//  1. warp p (p = 0..5, the planes xy xz xt yz yt zt) computes Fhat_p of its
+//     site (lane) and leaves it in shared memory;
+//  2. 64 threads (site, chirality h) pack the Hermitian 6x6 block h from the
+//     six Fhat's (36 reals);
+//  3. 32 threads store each site in FP64, FP32 and FP16 (with its norm).
+// Holding one Fhat per thread instead of six keeps the FP64 leaf products
+// in registers.
+constexpr int CL_SITES = 32;
+
+__global__ void __launch_bounds__(6 * CL_SITES) clover_build_kernel(Geom g, const double2 *U64, double kappa,
+                                                                     double csw, double2 *A64, float4 *A32,
+                                                                     uint4 *A16, float *A16n)
 {
-    const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= g.V) return;
-    int c[4];
-    site_coords(g, x, c);
-    // planes in the order (x,y) (x,z) (x,t) (y,z) (y,t) (z,t)
-    M3 F01 = field_strength(g, U64, x, c, 0, 1);
-    M3 F02 = field_strength(g, U64, x, c, 0, 2);
-    M3 F03 = field_strength(g, U64, x, c, 0, 3);
-    M3 F12 = field_strength(g, U64, x, c, 1, 2);
-    M3 F13 = field_strength(g, U64, x, c, 1, 3);
-    M3 F23 = field_strength(g, U64, x, c, 2, 3);
-    double pk[72];
-    const double kc = kappa * csw;
-#pragma unroll 1
-    for (int h = 0; h < 2; h++) {
-        const double sg = h == 0 ? -1.0 : 1.0;
-        Z Gz[9], Gy[9], Gx[9];
+    __shared__ double sF[6][18][CL_SITES];
+    __shared__ double sP[72][CL_SITES];
+    const int lane = threadIdx.x % CL_SITES;
+    const long long x = (long long)blockIdx.x * CL_SITES + lane;
+    const bool act = x < g.V;
+    {
+        const int plane = threadIdx.x / CL_SITES;
+        // planes (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)
+        const int mu = (plane >= 3) + (plane >= 5);
+        const int nu = plane < 3 ? plane + 1 : plane < 5 ? plane - 1 : 3;
+        if (act) {
+            int c[4];
+            site_coords(g, x, c);
+            M3 F = field_strength(g, U64, x, c, mu, nu);
 #pragma unroll
-        for (int k = 0; k < 9; k++) {
-            Gz[k] = cadd(F01.e[k], cscale(F23.e[k], sg));
-            Gy[k] = csub(F02.e[k], cscale(F13.e[k], sg));
-            Gx[k] = cadd(F12.e[k], cscale(F03.e[k], sg));
+            for (int k = 0; k < 9; k++) {
+                sF[plane][2 * k][lane] = F.e[k].r;
+                sF[plane][2 * k + 1][lane] = F.e[k].i;
+            }
         }
-        // 6x6 block M = 1 + i kc B, B = [[Gz, Gx - i Gy], [Gx + i Gy, -Gz]]
-        Z M[36];
-#pragma unroll
-        for (int s = 0; s < 2; s++)
-#pragma unroll
-            for (int t = 0; t < 2; t++)
-#pragma unroll
-                for (int a = 0; a < 3; a++)
-#pragma unroll
-                    for (int b = 0; b < 3; b++) {
-                        const int k = a * 3 + b;
-                        Z bst;
-                        if (s == 0 && t == 0) bst = Gz[k];
-                        else if (s == 1 && t == 1) bst = cneg(Gz[k]);
-                        else if (s == 0) bst = csub(Gx[k], ci(Gy[k]));
-                        else bst = cadd(Gx[k], ci(Gy[k]));
-                        Z m = cscale(ci(bst), kc);
-                        if (s == t && a == b) m.r += 1.0;
-                        M[(s * 3 + a) * 6 + (t * 3 + b)] = m;
-                    }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * CL_SITES && act) {
+        // block h: 1 + i kc [[Gz, Gx - i Gy], [Gx + i Gy, -Gz]] with
+        //   Gz = F_xy -+ F_zt, Gy = F_xz +- F_yt, Gx = F_yz -+ F_xt (upper / lower)
+        const int h = threadIdx.x / CL_SITES;
+        const double sg = h == 0 ? -1.0 : 1.0;
+        const double kc = kappa * csw;
+        auto G = [&](int which, int a, int b) -> Z {
+            const int k = a * 3 + b;
+            int p0, p1;
+            double w;
+            if (which == 0) { p0 = 0; p1 = 5; w = sg; }          // Gz = F_xy + sg F_zt
+            else if (which == 1) { p0 = 1; p1 = 4; w = -sg; }    // Gy = F_xz - sg F_yt
+            else { p0 = 3; p1 = 2; w = sg; }                     // Gx = F_yz + sg F_xt
+            return Z{sF[p0][2 * k][lane] + w * sF[p1][2 * k][lane], sF[p0][2 * k + 1][lane] + w * sF[p1][2 * k + 1][lane]};
+        };
+        auto M = [&](int i, int j) -> Z {
+            const int s = i / 3, a = i % 3, t = j / 3, b = j % 3;
+            Z bst;
+            if (s == 0 && t == 0) bst = G(0, a, b);
+            else if (s == 1 && t == 1) bst = cneg(G(0, a, b));
+            else if (s == 0) bst = csub(G(2, a, b), ci(G(1, a, b)));
+            else bst = cadd(G(2, a, b), ci(G(1, a, b)));
+            Z m = cscale(ci(bst), kc);
+            if (i == j) m.r += 1.0;
+            return m;
+        };
         const int base = 36 * h;
-#pragma unroll
-        for (int i = 0; i < 6; i++) pk[base + i] = M[i * 6 + i].r;
-#pragma unroll
+#pragma unroll 1
+        for (int i = 0; i < 6; i++) sP[base + i][lane] = M(i, i).r;
+#pragma unroll 1
         for (int i = 1; i < 6; i++)
-#pragma unroll
+#pragma unroll 1
             for (int j = 0; j < i; j++) {
-                pk[base + cl_off(i, j)] = M[i * 6 + j].r;
-                pk[base + cl_off(i, j) + 1] = M[i * 6 + j].i;
+                const Z m = M(i, j);
+                sP[base + cl_off(i, j)][lane] = m.r;
+                sP[base + cl_off(i, j) + 1][lane] = m.i;
             }
     }
-    const long long V = g.V;
-    double nrm = 0.0;
+    __syncthreads();
+    if (threadIdx.x < CL_SITES && act) {
+        const long long V = g.V;
+        double nrm = 0.0;
+#pragma unroll 1
+        for (int k = 0; k < 72; k++) nrm = fmax(nrm, fabs(sP[k][lane]));
+        const double inv = nrm > 0 ? 1.0 / nrm : 0.0;
+#pragma unroll 1
+        for (int k = 0; k < 36; k++) A64[k * V + x] = make_double2(sP[2 * k][lane], sP[2 * k + 1][lane]);
+#pragma unroll 1
+        for (int k = 0; k < 18; k++)
+            A32[k * V + x] = make_float4((float)sP[4 * k][lane], (float)sP[4 * k + 1][lane], (float)sP[4 * k + 2][lane],
+                                         (float)sP[4 * k + 3][lane]);
+#pragma unroll 1
+        for (int k = 0; k < 9; k++) {
+            unsigned w[4];
 #pragma unroll
-    for (int k = 0; k < 72; k++) nrm = fmax(nrm, fabs(pk[k]));
-    const double inv = nrm > 0 ? 1.0 / nrm : 0.0;
-#pragma unroll
-    for (int k = 0; k < 36; k++) A64[k * V + x] = make_double2(pk[2 * k], pk[2 * k + 1]);
-#pragma unroll
-    for (int k = 0; k < 18; k++)
-        A32[k * V + x] = make_float4((float)pk[4 * k], (float)pk[4 * k + 1], (float)pk[4 * k + 2], (float)pk[4 * k + 3]);
-#pragma unroll
-    for (int k = 0; k < 9; k++) {
-        unsigned w[4];
-#pragma unroll
-        for (int j = 0; j < 4; j++) {
-            __half2 hh = __floats2half2_rn((float)(pk[8 * k + 2 * j] * inv), (float)(pk[8 * k + 2 * j + 1] * inv));
-            w[j] = *reinterpret_cast<unsigned *>(&hh);
+            for (int j = 0; j < 4; j++) {
+                __half2 hh = __floats2half2_rn((float)(sP[8 * k + 2 * j][lane] * inv),
+                                               (float)(sP[8 * k + 2 * j + 1][lane] * inv));
+                w[j] = *reinterpret_cast<unsigned *>(&hh);
+            }
+            A16[k * V + x] = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        A16[k * V + x] = make_uint4(w[0], w[1], w[2], w[3]);
+        A16n[x] = (float)nrm;
     }
-    A16n[x] = (float)nrm;
 }
 
 cudaError_t launch_clover_build(const Geom &g, const void *U64, double kappa, double csw, void *A64, void *A32,
                                 void *A16, float *A16n, cudaStream_t st)
 {
-    const unsigned nb = (unsigned)((g.V + 127) / 128);
-    clover_build_kernel<<<nb, 128, 0, st>>>(g, (const double2 *)U64, kappa, csw, (double2 *)A64, (float4 *)A32,
+    const unsigned nb = (unsigned)((g.V + CL_SITES - 1) / CL_SITES);
+    clover_build_kernel<<<nb, 6 * CL_SITES, 0, st>>>(g, (const double2 *)U64, kappa, csw, (double2 *)A64, (float4 *)A32,
                                             (uint4 *)A16, A16n);
     note_launch();
     return cudaGetLastError();

@@ -147,51 +147,202 @@ __device__ __forceinline__ void write_outputs(const RasArgs &a, long long x, con
     }
 }
 
-template <int P, int NT>
-__global__ void __launch_bounds__(NT) ras_smem_kernel(const RasArgs a)
+// Compact description of one site of the extended domain held by a thread
+// of the shared-memory kernel.
+struct LocSite {
+    int x;           // global site index
+    unsigned m;      // bit mu / 4+mu: forward / backward hop kept (inside the domain)
+                     // bit 8+mu / 12+mu: that hop carries the boundary sign -1
+                     // bit 16+mu / 20+mu: that hop wraps around a whole-lattice direction
+    int ls[4];       // local strides
+    int e[4];
+};
+
+enum { M_ACT = 1u << 24, M_BULK = 1u << 25 };
+
+__device__ __forceinline__ void loc_site(const Geom &g, const DomainGeom &dg, int dom, int l, LocSite &s)
+{
+    int k[4], lc[4];
+    int r = dom;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) { k[mu] = r % dg.nb[mu]; r /= dg.nb[mu]; }
+    const bool act = l < dg.nloc;
+    r = act ? l : 0;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) { lc[mu] = r % dg.e[mu]; r /= dg.e[mu]; }
+    unsigned m = act ? (unsigned)M_ACT : 0u;
+    bool bulk = act;
+    long long x = 0;
+    int ls = 1;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        int gc = (k[mu] * dg.b[mu] - dg.sh[mu] + lc[mu]) % g.L[mu];
+        if (gc < 0) gc += g.L[mu];
+        x += (long long)gc * g.stride[mu];
+        if (lc[mu] < dg.sh[mu] || lc[mu] >= dg.sh[mu] + dg.b[mu]) bulk = false;
+        const int e = dg.e[mu];
+        const bool whole = dg.b[mu] == g.L[mu];
+        if (whole || lc[mu] + 1 < e) m |= 1u << mu;
+        if (whole || lc[mu] > 0) m |= 1u << (4 + mu);
+        if (whole && lc[mu] == e - 1) m |= 1u << (16 + mu);
+        if (whole && lc[mu] == 0) m |= 1u << (20 + mu);
+        if (g.bc[mu] < 0 && gc == g.L[mu] - 1) m |= 1u << (8 + mu);
+        if (g.bc[mu] < 0 && gc == 0) m |= 1u << (12 + mu);
+        s.ls[mu] = ls;
+        s.e[mu] = e;
+        ls *= e;
+    }
+    if (bulk) m |= M_BULK;
+    s.m = m;
+    s.x = (int)x;
+}
+
+// Shared-memory layout of one CTA (one domain, NT threads):
+//   rho  float2[12][NT]   MR residual (read by the neighbours' hops)
+//   v    float2[12][NT]   MR solution
+//   U    links of the domain's sites, 4 directions, in the storage format of
+//        the field (FP16: uint2[12][NT], FP32: float4[12][NT]); the backward hop
+//        from a site uses the forward link of its neighbour, which is inside
+//        the domain whenever the hop is kept
+//   A    clover (only when SC): FP16 uint4[9][NT] + float[NT], FP32 float4[18][NT]
+template <int P> struct RasSmem {
+    static constexpr size_t link_bytes = P == P16 ? 96 : 192;
+    static constexpr size_t clover_bytes = P == P16 ? 148 : 288;
+    static constexpr size_t bytes(int nt, bool sc) { return (size_t)nt * (192 + link_bytes + (sc ? clover_bytes : 0)); }
+};
+
+template <int P, int MU>
+__device__ __forceinline__ void smem_hops(const LocSite &s, int l, const float2 *srho, LinkView sU, float kappa,
+                                          C<float> (&q)[12], int NT)
+{
+    const int ls = s.ls[MU], e = s.e[MU];
+    if (s.m & (1u << MU)) {
+        const int nf = (s.m & (1u << (16 + MU))) ? l - (e - 1) * ls : l + ls;
+        C<float> n[12], U[9];
+        ld_local(srho, NT, nf, n);
+        load_link<P>(sU, NT, MU, l, U);
+        hop<MU, true>(q, n, U, (s.m & (1u << (8 + MU))) ? kappa : -kappa);
+    }
+    if (s.m & (1u << (4 + MU))) {
+        const int nb = (s.m & (1u << (20 + MU))) ? l + (e - 1) * ls : l - ls;
+        C<float> n[12], U[9];
+        ld_local(srho, NT, nb, n);
+        load_link<P>(sU, NT, MU, nb, U);
+        hop<MU, false>(q, n, U, (s.m & (1u << (12 + MU))) ? kappa : -kappa);
+    }
+}
+
+template <int P, int NT, bool SC>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(const RasArgs a)
 {
     if (a.sc && a.sc->status != S_RUN) return;
-    extern __shared__ float2 srho[];  // [12][NT]
+    extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double red_sm[3 * 32 + 3];
+    float2 *srho = reinterpret_cast<float2 *>(smem);
+    float2 *sv = srho + 12 * NT;
+    unsigned char *sU = reinterpret_cast<unsigned char *>(sv + 12 * NT);
+    unsigned char *sA = sU + (size_t)NT * RasSmem<P>::link_bytes;
+    float *sAn = reinterpret_cast<float *>(sA + (size_t)NT * (P == P16 ? 144 : 288));
+    const LinkView lU{sU};
+    const CloverView lA = SC ? CloverView{sA, sAn} : a.A;
+    const long long V = a.g.V;
     const int l = threadIdx.x;
-    DomSite ds;
-    dom_site(a.g, a.dg, blockIdx.x, l, a.kappa, ds);
+    LocSite s;
+    loc_site(a.g, a.dg, blockIdx.x, l, s);
+    const bool act = s.m & M_ACT;
 
-    C<float> rho[12], v[12];
+    // stage the projection P_{Omega'} r, and the domain's links and clover
+    {
+        C<float> r[12], z[12];
 #pragma unroll
-    for (int k = 0; k < 12; k++) { rho[k] = {0.f, 0.f}; v[k] = {0.f, 0.f}; }
-    if (ds.act) load_spinor<P>(a.in, a.g.V, ds.x, rho);   // projection P_{Omega'}
-    st_local(srho, NT, l, rho);
+        for (int k = 0; k < 12; k++) { r[k] = {0.f, 0.f}; z[k] = {0.f, 0.f}; }
+        if (act) load_spinor<P>(a.in, V, s.x, r);
+        st_local(srho, NT, l, r);
+        st_local(sv, NT, l, z);
+        if (act) {
+            if constexpr (P == P16) {
+                const uint2 *g = (const uint2 *)a.U.d;
+#pragma unroll
+                for (int k = 0; k < 12; k++) ((uint2 *)sU)[k * NT + l] = g[(long long)k * V + s.x];
+                if constexpr (SC) {
+                    const uint4 *ga = (const uint4 *)a.A.d;
+#pragma unroll
+                    for (int k = 0; k < 9; k++) ((uint4 *)sA)[k * NT + l] = ga[(long long)k * V + s.x];
+                    sAn[l] = a.A.n[s.x];
+                }
+            } else {
+                const float4 *g = (const float4 *)a.U.d;
+#pragma unroll
+                for (int k = 0; k < 12; k++) ((float4 *)sU)[k * NT + l] = g[(long long)k * V + s.x];
+                if constexpr (SC) {
+                    const float4 *ga = (const float4 *)a.A.d;
+#pragma unroll
+                    for (int k = 0; k < 18; k++) ((float4 *)sA)[k * NT + l] = ga[(long long)k * V + s.x];
+                }
+            }
+        }
+    }
 
     for (int it = 0; it < a.n_iter; it++) {
         __syncthreads();
         C<float> q[12];
 #pragma unroll
         for (int k = 0; k < 12; k++) q[k] = {0.f, 0.f};
-        if (ds.act) dom_apply<P>(a, ds, rho, srho, NT, q);
-        float qr = 0.f, qi = 0.f, qq = 0.f;
+        if (act) {
+            {
+                C<float> own[12];
+                float av[72];
+                ld_local(srho, NT, l, own);
+                const float na = load_clover_u<P>(lA, SC ? (long long)NT : V, SC ? l : s.x, av);
+                clover_apply(av, own, q);
+                if constexpr (P == P16) {
 #pragma unroll
-        for (int k = 0; k < 12; k++) {
-            C<float> t = cmulc(q[k], rho[k]);
-            qr += t.r;
-            qi += t.i;
-            qq += q[k].r * q[k].r + q[k].i * q[k].i;
+                    for (int k = 0; k < 12; k++) q[k] = cscale(q[k], na);
+                }
+            }
+            smem_hops<P, 0>(s, l, srho, lU, a.kappa, q, NT);
+            smem_hops<P, 1>(s, l, srho, lU, a.kappa, q, NT);
+            smem_hops<P, 2>(s, l, srho, lU, a.kappa, q, NT);
+            smem_hops<P, 3>(s, l, srho, lU, a.kappa, q, NT);
         }
-        double red[3] = {qr, qi, qq};
-        block_allsum<3>(red, red_sm);
-        if (red[2] > 0.0) {
-            const C<float> al = {(float)(red[0] / red[2]), (float)(red[1] / red[2])};
+        double red[3];
+        {
+            C<float> own[12];
+            ld_local(srho, NT, l, own);
+            float qr = 0.f, qi = 0.f, qq = 0.f;
 #pragma unroll
             for (int k = 0; k < 12; k++) {
-                v[k] = cadd(v[k], cmul(al, rho[k]));
-                rho[k] = csub(rho[k], cmul(al, q[k]));
+                C<float> t = cmulc(q[k], own[k]);
+                qr += t.r;
+                qi += t.i;
+                qq += q[k].r * q[k].r + q[k].i * q[k].i;
             }
+            red[0] = qr;
+            red[1] = qi;
+            red[2] = qq;
         }
-        // every thread is past the barriers of block_allsum, so all reads of
-        // srho for this iteration are done
-        st_local(srho, NT, l, rho);
+        block_allsum<3>(red, red_sm);
+        // every thread is past the barriers of block_allsum: all reads of rho
+        // for this iteration are done and rho can be updated in place
+        if (red[2] > 0.0) {
+            const C<float> al = {(float)(red[0] / red[2]), (float)(red[1] / red[2])};
+            C<float> own[12], vv[12];
+            ld_local(srho, NT, l, own);
+            ld_local(sv, NT, l, vv);
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                vv[k] = cadd(vv[k], cmul(al, own[k]));
+                own[k] = csub(own[k], cmul(al, q[k]));
+            }
+            st_local(sv, NT, l, vv);
+            st_local(srho, NT, l, own);
+        }
     }
-    if (ds.bulk) write_outputs<P>(a, ds.x, v);  // restriction R_{Omega}
+    if (s.m & M_BULK) {  // restriction R_{Omega}
+        C<float> vv[12];
+        ld_local(sv, NT, l, vv);
+        write_outputs<P>(a, s.x, vv);
+    }
 }
 
 constexpr int RAS_GMEM_NT = 256;
@@ -268,26 +419,37 @@ __global__ void __launch_bounds__(RAS_GMEM_NT) ras_gmem_kernel(const RasArgs a)
     }
 }
 
-template <int P, int NT>
+template <int P, int NT, bool SC>
 static cudaError_t launch_smem(const RasArgs &a, cudaStream_t st)
 {
-    const size_t smem = (size_t)12 * NT * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(ras_smem_kernel<P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = RasSmem<P>::bytes(NT, SC);
+    cudaError_t e = cudaFuncSetAttribute(ras_smem_kernel<P, NT, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    ras_smem_kernel<P, NT><<<a.dg.ndom, NT, smem, st>>>(a);
+    ras_smem_kernel<P, NT, SC><<<a.dg.ndom, NT, smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
 
+// The shared-memory kernel stages the clover too when it fits: always for
+// FP16 storage (111.6 KB per 256-site domain, two CTAs per SM), for FP32 only
+// up to 128 sites (at 256 sites the FP32 clover would leave one CTA per SM;
+// it is read through L1 instead).
 template <int P>
 static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
 {
     const int n = a.dg.nloc;
-    if (n <= 64) return launch_smem<P, 64>(a, st);
-    if (n <= 128) return launch_smem<P, 128>(a, st);
-    if (n <= 256) return launch_smem<P, 256>(a, st);
-    if (n <= RAS_SMEM_MAX_SITES) return launch_smem<P, 512>(a, st);
+    if constexpr (P == P16) {
+        if (n <= 64) return launch_smem<P, 64, true>(a, st);
+        if (n <= 128) return launch_smem<P, 128, true>(a, st);
+        if (n <= 256) return launch_smem<P, 256, true>(a, st);
+        if (n <= RAS_SMEM_MAX_SITES) return launch_smem<P, 512, true>(a, st);
+    } else if constexpr (P == P32) {
+        if (n <= 64) return launch_smem<P, 64, true>(a, st);
+        if (n <= 128) return launch_smem<P, 128, true>(a, st);
+        if (n <= 256) return launch_smem<P, 256, false>(a, st);
+        if (n <= RAS_SMEM_MAX_SITES) return launch_smem<P, 512, false>(a, st);
+    }
     if (!a.scratch || a.slots < 1) return cudaErrorInvalidValue;
     const int grid = a.slots < a.dg.ndom ? a.slots : a.dg.ndom;
     ras_gmem_kernel<P><<<grid, RAS_GMEM_NT, 0, st>>>(a);
