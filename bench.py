@@ -245,6 +245,16 @@ def run_ours(args, rank, world):
     params = qdd.default_params(inner_prec=args.prec, use_ras=1, block=args.block, overlap=args.overlap,
                                 n_dominv=args.n_dominv, n_ras=args.n_ras, inner_tol=args.inner_tol)
     plain = qdd.default_params(inner_prec="f64", use_ras=0)
+    tune = None
+    if not args.no_autotune:
+        qdd.load_gauge(lat, dU)
+        t0 = time.perf_counter()
+        params, best_ms = qdd.autotune(lat, deta, KAPPA, CSW, TOL, params, max_trials=args.tune_trials)
+        tune = {"seconds": round(time.perf_counter() - t0, 2), "best_solve_ms": round(best_ms, 2),
+                "block": list(params.block), "overlap": params.overlap, "n_dominv": params.n_dominv,
+                "n_ras": params.n_ras}
+        log(f"autotune: {tune}")
+    blk, ov, nd, nr = list(params.block), params.overlap, params.n_dominv, params.n_ras
 
     def step():
         qdd.load_gauge(lat, dU)           # gauge import + invalidates the clover: rebuilt inside the solve
@@ -302,12 +312,12 @@ def run_ours(args, rank, world):
     if dom == "ras":
         ms_l = prof["ras"][0] / max(1, prof["ras"][1])
         nloc = 1
-        for b, L in zip(args.block, DIMS):
-            nloc *= b if b == L else b + 2 * args.overlap
+        for b, L in zip(blk, DIMS):
+            nloc *= b if b == L else b + 2 * ov
         ndom = 1
-        for b, L in zip(args.block, DIMS):
+        for b, L in zip(blk, DIMS):
             ndom *= L // b
-        flops = ndom * nloc * args.n_dominv * (FLOPS_PER_SITE_D + 96 + 48)
+        flops = ndom * nloc * nd * (FLOPS_PER_SITE_D + 96 + 48)
         ach = flops / (ms_l * 1e-3) / 1e12
         roof = {"kernel": "ras_smem_kernel (RAS sweep)", "bound": "alu", "achieved": round(ach, 2),
                 "peak": round(fp32_alu_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_alu_peak, 3),
@@ -366,8 +376,9 @@ def run_ours(args, rank, world):
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "lattice": list(DIMS),
                        "method": f"FP64 defect correction + {args.prec}-storage/FP32 inner BiCGStab, RAS "
-                                 f"block {'x'.join(map(str, args.block))} s={args.overlap} "
-                                 f"N_dominv={args.n_dominv} NRAS={args.n_ras}, inner tol {args.inner_tol}",
+                                 f"block {'x'.join(map(str, blk))} s={ov} "
+                                 f"N_dominv={nd} NRAS={nr}, inner tol {args.inner_tol}",
+                       "autotune": tune,
                        "l2": "inputs larger than L2 (links 604 MB, source 201 MB FP64 per replica)",
                        "parallelism": f"{world} independent replica(s)"},
             "solve": {k: info[k] for k in ("outer_iters", "inner_iters", "dv_count", "ras_sweeps",
@@ -444,6 +455,9 @@ def main():
     ap.add_argument("--n-ras", dest="n_ras", type=int, default=3)
     ap.add_argument("--inner-tol", dest="inner_tol", type=float, default=1e-3)
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
+    ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
+                    help="use --block/--overlap/--n-dominv/--n-ras as given instead of tuning them")
+    ap.add_argument("--tune-trials", dest="tune_trials", type=int, default=36)
     ap.add_argument("--kernels", default=None,
                     help="profiler workload: dslash:f16|f32|f64, ras:f16|f32 or clover, three launches at 32^4")
     args = ap.parse_args()

@@ -161,6 +161,16 @@ qdd_status qdd_ras_apply(qdd_lattice *lat, double *out, const double *in, double
 qdd_status qdd_solve(qdd_lattice *lat, double *phi, const double *eta, double kappa, double c_sw,
                      double tol, const qdd_solver_params *params, qdd_solve_info *info);
 
+/* Chooses the RAS parameters that minimise the time of a whole solve of
+ * D phi = eta (the paper's parameter survey of Sec. 5, done by timing):
+ * coordinate search over (n_dominv, n_ras), block shapes of 16 to 256 sites,
+ * and overlap 1, at most max_trials solves.  params is the starting point
+ * (inner_prec QDD_F32 or QDD_F16, use_ras = 1) and receives the best
+ * parameters; best_ms (may be NULL) receives the best solve time.  eta is a
+ * canonical FP64 spinor, host or device.  Runs synchronously. */
+qdd_status qdd_autotune(qdd_lattice *lat, const double *eta, double kappa, double c_sw, double tol,
+                        qdd_solver_params *params, int max_trials, double *best_ms);
+
 /* -- internal-layout fields ------------------------------------------------ */
 
 /* Creates a spinor field of precision prec in the internal layout. */

@@ -65,7 +65,7 @@ qdd_status ensure_clover(qdd_lattice *lat, double kappa, double csw)
     }
     if (lat->clover_valid && lat->kappa_c == kappa && lat->csw_c == csw) return QDD_OK;
     ProfScope ps(lat, QDD_K_CLOVER);
-    cudaError_t e = launch_clover_build(lat->g, lat->U64, kappa, csw, lat->A64, lat->A32, lat->A16, lat->A16n,
+    cudaError_t e = launch_clover_build(lat->g, lat->Udf, kappa, csw, lat->A64, lat->A32, lat->A16, lat->A16n,
                                         lat->stream);
     if (e != cudaSuccess) return cuda_fail(e, "clover build");
     lat->clover_valid = true;
@@ -226,7 +226,7 @@ qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc
         void **p;
         size_t bytes;
     } allocs[] = {
-        {&lat->U64, (size_t)V * 4 * 9 * 16}, {&lat->U32, (size_t)V * 4 * 3 * 16}, {&lat->U16, (size_t)V * 4 * 3 * 8},
+        {&lat->U64, (size_t)V * 4 * 9 * 16}, {&lat->Udf, (size_t)V * 4 * 9 * 16}, {&lat->U32, (size_t)V * 4 * 3 * 16}, {&lat->U16, (size_t)V * 4 * 3 * 8},
         {&lat->A64, (size_t)V * 36 * 16},    {&lat->A32, (size_t)V * 18 * 16},    {&lat->A16, (size_t)V * 9 * 16},
         {(void **)&lat->A16n, (size_t)V * 4}, {(void **)&lat->rs.partials, (size_t)max_blocks * 4 * sizeof(double)},
         {(void **)&lat->rs.counter, 64},     {(void **)&lat->sc, sizeof(Scalars)},
@@ -255,7 +255,7 @@ qdd_status qdd_destroy_lattice(qdd_lattice *lat)
 {
     if (!lat) return QDD_OK;
     cudaStreamSynchronize(lat->stream);
-    void *ptrs[] = {lat->U64, lat->U32, lat->U16, lat->A64, lat->A32, lat->A16, lat->A16n, lat->rs.partials,
+    void *ptrs[] = {lat->U64, lat->Udf, lat->U32, lat->U16, lat->A64, lat->A32, lat->A16, lat->A16n, lat->rs.partials,
                     lat->rs.counter, lat->sc, lat->maxdev, lat->stage_a, lat->stage_b, lat->ras_scratch};
     for (void *p : ptrs) cudaFree(p);
     if (lat->sc_host) cudaFreeHost(lat->sc_host);
@@ -291,7 +291,7 @@ qdd_status qdd_load_gauge(qdd_lattice *lat, const double *U)
     e = cudaMemsetAsync(lat->maxdev, 0, sizeof(unsigned long long), lat->stream);
     if (e == cudaSuccess) {
         ProfScope ps(lat, QDD_K_CLOVER);
-        e = launch_gauge_convert(lat->g, src, lat->U64, lat->U32, lat->U16, lat->maxdev, lat->stream);
+        e = launch_gauge_convert(lat->g, src, lat->U64, lat->U32, lat->U16, lat->Udf, lat->maxdev, lat->stream);
     }
     unsigned long long bits = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, lat->maxdev, sizeof(bits), cudaMemcpyDeviceToHost, lat->stream);
@@ -420,6 +420,27 @@ qdd_status qdd_solve(qdd_lattice *lat, double *phi, const double *eta, double ka
     if (st != QDD_OK) return st;
     g_err = keep;
     return res;
+}
+
+qdd_status qdd_autotune(qdd_lattice *lat, const double *eta, double kappa, double c_sw, double tol,
+                        qdd_solver_params *params, int max_trials, double *best_ms)
+{
+    g_err.clear();
+    if (!lat || !eta || !params || !(tol > 0) || max_trials < 1) {
+        set_error("invalid argument");
+        return QDD_ERR_ARG;
+    }
+    if ((params->inner_prec != QDD_F32 && params->inner_prec != QDD_F16) || !params->use_ras) {
+        set_error("qdd_autotune tunes the RAS parameters of an FP32 or FP16 inner solve (use_ras = 1)");
+        return QDD_ERR_ARG;
+    }
+    qdd_status st;
+    const double *deta;
+    if ((st = stage_in(lat, eta, &lat->stage_a, &deta)) != QDD_OK) return st;
+    double *dphi = nullptr;
+    if ((st = ensure_stage(lat, &lat->stage_b)) != QDD_OK) return st;
+    dphi = lat->stage_b;
+    return autotune_impl(lat, dphi, deta, kappa, c_sw, tol, params, max_trials, best_ms);
 }
 
 qdd_status qdd_field_create(qdd_lattice *lat, qdd_prec prec, qdd_field **out)

@@ -1,0 +1,114 @@
+// autotune.cu -- picks the RAS parameters that minimise time to solution.
+//
+// The paper surveys NRAS = 1..10, N_dominv = 1..20 and d = 0, 2, 4 on its
+// cluster and keeps the fastest (Sec. 5).  The best point depends on the
+// machine: there the global D was dominated by GigE communication, here it is
+// an HBM-bound kernel, so the balance between domain work and Krylov
+// iterations moves.  This tuner times whole solves of the caller's system
+// and searches coordinate-wise:
+//   1. (N_dominv, NRAS) on the starting block shape,
+//   2. the block shape (16 .. 256-site blocks, one orientation per shape),
+//   3. (N_dominv, NRAS) again around the best point on the best shape,
+//   4. overlap s = 1 on the best shape when its extended domain stays small.
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include "lib.h"
+
+namespace qdd {
+
+namespace {
+
+struct Trial {
+    qdd_solver_params p;
+    double ms;
+};
+
+bool same_ras(const qdd_solver_params &a, const qdd_solver_params &b)
+{
+    return memcmp(a.block, b.block, sizeof(a.block)) == 0 && a.overlap == b.overlap && a.n_dominv == b.n_dominv &&
+           a.n_ras == b.n_ras;
+}
+
+}  // namespace
+
+qdd_status autotune_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, double kappa, double csw,
+                         double tol, qdd_solver_params *p, int max_trials, double *best_ms)
+{
+    using clk = std::chrono::steady_clock;
+    std::vector<Trial> done;
+    Trial best{*p, 1e300};
+    qdd_status st = QDD_OK;
+
+    auto trial = [&](qdd_solver_params q) -> void {
+        if ((int)done.size() >= max_trials) return;
+        for (const Trial &t : done)
+            if (same_ras(t.p, q)) return;
+        DomainGeom dg;
+        if (!domain_geom(lat->g, q.block, q.overlap, &dg, nullptr)) return;
+        if (dg.nloc > RAS_SMEM_MAX_SITES) return;  // the general kernel is never the fastest
+        qdd_solve_info info;
+        const auto t0 = clk::now();
+        qdd_status s = solve_impl(lat, phi_dev, eta_dev, kappa, csw, tol, &q, &info);
+        const double ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+        if (s != QDD_OK && s != QDD_ERR_NOT_CONVERGED && s != QDD_ERR_BREAKDOWN) {
+            st = s;
+            return;
+        }
+        const double score = s == QDD_OK ? ms : 1e299;
+        done.push_back(Trial{q, score});
+        if (score < best.ms) best = Trial{q, score};
+    };
+
+    // warm the clover cache and the work vectors so the first trial is not penalised
+    {
+        qdd_solve_info info;
+        qdd_solver_params q = *p;
+        solve_impl(lat, phi_dev, eta_dev, kappa, csw, tol, &q, &info);
+    }
+    const int nds[] = {1, 2, 3, 4, 6};
+    const int nrs[] = {1, 2, 3};
+    for (int nd : nds)
+        for (int nr : nrs) {
+            qdd_solver_params q = *p;
+            q.n_dominv = nd;
+            q.n_ras = nr;
+            trial(q);
+            if (st != QDD_OK) return st;
+        }
+    const int shapes[][4] = {{2, 2, 2, 2}, {4, 2, 2, 2}, {4, 4, 2, 2}, {4, 4, 4, 2}, {4, 4, 4, 4}, {8, 4, 4, 4}};
+    const qdd_solver_params base = best.p;
+    for (const auto &sh : shapes) {
+        qdd_solver_params q = base;
+        for (int mu = 0; mu < 4; mu++) q.block[mu] = sh[mu];
+        q.overlap = 0;
+        trial(q);
+        if (st != QDD_OK) return st;
+    }
+    const qdd_solver_params around = best.p;
+    for (int dnd = -1; dnd <= 1; dnd++)
+        for (int nr : nrs) {
+            qdd_solver_params q = around;
+            q.n_dominv = around.n_dominv + dnd;
+            q.n_ras = nr;
+            if (q.n_dominv < 1) continue;
+            trial(q);
+            if (st != QDD_OK) return st;
+        }
+    {
+        qdd_solver_params q = best.p;
+        q.overlap = 1;
+        trial(q);
+        if (st != QDD_OK) return st;
+    }
+    if (best.ms >= 1e299) {
+        set_error("autotune: no candidate converged");
+        return QDD_ERR_NOT_CONVERGED;
+    }
+    *p = best.p;
+    if (best_ms) *best_ms = best.ms;
+    return QDD_OK;
+}
+
+}  // namespace qdd

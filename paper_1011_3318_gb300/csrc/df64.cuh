@@ -1,0 +1,107 @@
+// df64.cuh -- double-float arithmetic: a value is the unevaluated sum hi + lo
+// of two FP32 numbers with |lo| <= ulp(hi)/2, giving about 2^-47 relative
+// precision on the FP32 pipes.
+//
+// Methods: Dekker, "A floating-point technique for extending the available
+// precision" (Numer. Math. 18, 1971) for the representation and the fast
+// two-sum; Knuth (TAOCP vol. 2) for the branch-free two-sum; Ogita, Rump and
+// Oishi, "Accurate sum and dot product" (SIAM J. Sci. Comput. 26, 2005) for
+// the FMA-based two-product.  Every step uses the _rn intrinsics so that the
+// compiler neither contracts nor reorders the error-free transformations.
+//
+// Used where FP64 accuracy is needed but GB300's FP64 rate (about 1/74 of its
+// FP32 rate) would dominate: the clover-term build.
+#pragma once
+
+namespace qdd {
+
+struct DF {
+    float h, l;
+};
+
+__device__ __forceinline__ DF df_from_double(double d)
+{
+    const float h = __double2float_rn(d);
+    const float l = __double2float_rn(d - (double)h);
+    return DF{h, l};
+}
+
+__device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (double)a.l; }
+
+// s + e = a + b exactly (Knuth)
+__device__ __forceinline__ DF two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return DF{s, e};
+}
+
+// s + e = a + b exactly when |a| >= |b| (Dekker)
+__device__ __forceinline__ DF fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b)
+{
+    DF s = two_sum(a.h, b.h);
+    const float t = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+    return fast_two_sum(s.h, t);
+}
+
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.h, -a.l}; }
+
+__device__ __forceinline__ DF df_sub(DF a, DF b) { return df_add(a, df_neg(b)); }
+
+// c + a b
+__device__ __forceinline__ DF df_fma(DF a, DF b, DF c)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);           // p + e = a.h b.h exactly (Ogita-Rump-Oishi)
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    DF s = two_sum(p, c.h);
+    const float t = __fadd_rn(s.l, __fadd_rn(e, c.l));
+    return fast_two_sum(s.h, t);
+}
+
+// Scaling by a power of two is exact.
+__device__ __forceinline__ DF df_scale2(DF a, float pow2) { return DF{a.h * pow2, a.l * pow2}; }
+
+struct CDF {
+    DF r, i;
+};
+
+// c + a b (complex)
+__device__ __forceinline__ CDF cdf_fma(CDF a, CDF b, CDF c)
+{
+    c.r = df_fma(a.r, b.r, c.r);
+    c.r = df_fma(df_neg(a.i), b.i, c.r);
+    c.i = df_fma(a.r, b.i, c.i);
+    c.i = df_fma(a.i, b.r, c.i);
+    return c;
+}
+
+// c + conj(a) b
+__device__ __forceinline__ CDF cdf_fma_ca(CDF a, CDF b, CDF c)
+{
+    c.r = df_fma(a.r, b.r, c.r);
+    c.r = df_fma(a.i, b.i, c.r);
+    c.i = df_fma(a.r, b.i, c.i);
+    c.i = df_fma(df_neg(a.i), b.r, c.i);
+    return c;
+}
+
+// c + a conj(b)
+__device__ __forceinline__ CDF cdf_fma_cb(CDF a, CDF b, CDF c)
+{
+    c.r = df_fma(a.r, b.r, c.r);
+    c.r = df_fma(a.i, b.i, c.r);
+    c.i = df_fma(df_neg(a.r), b.i, c.i);
+    c.i = df_fma(a.i, b.r, c.i);
+    return c;
+}
+
+}  // namespace qdd

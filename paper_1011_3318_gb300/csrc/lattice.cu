@@ -15,6 +15,7 @@
 // The build runs once per (gauge field, kappa, c_sw) in FP64 and stores the
 // result in all three working precisions.
 #include "device.cuh"
+#include "df64.cuh"
 #include "lib.h"
 
 namespace qdd {
@@ -70,7 +71,7 @@ cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorVie
 }
 
 // ---------------------------------------------------------------- gauge
-__global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, float4 *U32, uint2 *U16,
+__global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, float4 *U32, uint2 *U16, float4 *Udf,
                                      unsigned long long *maxdev)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -104,7 +105,11 @@ __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, floa
 
         const long long V = g.V;
 #pragma unroll
-        for (int k = 0; k < 9; k++) U64[((long long)mu * 9 + k) * V + x] = make_double2(m[k].r, m[k].i);
+        for (int k = 0; k < 9; k++) {
+            U64[((long long)mu * 9 + k) * V + x] = make_double2(m[k].r, m[k].i);
+            const DF re = df_from_double(m[k].r), im = df_from_double(m[k].i);
+            Udf[((long long)mu * 9 + k) * V + x] = make_float4(re.h, re.l, im.h, im.l);
+        }
 #pragma unroll
         for (int q = 0; q < 3; q++) {
             U32[((long long)mu * 3 + q) * V + x] =
@@ -121,12 +126,13 @@ __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, floa
     if ((threadIdx.x & 31) == 0) atomicMax(maxdev, (unsigned long long)__double_as_longlong(dev));
 }
 
-cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void *U32, void *U16,
+cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void *U32, void *U16, void *Udf,
                                  unsigned long long *maxdev, cudaStream_t st)
 {
     const long long n = g.V * 4;
     const unsigned nb = (unsigned)((n + 255) / 256);
-    gauge_convert_kernel<<<nb, 256, 0, st>>>(g, U, (double2 *)U64, (float4 *)U32, (uint2 *)U16, maxdev);
+    gauge_convert_kernel<<<nb, 256, 0, st>>>(g, U, (double2 *)U64, (float4 *)U32, (uint2 *)U16, (float4 *)Udf,
+                                             maxdev);
     note_launch();
     return cudaGetLastError();
 }
@@ -134,77 +140,81 @@ cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void
 // ---------------------------------------------------------------- clover
 typedef C<double> Z;
 
-struct M3 {
-    Z e[9];
+// 3x3 complex matrices in double-float arithmetic (df64.cuh).
+struct M3D {
+    CDF e[9];
 };
 
-__device__ __forceinline__ M3 m3_load(const double2 *U64, long long V, int mu, long long x)
+__device__ __forceinline__ M3D md_load(const float4 *Udf, long long V, int mu, long long x)
 {
-    M3 m;
-    const double2 *p = U64 + (long long)mu * 9 * V;
+    M3D m;
+    const float4 *p = Udf + (long long)mu * 9 * V;
 #pragma unroll
     for (int k = 0; k < 9; k++) {
-        double2 v = p[k * V + x];
-        m.e[k] = {v.x, v.y};
+        const float4 v = p[k * V + x];
+        m.e[k] = CDF{DF{v.x, v.y}, DF{v.z, v.w}};
     }
     return m;
 }
 
-__device__ __forceinline__ M3 m3_mul(const M3 &a, const M3 &b)
+__device__ __forceinline__ M3D md_zero()
 {
-    M3 c;
+    M3D c;
 #pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            Z s = {0, 0};
-#pragma unroll
-            for (int k = 0; k < 3; k++) s = cadd(s, cmul(a.e[i * 3 + k], b.e[k * 3 + j]));
-            c.e[i * 3 + j] = s;
-        }
+    for (int k = 0; k < 9; k++) c.e[k] = CDF{DF{0.f, 0.f}, DF{0.f, 0.f}};
     return c;
 }
 
-__device__ __forceinline__ M3 m3_dag(const M3 &a)
+__device__ __forceinline__ M3D md_mul(const M3D &a, const M3D &b)  // a b
 {
-    M3 c;
+    M3D c = md_zero();
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) c.e[i * 3 + j] = cconj(a.e[j * 3 + i]);
+        for (int j = 0; j < 3; j++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) c.e[i * 3 + j] = cdf_fma(a.e[i * 3 + k], b.e[k * 3 + j], c.e[i * 3 + j]);
     return c;
 }
 
-// a * b^dag
-__device__ __forceinline__ M3 m3_mul_d(const M3 &a, const M3 &b)
+__device__ __forceinline__ M3D md_mul_d(const M3D &a, const M3D &b)  // a b^dag
 {
-    M3 c;
+    M3D c = md_zero();
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            Z s = {0, 0};
+        for (int j = 0; j < 3; j++)
 #pragma unroll
-            for (int k = 0; k < 3; k++) s = cadd(s, cmul(a.e[i * 3 + k], cconj(b.e[j * 3 + k])));
-            c.e[i * 3 + j] = s;
-        }
+            for (int k = 0; k < 3; k++) c.e[i * 3 + j] = cdf_fma_cb(a.e[i * 3 + k], b.e[j * 3 + k], c.e[i * 3 + j]);
     return c;
 }
 
-// a^dag * b
-__device__ __forceinline__ M3 m3_dmul(const M3 &a, const M3 &b)
+__device__ __forceinline__ M3D md_dmul(const M3D &a, const M3D &b)  // a^dag b
 {
-    M3 c;
+    M3D c = md_zero();
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            Z s = {0, 0};
+        for (int j = 0; j < 3; j++)
 #pragma unroll
-            for (int k = 0; k < 3; k++) s = cadd(s, cmulc(a.e[k * 3 + i], b.e[k * 3 + j]));
-            c.e[i * 3 + j] = s;
-        }
+            for (int k = 0; k < 3; k++) c.e[i * 3 + j] = cdf_fma_ca(a.e[k * 3 + i], b.e[k * 3 + j], c.e[i * 3 + j]);
     return c;
+}
+
+__device__ __forceinline__ M3D md_dag(const M3D &a)
+{
+    M3D c;
+#pragma unroll
+    for (int i = 0; i < 3; i++)
+#pragma unroll
+        for (int j = 0; j < 3; j++) c.e[i * 3 + j] = CDF{a.e[j * 3 + i].r, df_neg(a.e[j * 3 + i].i)};
+    return c;
+}
+
+__device__ __forceinline__ void md_acc(M3D &q, const M3D &l)
+{
+#pragma unroll
+    for (int k = 0; k < 9; k++) q.e[k] = CDF{df_add(q.e[k].r, l.e[k].r), df_add(q.e[k].i, l.e[k].i)};
 }
 
 __device__ __forceinline__ long long shifted(const Geom &g, const int c[4], int mu, int dm, int nu, int dn)
@@ -215,47 +225,44 @@ __device__ __forceinline__ long long shifted(const Geom &g, const int c[4], int 
     return d[0] + g.stride[1] * d[1] + g.stride[2] * d[2] + g.stride[3] * d[3];
 }
 
-// Fhat_{mu nu}(x) = (Q - Q^dag) / 8 from the four counter-clockwise leaves.
-__device__ M3 field_strength(const Geom &g, const double2 *U64, long long x, const int c[4], int mu, int nu)
+// Fhat_{mu nu}(x) = (Q - Q^dag) / 8 from the four counter-clockwise leaves,
+// in double-float arithmetic; returned as FP64 (18 reals, row-major re/im).
+__device__ void field_strength(const Geom &g, const float4 *Udf, long long x, const int c[4], int mu, int nu,
+                               double (&F)[18])
 {
     const long long V = g.V;
     const long long xpm = shifted(g, c, mu, 1, nu, 0), xpn = shifted(g, c, mu, 0, nu, 1);
     const long long xmm = shifted(g, c, mu, -1, nu, 0), xmn = shifted(g, c, mu, 0, nu, -1);
     const long long xmm_pn = shifted(g, c, mu, -1, nu, 1), xmm_mn = shifted(g, c, mu, -1, nu, -1);
     const long long xpm_mn = shifted(g, c, mu, 1, nu, -1);
-    M3 Q;
     // x -> x+mu -> x+mu+nu -> x+nu -> x
-    M3 l = m3_mul(m3_load(U64, V, mu, x), m3_load(U64, V, nu, xpm));
-    l = m3_mul_d(l, m3_load(U64, V, mu, xpn));
-    l = m3_mul_d(l, m3_load(U64, V, nu, x));
-    Q = l;
+    M3D Q = md_mul(md_load(Udf, V, mu, x), md_load(Udf, V, nu, xpm));
+    Q = md_mul_d(Q, md_load(Udf, V, mu, xpn));
+    Q = md_mul_d(Q, md_load(Udf, V, nu, x));
     // x -> x+nu -> x-mu+nu -> x-mu -> x
-    l = m3_mul_d(m3_load(U64, V, nu, x), m3_load(U64, V, mu, xmm_pn));
-    l = m3_mul_d(l, m3_load(U64, V, nu, xmm));
-    l = m3_mul(l, m3_load(U64, V, mu, xmm));
-#pragma unroll
-    for (int k = 0; k < 9; k++) Q.e[k] = cadd(Q.e[k], l.e[k]);
+    M3D l = md_mul_d(md_load(Udf, V, nu, x), md_load(Udf, V, mu, xmm_pn));
+    l = md_mul_d(l, md_load(Udf, V, nu, xmm));
+    l = md_mul(l, md_load(Udf, V, mu, xmm));
+    md_acc(Q, l);
     // x -> x-mu -> x-mu-nu -> x-nu -> x:  U_mu(x-mu)^dag U_nu(x-mu-nu)^dag = (U_nu(x-mu-nu) U_mu(x-mu))^dag
-    l = m3_dag(m3_mul(m3_load(U64, V, nu, xmm_mn), m3_load(U64, V, mu, xmm)));
-    l = m3_mul(l, m3_load(U64, V, mu, xmm_mn));
-    l = m3_mul(l, m3_load(U64, V, nu, xmn));
-#pragma unroll
-    for (int k = 0; k < 9; k++) Q.e[k] = cadd(Q.e[k], l.e[k]);
+    l = md_dag(md_mul(md_load(Udf, V, nu, xmm_mn), md_load(Udf, V, mu, xmm)));
+    l = md_mul(l, md_load(Udf, V, mu, xmm_mn));
+    l = md_mul(l, md_load(Udf, V, nu, xmn));
+    md_acc(Q, l);
     // x -> x-nu -> x+mu-nu -> x+mu -> x
-    l = m3_dmul(m3_load(U64, V, nu, xmn), m3_load(U64, V, mu, xmn));
-    l = m3_mul(l, m3_load(U64, V, nu, xpm_mn));
-    l = m3_mul_d(l, m3_load(U64, V, mu, x));
-#pragma unroll
-    for (int k = 0; k < 9; k++) Q.e[k] = cadd(Q.e[k], l.e[k]);
-    M3 F;
+    l = md_dmul(md_load(Udf, V, nu, xmn), md_load(Udf, V, mu, xmn));
+    l = md_mul(l, md_load(Udf, V, nu, xpm_mn));
+    l = md_mul_d(l, md_load(Udf, V, mu, x));
+    md_acc(Q, l);
 #pragma unroll
     for (int i = 0; i < 3; i++)
 #pragma unroll
         for (int j = 0; j < 3; j++) {
-            Z q = Q.e[i * 3 + j], qd = cconj(Q.e[j * 3 + i]);
-            F.e[i * 3 + j] = cscale(csub(q, qd), 0.125);
+            const CDF q = Q.e[i * 3 + j], qt = Q.e[j * 3 + i];
+            // (Q - Q^dag)_{ij} / 8 = (q - conj(qt)) / 8
+            F[2 * (i * 3 + j)] = df_to_double(df_scale2(df_sub(q.r, qt.r), 0.125f));
+            F[2 * (i * 3 + j) + 1] = df_to_double(df_scale2(df_add(q.i, qt.i), 0.125f));
         }
-    return F;
 }
 
 // One CTA builds the clover of 32 consecutive sites in three phases:
@@ -268,7 +275,7 @@ __device__ M3 field_strength(const Geom &g, const double2 *U64, long long x, con
 // in registers.
 constexpr int CL_SITES = 32;
 
-__global__ void __launch_bounds__(6 * CL_SITES) clover_build_kernel(Geom g, const double2 *U64, double kappa,
+__global__ void __launch_bounds__(6 * CL_SITES, 2) clover_build_kernel(Geom g, const float4 *Udf, double kappa,
                                                                      double csw, double2 *A64, float4 *A32,
                                                                      uint4 *A16, float *A16n)
 {
@@ -285,12 +292,10 @@ __global__ void __launch_bounds__(6 * CL_SITES) clover_build_kernel(Geom g, cons
         if (act) {
             int c[4];
             site_coords(g, x, c);
-            M3 F = field_strength(g, U64, x, c, mu, nu);
+            double F[18];
+            field_strength(g, Udf, x, c, mu, nu, F);
 #pragma unroll
-            for (int k = 0; k < 9; k++) {
-                sF[plane][2 * k][lane] = F.e[k].r;
-                sF[plane][2 * k + 1][lane] = F.e[k].i;
-            }
+            for (int k = 0; k < 18; k++) sF[plane][k][lane] = F[k];
         }
     }
     __syncthreads();
@@ -360,11 +365,11 @@ __global__ void __launch_bounds__(6 * CL_SITES) clover_build_kernel(Geom g, cons
     }
 }
 
-cudaError_t launch_clover_build(const Geom &g, const void *U64, double kappa, double csw, void *A64, void *A32,
+cudaError_t launch_clover_build(const Geom &g, const void *Udf, double kappa, double csw, void *A64, void *A32,
                                 void *A16, float *A16n, cudaStream_t st)
 {
     const unsigned nb = (unsigned)((g.V + CL_SITES - 1) / CL_SITES);
-    clover_build_kernel<<<nb, 6 * CL_SITES, 0, st>>>(g, (const double2 *)U64, kappa, csw, (double2 *)A64, (float4 *)A32,
+    clover_build_kernel<<<nb, 6 * CL_SITES, 0, st>>>(g, (const float4 *)Udf, kappa, csw, (double2 *)A64, (float4 *)A32,
                                             (uint4 *)A16, A16n);
     note_launch();
     return cudaGetLastError();

@@ -58,11 +58,11 @@ cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorVie
 
 // Gauge conversion; writes max(|U^dag U - 1|, |det U - 1|) as the bit
 // pattern of a non-negative double into *maxdev (device, zeroed first).
-cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void *U32, void *U16,
+cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void *U32, void *U16, void *Udf,
                                  unsigned long long *maxdev, cudaStream_t st);
 
-// Clover term from the FP64 links, stored in all three precisions.
-cudaError_t launch_clover_build(const Geom &g, const void *U64, double kappa, double csw, void *A64, void *A32,
+// Clover term from the double-float links, stored in all three precisions.
+cudaError_t launch_clover_build(const Geom &g, const void *Udf, double kappa, double csw, void *A64, void *A32,
                                 void *A16, float *A16n, cudaStream_t st);
 
 // BLAS of the Krylov solvers (K-B4 in the design notes).
@@ -144,8 +144,8 @@ struct qdd_lattice {
     qdd::Geom g;
     int device;
     cudaStream_t stream;
-    // links
-    void *U64, *U32, *U16;
+    // links (Udf: double-float copy, float4 (re.hi, re.lo, im.hi, im.lo) [4][9][V])
+    void *U64, *U32, *U16, *Udf;
     bool has_gauge;
     // clover cache
     bool clover_valid;
@@ -196,4 +196,6 @@ qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params 
 qdd_status solve_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, double kappa, double csw, double tol,
                       const qdd_solver_params *p, qdd_solve_info *info);
 void work_free(qdd_work *w);
+qdd_status autotune_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, double kappa, double csw,
+                         double tol, qdd_solver_params *p, int max_trials, double *best_ms);
 }  // namespace qdd

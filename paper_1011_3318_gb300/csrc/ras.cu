@@ -205,13 +205,34 @@ __device__ __forceinline__ void loc_site(const Geom &g, const DomainGeom &dg, in
 //        from a site uses the forward link of its neighbour, which is inside
 //        the domain whenever the hop is kept
 //   A    clover (only when SC): FP16 uint4[9][NT] + float[NT], FP32 float4[18][NT]
-template <int P> struct RasSmem {
-    static constexpr size_t link_bytes = P == P16 ? 96 : 192;
-    static constexpr size_t clover_bytes = P == P16 ? 148 : 288;
+//
+// Expanded variant (EXP): links are staged as full 18-real FP32 matrices
+// (float2[4][9][NT], third row rebuilt once) and the clover as FP32
+// (float4[18][NT], FP16 norm applied once), so that the MR iterations do no
+// conversions and no row rebuilds: 768 B per site, for small domains.
+template <int P, bool EXP> struct RasSmem {
+    static constexpr size_t link_bytes = EXP ? 288 : (P == P16 ? 96 : 192);
+    static constexpr size_t clover_bytes = EXP ? 288 : (P == P16 ? 148 : 288);
+    static constexpr size_t clover_data = EXP ? 288 : (P == P16 ? 144 : 288);
     static constexpr size_t bytes(int nt, bool sc) { return (size_t)nt * (192 + link_bytes + (sc ? clover_bytes : 0)); }
 };
 
-template <int P, int MU>
+template <int P, bool EXP>
+__device__ __forceinline__ void smem_link(LinkView sU, int NT, int mu, int l, C<float> (&U)[9])
+{
+    if constexpr (EXP) {
+        const float2 *p = (const float2 *)sU.d + mu * 9 * NT;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const float2 v = p[k * NT + l];
+            U[k] = {v.x, v.y};
+        }
+    } else {
+        load_link<P>(sU, NT, mu, l, U);
+    }
+}
+
+template <int P, bool EXP, int MU>
 __device__ __forceinline__ void smem_hops(const LocSite &s, int l, const float2 *srho, LinkView sU, float kappa,
                                           C<float> (&q)[12], int NT)
 {
@@ -220,29 +241,29 @@ __device__ __forceinline__ void smem_hops(const LocSite &s, int l, const float2 
         const int nf = (s.m & (1u << (16 + MU))) ? l - (e - 1) * ls : l + ls;
         C<float> n[12], U[9];
         ld_local(srho, NT, nf, n);
-        load_link<P>(sU, NT, MU, l, U);
+        smem_link<P, EXP>(sU, NT, MU, l, U);
         hop<MU, true>(q, n, U, (s.m & (1u << (8 + MU))) ? kappa : -kappa);
     }
     if (s.m & (1u << (4 + MU))) {
         const int nb = (s.m & (1u << (20 + MU))) ? l + (e - 1) * ls : l - ls;
         C<float> n[12], U[9];
         ld_local(srho, NT, nb, n);
-        load_link<P>(sU, NT, MU, nb, U);
+        smem_link<P, EXP>(sU, NT, MU, nb, U);
         hop<MU, false>(q, n, U, (s.m & (1u << (12 + MU))) ? kappa : -kappa);
     }
 }
 
-template <int P, int NT, bool SC>
+template <int P, int NT, bool SC, bool EXP>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(const RasArgs a)
 {
     if (a.sc && a.sc->status != S_RUN) return;
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ double red_sm[3 * 32 + 3];
+    __shared__ float wpart[3][NT / 32];
     float2 *srho = reinterpret_cast<float2 *>(smem);
     float2 *sv = srho + 12 * NT;
     unsigned char *sU = reinterpret_cast<unsigned char *>(sv + 12 * NT);
-    unsigned char *sA = sU + (size_t)NT * RasSmem<P>::link_bytes;
-    float *sAn = reinterpret_cast<float *>(sA + (size_t)NT * (P == P16 ? 144 : 288));
+    unsigned char *sA = sU + (size_t)NT * RasSmem<P, EXP>::link_bytes;
+    float *sAn = reinterpret_cast<float *>(sA + (size_t)NT * RasSmem<P, EXP>::clover_data);
     const LinkView lU{sU};
     const CloverView lA = SC ? CloverView{sA, sAn} : a.A;
     const long long V = a.g.V;
@@ -260,7 +281,20 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(const R
         st_local(srho, NT, l, r);
         st_local(sv, NT, l, z);
         if (act) {
-            if constexpr (P == P16) {
+            if constexpr (EXP) {
+#pragma unroll 1
+                for (int mu = 0; mu < 4; mu++) {
+                    C<float> U[9];
+                    load_link<P>(a.U, V, mu, s.x, U);
+#pragma unroll
+                    for (int k = 0; k < 9; k++) ((float2 *)sU)[(mu * 9 + k) * NT + l] = make_float2(U[k].r, U[k].i);
+                }
+                float av[72];
+                load_clover<P>(a.A, V, s.x, av);
+#pragma unroll
+                for (int k = 0; k < 18; k++)
+                    ((float4 *)sA)[k * NT + l] = make_float4(av[4 * k], av[4 * k + 1], av[4 * k + 2], av[4 * k + 3]);
+            } else if constexpr (P == P16) {
                 const uint2 *g = (const uint2 *)a.U.d;
 #pragma unroll
                 for (int k = 0; k < 12; k++) ((uint2 *)sU)[k * NT + l] = g[(long long)k * V + s.x];
@@ -293,19 +327,27 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(const R
                 C<float> own[12];
                 float av[72];
                 ld_local(srho, NT, l, own);
-                const float na = load_clover_u<P>(lA, SC ? (long long)NT : V, SC ? l : s.x, av);
-                clover_apply(av, own, q);
-                if constexpr (P == P16) {
+                if constexpr (EXP) {
+                    load_clover<P32>(CloverView{sA, nullptr}, NT, l, av);
+                    clover_apply(av, own, q);
+                } else {
+                    const float na = load_clover_u<P>(lA, SC ? (long long)NT : V, SC ? l : s.x, av);
+                    clover_apply(av, own, q);
+                    if constexpr (P == P16) {
 #pragma unroll
-                    for (int k = 0; k < 12; k++) q[k] = cscale(q[k], na);
+                        for (int k = 0; k < 12; k++) q[k] = cscale(q[k], na);
+                    }
                 }
             }
-            smem_hops<P, 0>(s, l, srho, lU, a.kappa, q, NT);
-            smem_hops<P, 1>(s, l, srho, lU, a.kappa, q, NT);
-            smem_hops<P, 2>(s, l, srho, lU, a.kappa, q, NT);
-            smem_hops<P, 3>(s, l, srho, lU, a.kappa, q, NT);
+            smem_hops<P, EXP, 0>(s, l, srho, lU, a.kappa, q, NT);
+            smem_hops<P, EXP, 1>(s, l, srho, lU, a.kappa, q, NT);
+            smem_hops<P, EXP, 2>(s, l, srho, lU, a.kappa, q, NT);
+            smem_hops<P, EXP, 3>(s, l, srho, lU, a.kappa, q, NT);
         }
-        double red[3];
+        // <q, rho> and |q|^2 over the domain in FP32: warp sums, then every
+        // thread adds the per-warp partials itself (one barrier; the next write
+        // of wpart comes after the next iteration's first barrier)
+        float red[3];
         {
             C<float> own[12];
             ld_local(srho, NT, l, own);
@@ -317,15 +359,31 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(const R
                 qi += t.i;
                 qq += q[k].r * q[k].r + q[k].i * q[k].i;
             }
-            red[0] = qr;
-            red[1] = qi;
-            red[2] = qq;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                qr += __shfl_xor_sync(0xffffffffu, qr, o);
+                qi += __shfl_xor_sync(0xffffffffu, qi, o);
+                qq += __shfl_xor_sync(0xffffffffu, qq, o);
+            }
+            if ((l & 31) == 0) {
+                wpart[0][l >> 5] = qr;
+                wpart[1][l >> 5] = qi;
+                wpart[2][l >> 5] = qq;
+            }
+            __syncthreads();
+            red[0] = red[1] = red[2] = 0.f;
+#pragma unroll
+            for (int w = 0; w < NT / 32; w++) {
+                red[0] += wpart[0][w];
+                red[1] += wpart[1][w];
+                red[2] += wpart[2][w];
+            }
         }
-        block_allsum<3>(red, red_sm);
-        // every thread is past the barriers of block_allsum: all reads of rho
-        // for this iteration are done and rho can be updated in place
-        if (red[2] > 0.0) {
-            const C<float> al = {(float)(red[0] / red[2]), (float)(red[1] / red[2])};
+        // every thread is past the barrier above: all reads of rho for this
+        // iteration are done and rho can be updated in place
+        if (red[2] > 0.f) {
+            const float inv = 1.0f / red[2];
+            const C<float> al = {red[0] * inv, red[1] * inv};
             C<float> own[12], vv[12];
             ld_local(srho, NT, l, own);
             ld_local(sv, NT, l, vv);
@@ -419,36 +477,32 @@ __global__ void __launch_bounds__(RAS_GMEM_NT) ras_gmem_kernel(const RasArgs a)
     }
 }
 
-template <int P, int NT, bool SC>
+template <int P, int NT, bool SC, bool EXP = false>
 static cudaError_t launch_smem(const RasArgs &a, cudaStream_t st)
 {
-    const size_t smem = RasSmem<P>::bytes(NT, SC);
-    cudaError_t e = cudaFuncSetAttribute(ras_smem_kernel<P, NT, SC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const size_t smem = RasSmem<P, EXP>::bytes(NT, SC || EXP);
+    cudaError_t e = cudaFuncSetAttribute(ras_smem_kernel<P, NT, SC || EXP, EXP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    ras_smem_kernel<P, NT, SC><<<a.dg.ndom, NT, smem, st>>>(a);
+    ras_smem_kernel<P, NT, SC || EXP, EXP><<<a.dg.ndom, NT, smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
 
-// The shared-memory kernel stages the clover too when it fits: always for
-// FP16 storage (111.6 KB per 256-site domain, two CTAs per SM), for FP32 only
-// up to 128 sites (at 256 sites the FP32 clover would leave one CTA per SM;
-// it is read through L1 instead).
+// Domains of up to 128 sites use the expanded staging (FP32 18-real links and
+// FP32 clover, 768 B per site); 256-site domains keep the links 12-real and,
+// for FP16 storage, the clover in FP16 (111.6 KB, two CTAs per SM); for FP32
+// storage the clover is read through L1 instead.
 template <int P>
 static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
 {
     const int n = a.dg.nloc;
-    if constexpr (P == P16) {
-        if (n <= 64) return launch_smem<P, 64, true>(a, st);
-        if (n <= 128) return launch_smem<P, 128, true>(a, st);
-        if (n <= 256) return launch_smem<P, 256, true>(a, st);
-        if (n <= RAS_SMEM_MAX_SITES) return launch_smem<P, 512, true>(a, st);
-    } else if constexpr (P == P32) {
-        if (n <= 64) return launch_smem<P, 64, true>(a, st);
-        if (n <= 128) return launch_smem<P, 128, true>(a, st);
-        if (n <= 256) return launch_smem<P, 256, false>(a, st);
-        if (n <= RAS_SMEM_MAX_SITES) return launch_smem<P, 512, false>(a, st);
+    if constexpr (P == P16 || P == P32) {
+        if (n <= 32) return launch_smem<P, 32, true, true>(a, st);
+        if (n <= 64) return launch_smem<P, 64, true, true>(a, st);
+        if (n <= 128) return launch_smem<P, 128, true, true>(a, st);
+        if (n <= 256) return launch_smem<P, 256, P == P16>(a, st);
+        if (n <= RAS_SMEM_MAX_SITES) return launch_smem<P, 512, P == P16>(a, st);
     }
     if (!a.scratch || a.slots < 1) return cudaErrorInvalidValue;
     const int grid = a.slots < a.dg.ndom ? a.slots : a.dg.ndom;

@@ -41,7 +41,7 @@ PREC = {"f64": QDD_F64, "f32": QDD_F32, "f16": QDD_F16, QDD_F64: QDD_F64, QDD_F3
 ABI = ("qdd_version", "qdd_last_error", "qdd_default_params", "qdd_create_lattice", "qdd_destroy_lattice",
        "qdd_load_gauge", "qdd_dslash", "qdd_ras_apply", "qdd_solve", "qdd_field_create", "qdd_field_destroy",
        "qdd_field_import", "qdd_field_export", "qdd_dslash_field", "qdd_kernel_launches", "qdd_set_profiling",
-       "qdd_profile_read", "qdd_measure_fma_peak", "qdd_ras_field_noalloc")
+       "qdd_profile_read", "qdd_measure_fma_peak", "qdd_ras_field_noalloc", "qdd_autotune")
 
 # Kernel classes of the per-class GPU timers (qdd_profile).
 KCLASS = ("dslash", "dslash_f64", "ras", "blas", "convert", "clover")
@@ -97,6 +97,8 @@ def _load():
     lib.qdd_set_profiling.argtypes = [P, ctypes.c_int]
     lib.qdd_profile_read.argtypes = [P, ctypes.POINTER(Profile), ctypes.c_int]
     lib.qdd_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.qdd_autotune.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                 ctypes.POINTER(SolverParams), ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.qdd_ras_field_noalloc.argtypes = [P, P, P, P, P, ctypes.c_double, ctypes.c_double,
                                           ctypes.POINTER(SolverParams)]
     for name in ABI:
@@ -225,6 +227,18 @@ def solve(lat: Lattice, phi, eta, kappa: float, c_sw: float, tol: float, params:
     out = {k: getattr(info, k) for k, _ in SolveInfo._fields_}
     out["return_status"] = st
     return out
+
+
+def autotune(lat: Lattice, eta, kappa: float, c_sw: float, tol: float, params: SolverParams | None = None,
+             max_trials: int = 40):
+    """Best RAS parameters for solving D phi = eta (timed whole solves);
+    returns (params, best_ms)."""
+    p = params if params is not None else default_params()
+    pe, _k = _ptr(eta)
+    best = ctypes.c_double()
+    _check(_lib.qdd_autotune(lat.handle, pe, float(kappa), float(c_sw), float(tol), ctypes.byref(p), int(max_trials),
+                             ctypes.byref(best)), "qdd_autotune")
+    return p, best.value
 
 
 class Field:

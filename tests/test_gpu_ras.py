@@ -23,6 +23,10 @@ CASES = [
     ((8, 8, 8, 8), (4, 4, 4, 4), 2),    # d = 4: extension wraps to the full extent
     ((8, 4, 4, 8), (4, 4, 4, 8), 0),    # t not decomposed: hops wrap inside the domain
     ((6, 4, 4, 8), (2, 2, 2, 2), 1),    # small blocks, ragged block count
+    ((8, 8, 8, 8), (2, 4, 4, 4), 0),    # 128-site domains: expanded FP32 staging
+    ((8, 8, 8, 8), (2, 2, 2, 2), 0),    # 16-site domains in 32-thread CTAs
+    ((8, 4, 4, 8), (2, 2, 4, 4), 0),    # 64-site domains
+    ((4, 4, 4, 8), (2, 2, 2, 8), 0),    # t not decomposed with expanded staging
 ]
 
 

@@ -92,3 +92,15 @@ def test_iteration_budget_returns_best_iterate(qdd, oracle_mod):
     assert info["return_status"] == qdd.QDD_ERR_NOT_CONVERGED
     r = op.true_residual(eta, phi)
     assert r < 1e-2 and abs(r - info["true_rel_residual"]) < 1e-6
+
+
+def test_autotune_returns_converging_parameters(qdd, oracle_mod):
+    """The tuner's choice solves the system to the tolerance, and its reported
+    time is that of a converged solve."""
+    op, lat, eta = setup(qdd, oracle_mod, (8, 8, 8, 8), 0.3, 0.12)
+    p, best = qdd.autotune(lat, eta, 0.12, 1.0, 1e-10, qdd.default_params(inner_prec="f16"), max_trials=12)
+    assert best > 0 and p.n_dominv >= 1 and p.n_ras >= 1
+    assert all(8 % b == 0 for b in p.block)
+    phi = np.empty_like(eta)
+    info = qdd.solve(lat, phi, eta, 0.12, 1.0, 1e-10, p)
+    assert info["status"] == 0 and op.true_residual(eta, phi) <= 1e-10
