@@ -24,8 +24,9 @@
  * always periodic.
  *
  * Canonical layouts (all FP64, interleaved complex: re, im):
- *   spinor  double[V][4 spin][3 colour][2]       (24 doubles per site)
- *   gauge   double[V][4 mu][3 row][3 col][2]     (72 doubles per site)
+ *   spinor  double[n_rhs][V][4 spin][3 colour][2] (24 doubles per site and
+ *           right-hand side; n_rhs as given to qdd_create_lattice)
+ *   gauge   double[V][4 mu][3 row][3 col][2]      (72 doubles per site)
  * Every double* argument may be a DEVICE pointer (cudaMalloc, torch CUDA
  * tensor) or a HOST pointer (pinned or pageable); the library detects which.
  * Host buffers are copied to and from the device inside the call, on the
@@ -67,6 +68,9 @@ typedef enum {
 } qdd_status;
 
 typedef enum { QDD_F64 = 0, QDD_F32 = 1, QDD_F16 = 2 } qdd_prec;
+
+/* Right-hand sides a lattice can hold (qdd_create_lattice n_rhs). */
+#define QDD_MAX_RHS 64
 
 /* Opaque lattice: geometry, boundary signs, links, clover cache, stream. */
 typedef struct qdd_lattice qdd_lattice;
@@ -114,11 +118,14 @@ const char *qdd_last_error(void);
 void qdd_default_params(qdd_solver_params *p);
 
 /* Creates a lattice of dims[4] = (Lx, Ly, Lz, Lt) sites with boundary signs
- * bc[4] (+1 / -1) on the current CUDA device.  n_rhs must be 1.
- * cuda_stream is a cudaStream_t (NULL: the legacy default stream); every
- * kernel of this lattice runs on it.  Allocates the lattice's device memory
- * (about 1.6 KB per site).  Errors: QDD_ERR_ARG for non-positive or odd-sized
- * nonsense dims, bc not +-1, n_rhs != 1; QDD_ERR_NOMEM. */
+ * bc[4] (+1 / -1) on the current CUDA device.  Every spinor the lattice
+ * works on holds n_rhs (1..QDD_MAX_RHS) right-hand sides, processed together
+ * by every kernel (links and clover are read once per site block for all of
+ * them).  cuda_stream is a cudaStream_t (NULL: the legacy default stream);
+ * every kernel of this lattice runs on it, and solves can be captured into
+ * CUDA graphs only on a non-default stream.  Allocates the lattice's device
+ * memory (about 2.2 KB per site).  Errors: QDD_ERR_ARG for extents outside
+ * 1..4096, bc not +-1, n_rhs out of range; QDD_ERR_NOMEM. */
 qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc[4], int n_rhs,
                               void *cuda_stream);
 
@@ -152,14 +159,29 @@ qdd_status qdd_ras_apply(qdd_lattice *lat, double *out, const double *in, double
                          const qdd_solver_params *params);
 
 /* Solves D phi = eta to |eta - D phi| / |eta| <= tol (the stopping rule of
- * Sec. 5), with the FP64 outer defect correction around the right-
- * preconditioned inner BiCGStab (Sec. 3, Eq. 3), or with the plain FP64
- * BiCGStab when params->inner_prec == QDD_F64.  params NULL: defaults.
- * phi is overwritten (no initial guess).  info may be NULL.  Returns QDD_OK,
+ * Sec. 5) for every right-hand side, with the FP64 outer defect correction
+ * around the right-preconditioned inner BiCGStab (Sec. 3, Eq. 3), or with the
+ * plain FP64 BiCGStab when params->inner_prec == QDD_F64.  params NULL:
+ * defaults.  phi is overwritten (no initial guess).  info may be NULL, else
+ * it receives n_rhs entries.  The inner iterations run as a CUDA graph when
+ * the lattice has a non-default stream and profiling is off.  Returns QDD_OK,
  * QDD_ERR_NOT_CONVERGED (phi = best iterate), QDD_ERR_BREAKDOWN or
- * QDD_ERR_NONFINITE. */
+ * QDD_ERR_NONFINITE (the first failure over the right-hand sides). */
 qdd_status qdd_solve(qdd_lattice *lat, double *phi, const double *eta, double kappa, double c_sw,
                      double tol, const qdd_solver_params *params, qdd_solve_info *info);
+
+/* Solves n independent systems, one per lattice (lattices of any shapes and
+ * right-hand-side counts, each with its own kappa[i] and c_sw[i], all to tol
+ * with the same params), in lockstep: the inner iterations of all lattices
+ * are captured into one CUDA graph forked across their streams (the lattices
+ * must then have distinct non-default streams; otherwise the same work is
+ * launched eagerly) and replayed until every right-hand side has converged.
+ * phi[i] and eta[i] are canonical spinors of lattice i (host or device);
+ * info (may be NULL) receives the entries of lattice 0's right-hand sides,
+ * then lattice 1's, and so on.  A lattice may appear only once. */
+qdd_status qdd_solve_batch(qdd_lattice *const *lats, double *const *phi, const double *const *eta, int n,
+                           const double *kappa, const double *c_sw, double tol,
+                           const qdd_solver_params *params, qdd_solve_info *info);
 
 /* Chooses the RAS parameters that minimise the time of a whole solve of
  * D phi = eta (the paper's parameter survey of Sec. 5, done by timing):

@@ -1,6 +1,7 @@
 // api.cu -- the C ABI declared in include/qdd.h.
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "lib.h"
 
@@ -91,10 +92,12 @@ bool is_device_ptr(const void *p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+size_t canon_bytes(const qdd_lattice *lat) { return (size_t)lat->g.V * lat->nrhs * 24 * sizeof(double); }
+
 qdd_status ensure_stage(qdd_lattice *lat, double **buf)
 {
     if (*buf) return QDD_OK;
-    cudaError_t e = cudaMalloc((void **)buf, (size_t)lat->g.V * 24 * sizeof(double));
+    cudaError_t e = cudaMalloc((void **)buf, canon_bytes(lat));
     if (e != cudaSuccess) {
         *buf = nullptr;
         return cuda_fail(e, "staging buffer");
@@ -111,8 +114,7 @@ qdd_status stage_in(qdd_lattice *lat, const double *src, double **buf, const dou
     }
     qdd_status st = ensure_stage(lat, buf);
     if (st != QDD_OK) return st;
-    cudaError_t e = cudaMemcpyAsync(*buf, src, (size_t)lat->g.V * 24 * sizeof(double), cudaMemcpyHostToDevice,
-                                    lat->stream);
+    cudaError_t e = cudaMemcpyAsync(*buf, src, canon_bytes(lat), cudaMemcpyHostToDevice, lat->stream);
     if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
     *dev = *buf;
     return QDD_OK;
@@ -135,8 +137,7 @@ qdd_status stage_out(qdd_lattice *lat, double *dst, double **buf, double **dev, 
 qdd_status finish_out(qdd_lattice *lat, double *dst, const double *dev, bool host)
 {
     if (!host) return QDD_OK;
-    cudaError_t e = cudaMemcpyAsync(dst, dev, (size_t)lat->g.V * 24 * sizeof(double), cudaMemcpyDeviceToHost,
-                                    lat->stream);
+    cudaError_t e = cudaMemcpyAsync(dst, dev, canon_bytes(lat), cudaMemcpyDeviceToHost, lat->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
     if (e != cudaSuccess) return cuda_fail(e, "device-to-host copy");
     return QDD_OK;
@@ -149,7 +150,7 @@ qdd_status io_fields(qdd_lattice *lat, int prec, SpinorView *fin, SpinorView *fo
 {
     for (int k = 0; k < 2; k++)
         if (!lat->io_d[prec][k]) {
-            qdd_status st = field_alloc(lat->g.V, prec, &lat->io_d[prec][k], &lat->io_n[prec][k]);
+            qdd_status st = field_alloc(lat->g.V * lat->nrhs, prec, &lat->io_d[prec][k], &lat->io_n[prec][k]);
             if (st != QDD_OK) return st;
         }
     *fin = SpinorView{lat->io_d[prec][0], lat->io_n[prec][0]};
@@ -206,8 +207,8 @@ qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc
         set_error("lattice too large");
         return QDD_ERR_ARG;
     }
-    if (n_rhs != 1) {
-        set_error("n_rhs must be 1");
+    if (n_rhs < 1 || n_rhs > QDD_MAX_RHS) {
+        set_error("n_rhs must be in 1..64");
         return QDD_ERR_ARG;
     }
     qdd_lattice *lat = new qdd_lattice();
@@ -219,6 +220,7 @@ qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc
     lat->g.stride[0] = 1;
     for (int mu = 1; mu < 4; mu++) lat->g.stride[mu] = lat->g.stride[mu - 1] * dims[mu - 1];
     lat->g.V = V;
+    lat->nrhs = n_rhs;
     lat->stream = (cudaStream_t)cuda_stream;
     cudaGetDevice(&lat->device);
     const int max_blocks = (int)(V / 64 + 4096);
@@ -228,8 +230,8 @@ qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc
     } allocs[] = {
         {&lat->U64, (size_t)V * 4 * 9 * 16}, {&lat->Udf, (size_t)V * 4 * 9 * 16}, {&lat->U32, (size_t)V * 4 * 3 * 16}, {&lat->U16, (size_t)V * 4 * 3 * 8},
         {&lat->A64, (size_t)V * 36 * 16},    {&lat->A32, (size_t)V * 18 * 16},    {&lat->A16, (size_t)V * 9 * 16},
-        {(void **)&lat->A16n, (size_t)V * 4}, {(void **)&lat->rs.partials, (size_t)max_blocks * 4 * sizeof(double)},
-        {(void **)&lat->rs.counter, 64},     {(void **)&lat->sc, sizeof(Scalars)},
+        {(void **)&lat->A16n, (size_t)V * 4}, {(void **)&lat->rs.partials, (size_t)max_blocks * 4 * sizeof(double) * n_rhs},
+        {(void **)&lat->rs.counter, (size_t)64 * n_rhs},     {(void **)&lat->sc, sizeof(Scalars) * n_rhs},
         {(void **)&lat->maxdev, 64},
     };
     for (auto &a : allocs) {
@@ -240,9 +242,9 @@ qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc
         }
     }
     lat->rs.max_blocks = max_blocks;
-    cudaError_t e = cudaMemset(lat->rs.counter, 0, 64);
-    if (e == cudaSuccess) e = cudaMemset(lat->sc, 0, sizeof(Scalars));
-    if (e == cudaSuccess) e = cudaMallocHost((void **)&lat->sc_host, sizeof(Scalars));
+    cudaError_t e = cudaMemset(lat->rs.counter, 0, (size_t)64 * n_rhs);
+    if (e == cudaSuccess) e = cudaMemset(lat->sc, 0, sizeof(Scalars) * n_rhs);
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&lat->sc_host, sizeof(Scalars) * n_rhs);
     if (e != cudaSuccess) {
         qdd_destroy_lattice(lat);
         return cuda_fail(e, "lattice initialisation");
@@ -323,13 +325,13 @@ qdd_status qdd_dslash(qdd_lattice *lat, double *out, const double *in, double ka
     if ((st = io_fields(lat, prec, &fin, &fout)) != QDD_OK) return st;
     const double *din;
     if ((st = stage_in(lat, in, &lat->stage_a, &din)) != QDD_OK) return st;
-    cudaError_t e = launch_import_spinor(lat->g, prec, fin, din, lat->stream);
+    cudaError_t e = launch_import_spinor(lat->g, prec, fin, din, lat->nrhs, lat->stream);
     if (e != cudaSuccess) return cuda_fail(e, "import");
     if ((st = run_dslash(lat, prec, EPI_D, fout, fin, SpinorView{nullptr, nullptr}, kappa, 0)) != QDD_OK) return st;
     double *dout;
     bool host;
     if ((st = stage_out(lat, out, &lat->stage_b, &dout, &host)) != QDD_OK) return st;
-    e = launch_export_spinor(lat->g, prec, dout, fout, lat->stream);
+    e = launch_export_spinor(lat->g, prec, dout, fout, lat->nrhs, lat->stream);
     if (e != cudaSuccess) return cuda_fail(e, "export");
     return finish_out(lat, out, dout, host);
 }
@@ -364,7 +366,7 @@ qdd_status qdd_ras_apply(qdd_lattice *lat, double *out, const double *in, double
     void *wd[2] = {nullptr, nullptr};
     float *wn[2] = {nullptr, nullptr};
     for (int k = 0; k < 2; k++)
-        if ((st = field_alloc(lat->g.V, prec, &wd[k], &wn[k])) != QDD_OK) {
+        if ((st = field_alloc(lat->g.V * lat->nrhs, prec, &wd[k], &wn[k])) != QDD_OK) {
             for (int j = 0; j < 2; j++) field_free(wd[j], wn[j]);
             return st;
         }
@@ -373,7 +375,7 @@ qdd_status qdd_ras_apply(qdd_lattice *lat, double *out, const double *in, double
     bool host = false;
     cudaError_t e = cudaSuccess;
     if ((st = stage_in(lat, in, &lat->stage_a, &din)) == QDD_OK) {
-        e = launch_import_spinor(lat->g, prec, fin, din, lat->stream);
+        e = launch_import_spinor(lat->g, prec, fin, din, lat->nrhs, lat->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "import");
     }
     if (st == QDD_OK)
@@ -381,7 +383,7 @@ qdd_status qdd_ras_apply(qdd_lattice *lat, double *out, const double *in, double
                               kappa, nullptr, nullptr);
     if (st == QDD_OK) st = stage_out(lat, out, &lat->stage_b, &dout, &host);
     if (st == QDD_OK) {
-        e = launch_export_spinor(lat->g, prec, dout, fout, lat->stream);
+        e = launch_export_spinor(lat->g, prec, dout, fout, lat->nrhs, lat->stream);
         if (e != cudaSuccess) st = cuda_fail(e, "export");
     }
     if (st == QDD_OK) st = finish_out(lat, out, dout, host);
@@ -422,6 +424,52 @@ qdd_status qdd_solve(qdd_lattice *lat, double *phi, const double *eta, double ka
     return res;
 }
 
+qdd_status qdd_solve_batch(qdd_lattice *const *lats, double *const *phi, const double *const *eta, int n,
+                           const double *kappa, const double *c_sw, double tol, const qdd_solver_params *params,
+                           qdd_solve_info *info)
+{
+    g_err.clear();
+    if (!lats || !phi || !eta || !kappa || !c_sw || n < 1 || !(tol > 0)) {
+        set_error("invalid argument");
+        return QDD_ERR_ARG;
+    }
+    qdd_solver_params p;
+    if (params) p = *params;
+    else qdd_default_params(&p);
+    if (!valid_prec(p.inner_prec) || p.max_inner < 1 || p.max_outer < 1 || p.n_ras < 1 || p.n_dominv < 0 ||
+        (p.inner_prec != QDD_F64 && !(p.inner_tol > 0 && p.inner_tol < 1))) {
+        set_error("invalid solver parameters");
+        return QDD_ERR_ARG;
+    }
+    std::vector<const double *> deta(n);
+    std::vector<double *> dphi(n);
+    std::vector<bool> host(n);
+    std::vector<qdd_solve_info *> infos(n, nullptr);
+    size_t off = 0;
+    qdd_status st;
+    for (int i = 0; i < n; i++) {
+        if (!lats[i] || !phi[i] || !eta[i]) {
+            set_error("null lattice or buffer in the batch");
+            return QDD_ERR_ARG;
+        }
+        bool h = false;
+        if ((st = stage_in(lats[i], eta[i], &lats[i]->stage_a, &deta[i])) != QDD_OK) return st;
+        if ((st = stage_out(lats[i], phi[i], &lats[i]->stage_b, &dphi[i], &h)) != QDD_OK) return st;
+        host[i] = h;
+        if (info) infos[i] = info + off;
+        off += lats[i]->nrhs;
+    }
+    qdd_status res = solve_batch_impl(lats, dphi.data(), deta.data(), n, kappa, c_sw, tol, &p,
+                                      info ? infos.data() : nullptr);
+    if (res != QDD_OK && res != QDD_ERR_NOT_CONVERGED && res != QDD_ERR_BREAKDOWN && res != QDD_ERR_NONFINITE)
+        return res;
+    std::string keep = g_err;
+    for (int i = 0; i < n; i++)
+        if ((st = finish_out(lats[i], phi[i], dphi[i], host[i])) != QDD_OK) return st;
+    g_err = keep;
+    return res;
+}
+
 qdd_status qdd_autotune(qdd_lattice *lat, const double *eta, double kappa, double c_sw, double tol,
                         qdd_solver_params *params, int max_trials, double *best_ms)
 {
@@ -453,7 +501,7 @@ qdd_status qdd_field_create(qdd_lattice *lat, qdd_prec prec, qdd_field **out)
     qdd_field *f = new qdd_field();
     f->lat = lat;
     f->prec = prec;
-    qdd_status st = field_alloc(lat->g.V, prec, &f->d, &f->n);
+    qdd_status st = field_alloc(lat->g.V * lat->nrhs, prec, &f->d, &f->n);
     if (st != QDD_OK) {
         delete f;
         return st;
@@ -482,7 +530,7 @@ qdd_status qdd_field_import(qdd_field *f, const double *src)
     const double *d;
     qdd_status st = stage_in(lat, src, &lat->stage_a, &d);
     if (st != QDD_OK) return st;
-    cudaError_t e = launch_import_spinor(lat->g, f->prec, f->view(), d, lat->stream);
+    cudaError_t e = launch_import_spinor(lat->g, f->prec, f->view(), d, lat->nrhs, lat->stream);
     return e == cudaSuccess ? QDD_OK : cuda_fail(e, "import");
 }
 
@@ -498,7 +546,7 @@ qdd_status qdd_field_export(const qdd_field *f, double *dst)
     bool host;
     qdd_status st = stage_out(lat, dst, &lat->stage_b, &d, &host);
     if (st != QDD_OK) return st;
-    cudaError_t e = launch_export_spinor(lat->g, f->prec, d, f->view(), lat->stream);
+    cudaError_t e = launch_export_spinor(lat->g, f->prec, d, f->view(), lat->nrhs, lat->stream);
     if (e != cudaSuccess) return cuda_fail(e, "export");
     return finish_out(lat, dst, d, host);
 }

@@ -48,9 +48,9 @@ qdd_status autotune_impl(qdd_lattice *lat, double *phi_dev, const double *eta_de
         DomainGeom dg;
         if (!domain_geom(lat->g, q.block, q.overlap, &dg, nullptr)) return;
         if (dg.nloc > RAS_SMEM_MAX_SITES) return;  // the general kernel is never the fastest
-        qdd_solve_info info;
+        std::vector<qdd_solve_info> info(lat->nrhs);
         const auto t0 = clk::now();
-        qdd_status s = solve_impl(lat, phi_dev, eta_dev, kappa, csw, tol, &q, &info);
+        qdd_status s = solve_impl(lat, phi_dev, eta_dev, kappa, csw, tol, &q, info.data());
         const double ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
         if (s != QDD_OK && s != QDD_ERR_NOT_CONVERGED && s != QDD_ERR_BREAKDOWN) {
             st = s;
@@ -63,9 +63,9 @@ qdd_status autotune_impl(qdd_lattice *lat, double *phi_dev, const double *eta_de
 
     // warm the clover cache and the work vectors so the first trial is not penalised
     {
-        qdd_solve_info info;
+        std::vector<qdd_solve_info> info(lat->nrhs);
         qdd_solver_params q = *p;
-        solve_impl(lat, phi_dev, eta_dev, kappa, csw, tol, &q, &info);
+        solve_impl(lat, phi_dev, eta_dev, kappa, csw, tol, &q, info.data());
     }
     const int nds[] = {1, 2, 3, 4, 6};
     const int nrs[] = {1, 2, 3};

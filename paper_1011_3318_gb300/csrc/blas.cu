@@ -22,14 +22,23 @@ __device__ __forceinline__ void zero12(C<T> (&a)[12])
 }
 
 template <int P, int OP>
-__global__ void __launch_bounds__(BLAS_NT) blas_kernel(const BlasArgs a)
+__global__ void __launch_bounds__(BLAS_NT) blas_kernel(BlasArgs a)
 {
     typedef typename RealOf<P>::T T;
     constexpr int NRED = (OP == B_INIT || OP == B_NORM || OP == B_RESTART) ? 1 : 0;
+    const int r = blockIdx.x % a.nrhs;
+    const unsigned bid = blockIdx.x / a.nrhs, nblk = gridDim.x / a.nrhs;
+    Scalars *sc = a.sc ? a.sc + r : nullptr;
     if constexpr (OP == B_P || OP == B_S) {
-        if (a.sc->status != S_RUN) return;
+        if (sc->status != S_RUN) return;
+    }
+    if constexpr (OP == B_RESTART) {
+        // restart only the right-hand sides whose BiCGStab broke down
+        if (sc->status != S_BREAK_RV && sc->status != S_BREAK_TT) return;
     }
     const long long V = a.V;
+#pragma unroll
+    for (int i = 0; i < 8; i++) a.f[i] = rhs_view<P>(a.f[i], V, r);
     double red[NRED > 0 ? NRED : 1];
 #pragma unroll
     for (int k = 0; k < (NRED > 0 ? NRED : 1); k++) red[k] = 0.0;
@@ -37,13 +46,13 @@ __global__ void __launch_bounds__(BLAS_NT) blas_kernel(const BlasArgs a)
     // coefficients read once per thread from the device scalars
     C<T> c1 = {0, 0}, c2 = {0, 0};
     if constexpr (OP == B_P) {
-        c1 = {(T)a.sc->beta.x, (T)a.sc->beta.y};
-        c2 = {(T)a.sc->omega.x, (T)a.sc->omega.y};
+        c1 = {(T)sc->beta.x, (T)sc->beta.y};
+        c2 = {(T)sc->omega.x, (T)sc->omega.y};
     } else if constexpr (OP == B_S) {
-        c1 = {(T)a.sc->alpha.x, (T)a.sc->alpha.y};
+        c1 = {(T)sc->alpha.x, (T)sc->alpha.y};
     }
 
-    for (long long x = (long long)blockIdx.x * BLAS_NT + threadIdx.x; x < V; x += (long long)gridDim.x * BLAS_NT) {
+    for (long long x = (long long)bid * BLAS_NT + threadIdx.x; x < V; x += (long long)nblk * BLAS_NT) {
         if constexpr (OP == B_INIT) {
             C<T> b[12], z[12];
             load_spinor<P>(a.f[0], V, x, b);
@@ -102,16 +111,17 @@ __global__ void __launch_bounds__(BLAS_NT) blas_kernel(const BlasArgs a)
     }
 
     if constexpr (NRED > 0) {
-        if (grid_sum<NRED>(red, a.rs)) {
-            Scalars *sc = a.sc;
+        if (grid_sum<NRED>(red, rs_partials(a.rs, r), rs_counter(a.rs, r), bid, nblk)) {
             if constexpr (OP == B_INIT) {
                 sc->rho = make_double2(red[0], 0.0);
                 sc->alpha = sc->omega = sc->beta = make_double2(1.0, 0.0);
                 sc->rr = red[0];
                 sc->rhat2 = red[0];
-                sc->tol2 = a.tol2_rel * red[0];
+                // relative tolerance^2: from the arguments, or per right-hand side from aux[7]
+                sc->tol2 = (a.tol2_rel >= 0 ? a.tol2_rel : sc->aux[7]) * red[0];
                 sc->iter = 0;
                 sc->status = isfinite(red[0]) ? (red[0] <= sc->tol2 ? S_CONVERGED : S_RUN) : S_NONFINITE;
+                if (!((a.active >> r) & 1ull)) sc->status = S_CONVERGED;
             } else if constexpr (OP == B_NORM) {
                 sc->aux[a.aux_slot] = red[0];
             } else if constexpr (OP == B_RESTART) {
@@ -127,15 +137,20 @@ __global__ void __launch_bounds__(BLAS_NT) blas_kernel(const BlasArgs a)
 // x += alpha phat + omega shat ; r = s - omega t ; then rho' = <rhat, r>,
 // |r|^2 and beta = (rho'/rho)(alpha/omega).  f = {x, phat, shat, r, s, t, rhat}.
 template <int P>
-__global__ void __launch_bounds__(BLAS_NT) bicg_xr_kernel(const BlasArgs a)
+__global__ void __launch_bounds__(BLAS_NT) bicg_xr_kernel(BlasArgs a)
 {
     typedef typename RealOf<P>::T T;
-    if (a.sc->status != S_RUN) return;
+    const int r = blockIdx.x % a.nrhs;
+    const unsigned bid = blockIdx.x / a.nrhs, nblk = gridDim.x / a.nrhs;
+    Scalars *sc = a.sc + r;
+    if (sc->status != S_RUN) return;
     const long long V = a.V;
-    const C<T> al = {(T)a.sc->alpha.x, (T)a.sc->alpha.y};
-    const C<T> om = {(T)a.sc->omega.x, (T)a.sc->omega.y};
+#pragma unroll
+    for (int i = 0; i < 8; i++) a.f[i] = rhs_view<P>(a.f[i], V, r);
+    const C<T> al = {(T)sc->alpha.x, (T)sc->alpha.y};
+    const C<T> om = {(T)sc->omega.x, (T)sc->omega.y};
     double red[3] = {0.0, 0.0, 0.0};
-    for (long long x = (long long)blockIdx.x * BLAS_NT + threadIdx.x; x < V; x += (long long)gridDim.x * BLAS_NT) {
+    for (long long x = (long long)bid * BLAS_NT + threadIdx.x; x < V; x += (long long)nblk * BLAS_NT) {
         C<T> xx[12], ph[12], sh[12];
         load_spinor<P>(a.f[0], V, x, xx);
         load_spinor<P>(a.f[1], V, x, ph);
@@ -161,8 +176,7 @@ __global__ void __launch_bounds__(BLAS_NT) bicg_xr_kernel(const BlasArgs a)
         red[1] += (double)di;
         red[2] += (double)n2;
     }
-    if (grid_sum<3>(red, a.rs)) {
-        Scalars *sc = a.sc;
+    if (grid_sum<3>(red, rs_partials(a.rs, r), rs_counter(a.rs, r), bid, nblk)) {
         const double2 rn = make_double2(red[0], red[1]);
         if (!isfinite(red[0]) || !isfinite(red[1]) || !isfinite(red[2])) {
             sc->status = S_NONFINITE;
@@ -188,7 +202,8 @@ static int blas_blocks(long long V, int max_blocks)
 template <int P>
 static cudaError_t launch_blas_p(int op, const BlasArgs &a, cudaStream_t st)
 {
-    const int nb = blas_blocks(a.V, a.rs.max_blocks);
+    if (a.nrhs < 1) return cudaErrorInvalidValue;
+    const int nb = blas_blocks(a.V, a.rs.max_blocks) * a.nrhs;
     switch (op) {
     case B_INIT: blas_kernel<P, B_INIT><<<nb, BLAS_NT, 0, st>>>(a); break;
     case B_P: blas_kernel<P, B_P><<<nb, BLAS_NT, 0, st>>>(a); break;
@@ -217,12 +232,16 @@ cudaError_t launch_blas(int prec, int op, const BlasArgs &a, cudaStream_t st)
 // ---------------------------------------------------------------- precision changes
 template <int PD>
 __global__ void __launch_bounds__(BLAS_NT) convert_scaled_kernel(long long V, SpinorView dst, SpinorView src64,
-                                                                 const Scalars *sc, int slot)
+                                                                 const Scalars *sc, int slot, int nrhs)
 {
     typedef typename RealOf<PD>::T T;
-    const double n2 = sc->aux[slot];
+    const int r = blockIdx.x % nrhs;
+    const unsigned bid = blockIdx.x / nrhs, nblk = gridDim.x / nrhs;
+    dst = rhs_view<PD>(dst, V, r);
+    src64 = rhs_view<P64>(src64, V, r);
+    const double n2 = sc[r].aux[slot];
     const double inv = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
-    for (long long x = (long long)blockIdx.x * BLAS_NT + threadIdx.x; x < V; x += (long long)gridDim.x * BLAS_NT) {
+    for (long long x = (long long)bid * BLAS_NT + threadIdx.x; x < V; x += (long long)nblk * BLAS_NT) {
         C<double> s[12];
         load_spinor<P64>(src64, V, x, s);
         C<T> d[12];
@@ -234,11 +253,15 @@ __global__ void __launch_bounds__(BLAS_NT) convert_scaled_kernel(long long V, Sp
 
 template <int PS>
 __global__ void __launch_bounds__(BLAS_NT) accum_scaled_kernel(long long V, SpinorView phi64, SpinorView xs,
-                                                               const Scalars *sc, int slot)
+                                                               const Scalars *sc, int slot, int nrhs)
 {
     typedef typename RealOf<PS>::T T;
-    const double sc_ = sqrt(sc->aux[slot]);
-    for (long long x = (long long)blockIdx.x * BLAS_NT + threadIdx.x; x < V; x += (long long)gridDim.x * BLAS_NT) {
+    const int r = blockIdx.x % nrhs;
+    const unsigned bid = blockIdx.x / nrhs, nblk = gridDim.x / nrhs;
+    phi64 = rhs_view<P64>(phi64, V, r);
+    xs = rhs_view<PS>(xs, V, r);
+    const double sc_ = sqrt(sc[r].aux[slot]);
+    for (long long x = (long long)bid * BLAS_NT + threadIdx.x; x < V; x += (long long)nblk * BLAS_NT) {
         C<double> p[12];
         C<T> e[12];
         load_spinor<P64>(phi64, V, x, p);
@@ -253,11 +276,15 @@ __global__ void __launch_bounds__(BLAS_NT) accum_scaled_kernel(long long V, Spin
 }
 
 template <int PD, int PS>
-__global__ void __launch_bounds__(BLAS_NT) convert_kernel(long long V, SpinorView dst, SpinorView src)
+__global__ void __launch_bounds__(BLAS_NT) convert_kernel(long long V, SpinorView dst, SpinorView src, int nrhs)
 {
     typedef typename RealOf<PS>::T TS;
     typedef typename RealOf<PD>::T TD;
-    for (long long x = (long long)blockIdx.x * BLAS_NT + threadIdx.x; x < V; x += (long long)gridDim.x * BLAS_NT) {
+    const int r = blockIdx.x % nrhs;
+    const unsigned bid = blockIdx.x / nrhs, nblk = gridDim.x / nrhs;
+    dst = rhs_view<PD>(dst, V, r);
+    src = rhs_view<PS>(src, V, r);
+    for (long long x = (long long)bid * BLAS_NT + threadIdx.x; x < V; x += (long long)nblk * BLAS_NT) {
         C<TS> s[12];
         load_spinor<PS>(src, V, x, s);
         C<TD> d[12];
@@ -268,43 +295,44 @@ __global__ void __launch_bounds__(BLAS_NT) convert_kernel(long long V, SpinorVie
 }
 
 cudaError_t launch_convert_scaled(long long V, int prec, SpinorView dst, SpinorView src64, const Scalars *sc,
-                                  int slot, cudaStream_t st)
+                                  int slot, int nrhs, cudaStream_t st)
 {
-    const int nb = blas_blocks(V, 1 << 30);
-    if (prec == P64) convert_scaled_kernel<P64><<<nb, BLAS_NT, 0, st>>>(V, dst, src64, sc, slot);
-    else if (prec == P32) convert_scaled_kernel<P32><<<nb, BLAS_NT, 0, st>>>(V, dst, src64, sc, slot);
-    else convert_scaled_kernel<P16><<<nb, BLAS_NT, 0, st>>>(V, dst, src64, sc, slot);
+    const int nb = blas_blocks(V, 1 << 30) * nrhs;
+    if (prec == P64) convert_scaled_kernel<P64><<<nb, BLAS_NT, 0, st>>>(V, dst, src64, sc, slot, nrhs);
+    else if (prec == P32) convert_scaled_kernel<P32><<<nb, BLAS_NT, 0, st>>>(V, dst, src64, sc, slot, nrhs);
+    else convert_scaled_kernel<P16><<<nb, BLAS_NT, 0, st>>>(V, dst, src64, sc, slot, nrhs);
     note_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_accum_scaled(long long V, int prec, SpinorView phi64, SpinorView x, const Scalars *sc, int slot,
-                                cudaStream_t st)
+                                int nrhs, cudaStream_t st)
 {
-    const int nb = blas_blocks(V, 1 << 30);
-    if (prec == P64) accum_scaled_kernel<P64><<<nb, BLAS_NT, 0, st>>>(V, phi64, x, sc, slot);
-    else if (prec == P32) accum_scaled_kernel<P32><<<nb, BLAS_NT, 0, st>>>(V, phi64, x, sc, slot);
-    else accum_scaled_kernel<P16><<<nb, BLAS_NT, 0, st>>>(V, phi64, x, sc, slot);
+    const int nb = blas_blocks(V, 1 << 30) * nrhs;
+    if (prec == P64) accum_scaled_kernel<P64><<<nb, BLAS_NT, 0, st>>>(V, phi64, x, sc, slot, nrhs);
+    else if (prec == P32) accum_scaled_kernel<P32><<<nb, BLAS_NT, 0, st>>>(V, phi64, x, sc, slot, nrhs);
+    else accum_scaled_kernel<P16><<<nb, BLAS_NT, 0, st>>>(V, phi64, x, sc, slot, nrhs);
     note_launch();
     return cudaGetLastError();
 }
 
 template <int PD>
-static cudaError_t convert_from(long long V, SpinorView dst, int ps, SpinorView src, int nb, cudaStream_t st)
+static cudaError_t convert_from(long long V, SpinorView dst, int ps, SpinorView src, int nb, int nrhs,
+                                cudaStream_t st)
 {
-    if (ps == P64) convert_kernel<PD, P64><<<nb, BLAS_NT, 0, st>>>(V, dst, src);
-    else if (ps == P32) convert_kernel<PD, P32><<<nb, BLAS_NT, 0, st>>>(V, dst, src);
-    else convert_kernel<PD, P16><<<nb, BLAS_NT, 0, st>>>(V, dst, src);
+    if (ps == P64) convert_kernel<PD, P64><<<nb, BLAS_NT, 0, st>>>(V, dst, src, nrhs);
+    else if (ps == P32) convert_kernel<PD, P32><<<nb, BLAS_NT, 0, st>>>(V, dst, src, nrhs);
+    else convert_kernel<PD, P16><<<nb, BLAS_NT, 0, st>>>(V, dst, src, nrhs);
     note_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_convert(long long V, int pd, SpinorView dst, int ps, SpinorView src, cudaStream_t st)
+cudaError_t launch_convert(long long V, int pd, SpinorView dst, int ps, SpinorView src, int nrhs, cudaStream_t st)
 {
-    const int nb = blas_blocks(V, 1 << 30);
-    if (pd == P64) return convert_from<P64>(V, dst, ps, src, nb, st);
-    if (pd == P32) return convert_from<P32>(V, dst, ps, src, nb, st);
-    return convert_from<P16>(V, dst, ps, src, nb, st);
+    const int nb = blas_blocks(V, 1 << 30) * nrhs;
+    if (pd == P64) return convert_from<P64>(V, dst, ps, src, nb, nrhs, st);
+    if (pd == P32) return convert_from<P32>(V, dst, ps, src, nb, nrhs, st);
+    return convert_from<P16>(V, dst, ps, src, nb, nrhs, st);
 }
 
 }  // namespace qdd

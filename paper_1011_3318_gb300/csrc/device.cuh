@@ -377,22 +377,24 @@ __device__ __forceinline__ void block_allsum(double (&v)[N], double *sm /* N * 3
     for (int k = 0; k < N; k++) v[k] = sm[N * 32 + k];
 }
 
-// Grid-wide sum by the last-block pattern: every block stores its partial
-// sums, and the block that arrives last adds them in block order (so the
-// result does not depend on scheduling) and returns true in thread 0 with
-// the totals in v.  No block waits for another.
+// Grid-wide sum by the last-block pattern over the nblk blocks that share
+// one reduction (one right-hand side): every block stores its partial sums,
+// and the block that arrives last adds them in block order (so the result
+// does not depend on scheduling) and returns true in thread 0 with the
+// totals in v.  No block waits for another.
 template <int N>
-__device__ __forceinline__ bool grid_sum(double (&v)[N], const ReduceScratch &rs)
+__device__ __forceinline__ bool grid_sum(double (&v)[N], double *partials, unsigned int *counter, unsigned bid,
+                                         unsigned nblk)
 {
     __shared__ double sm[N * 32];
     __shared__ int last;
     block_sum<N>(v, sm);
     if (threadIdx.x == 0) {
 #pragma unroll
-        for (int k = 0; k < N; k++) rs.partials[(long long)blockIdx.x * N + k] = v[k];
+        for (int k = 0; k < N; k++) partials[(long long)bid * N + k] = v[k];
         __threadfence();
-        unsigned t = atomicAdd(rs.counter, 1u);
-        last = (t == gridDim.x - 1);
+        unsigned t = atomicAdd(counter, 1u);
+        last = (t == nblk - 1);
     }
     __syncthreads();
     if (!last) return false;
@@ -400,16 +402,38 @@ __device__ __forceinline__ bool grid_sum(double (&v)[N], const ReduceScratch &rs
     double acc[N];
 #pragma unroll
     for (int k = 0; k < N; k++) acc[k] = 0.0;
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x)
+    for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x)
 #pragma unroll
-        for (int k = 0; k < N; k++) acc[k] += __ldcg(rs.partials + (long long)b * N + k);
+        for (int k = 0; k < N; k++) acc[k] += __ldcg(partials + (long long)b * N + k);
     block_sum<N>(acc, sm);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < N; k++) v[k] = acc[k];
-        *rs.counter = 0u;
+        *counter = 0u;
     }
     return threadIdx.x == 0;
+}
+
+// Reduction scratch of right-hand side r.
+__device__ __forceinline__ double *rs_partials(const ReduceScratch &rs, int r)
+{
+    return rs.partials + (long long)r * rs.max_blocks * 4;
+}
+__device__ __forceinline__ unsigned int *rs_counter(const ReduceScratch &rs, int r) { return rs.counter + r * 16; }
+
+// The field of right-hand side r inside a multi-RHS field (R vectors stored
+// one after the other, each in the planar layout of its precision).
+template <int P>
+__device__ __forceinline__ SpinorView rhs_view(SpinorView f, long long V, int r)
+{
+    if (!f.d) return f;
+    if constexpr (P == P64) f.d = (double2 *)f.d + (long long)r * 12 * V;
+    else if constexpr (P == P32) f.d = (float4 *)f.d + (long long)r * 6 * V;
+    else {
+        f.d = (uint4 *)f.d + (long long)r * 3 * V;
+        f.n = f.n + (long long)r * V;
+    }
+    return f;
 }
 
 // ---------------------------------------------------------------- scalars

@@ -11,6 +11,10 @@ static std::atomic<unsigned long long> g_launches{0};
 
 void note_launch(unsigned n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+void note_launch_adjust(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+
+unsigned long long launch_count() { return g_launches.load(); }
+
 Profiler::~Profiler()
 {
     for (auto &p : pending) {

@@ -38,15 +38,21 @@ __device__ __forceinline__ void hop_pair(const DslashArgs &a, long long x, const
 }
 
 template <int P, int EPI, int NT>
-__global__ void __launch_bounds__(NT) dslash_kernel(const DslashArgs a)
+__global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
 {
     typedef typename RealOf<P>::T T;
     constexpr int NRED = (EPI == EPI_XMY_NORM) ? 1 : (EPI == EPI_RV || EPI == EPI_TS) ? 3 : 0;
-    if constexpr (EPI == EPI_RV || EPI == EPI_TS) {
-        if (a.sc->status != S_RUN) return;
-    }
+    const int r = blockIdx.x % a.nrhs;
+    const unsigned bid = blockIdx.x / a.nrhs, nblk = gridDim.x / a.nrhs;
     const long long V = a.g.V;
-    const long long x = (long long)blockIdx.x * NT + threadIdx.x;
+    Scalars *sc = a.sc ? a.sc + r : nullptr;
+    if constexpr (EPI == EPI_RV || EPI == EPI_TS) {
+        if (sc->status != S_RUN) return;
+    }
+    a.out = rhs_view<P>(a.out, V, r);
+    a.in = rhs_view<P>(a.in, V, r);
+    a.y = rhs_view<P>(a.y, V, r);
+    const long long x = (long long)bid * NT + threadIdx.x;
     const bool active = x < V;
     double red[NRED > 0 ? NRED : 1] = {0.0};
 
@@ -104,8 +110,7 @@ __global__ void __launch_bounds__(NT) dslash_kernel(const DslashArgs a)
     }
 
     if constexpr (NRED > 0) {
-        if (grid_sum<NRED>(red, a.rs)) {
-            Scalars *sc = a.sc;
+        if (grid_sum<NRED>(red, rs_partials(a.rs, r), rs_counter(a.rs, r), bid, nblk)) {
             if constexpr (EPI == EPI_XMY_NORM) {
                 sc->aux[a.aux_slot] = red[0];
             } else if constexpr (EPI == EPI_RV) {
@@ -137,10 +142,11 @@ static cudaError_t launch_one(const DslashArgs &a, cudaStream_t st)
 {
     constexpr int NT = (P == P64) ? 128 : 256;
     const long long nb = (a.g.V + NT - 1) / NT;
+    if (a.nrhs < 1) return cudaErrorInvalidValue;
     if (EPI == EPI_XMY_NORM || EPI == EPI_RV || EPI == EPI_TS) {
         if (nb > a.rs.max_blocks) return cudaErrorInvalidConfiguration;
     }
-    dslash_kernel<P, EPI, NT><<<(unsigned)nb, NT, 0, st>>>(a);
+    dslash_kernel<P, EPI, NT><<<(unsigned)(nb * a.nrhs), NT, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }

@@ -27,7 +27,8 @@ __global__ void import_spinor_kernel(Geom g, SpinorView dst, const double *src)
     typedef typename RealOf<P>::T T;
     const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= g.V) return;
-    const double2 *s2 = reinterpret_cast<const double2 *>(src) + x * 12;
+    dst = rhs_view<P>(dst, g.V, blockIdx.y);
+    const double2 *s2 = reinterpret_cast<const double2 *>(src) + ((long long)blockIdx.y * g.V + x) * 12;
     C<T> s[12];
 #pragma unroll
     for (int k = 0; k < 12; k++) {
@@ -43,16 +44,18 @@ __global__ void export_spinor_kernel(Geom g, double *dst, SpinorView src)
     typedef typename RealOf<P>::T T;
     const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= g.V) return;
+    src = rhs_view<P>(src, g.V, blockIdx.y);
     C<T> s[12];
     load_spinor<P>(src, g.V, x, s);
-    double2 *d2 = reinterpret_cast<double2 *>(dst) + x * 12;
+    double2 *d2 = reinterpret_cast<double2 *>(dst) + ((long long)blockIdx.y * g.V + x) * 12;
 #pragma unroll
     for (int k = 0; k < 12; k++) d2[k] = make_double2((double)s[k].r, (double)s[k].i);
 }
 
-cudaError_t launch_import_spinor(const Geom &g, int prec, SpinorView dst, const double *src, cudaStream_t st)
+cudaError_t launch_import_spinor(const Geom &g, int prec, SpinorView dst, const double *src, int nrhs,
+                                 cudaStream_t st)
 {
-    const unsigned nb = (unsigned)((g.V + 255) / 256);
+    const dim3 nb((unsigned)((g.V + 255) / 256), (unsigned)nrhs);
     if (prec == P64) import_spinor_kernel<P64><<<nb, 256, 0, st>>>(g, dst, src);
     else if (prec == P32) import_spinor_kernel<P32><<<nb, 256, 0, st>>>(g, dst, src);
     else import_spinor_kernel<P16><<<nb, 256, 0, st>>>(g, dst, src);
@@ -60,9 +63,9 @@ cudaError_t launch_import_spinor(const Geom &g, int prec, SpinorView dst, const 
     return cudaGetLastError();
 }
 
-cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorView src, cudaStream_t st)
+cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorView src, int nrhs, cudaStream_t st)
 {
-    const unsigned nb = (unsigned)((g.V + 255) / 256);
+    const dim3 nb((unsigned)((g.V + 255) / 256), (unsigned)nrhs);
     if (prec == P64) export_spinor_kernel<P64><<<nb, 256, 0, st>>>(g, dst, src);
     else if (prec == P32) export_spinor_kernel<P32><<<nb, 256, 0, st>>>(g, dst, src);
     else export_spinor_kernel<P16><<<nb, 256, 0, st>>>(g, dst, src);

@@ -10,8 +10,11 @@
 
 namespace qdd {
 
-// Counts kernel launches of this library (qdd_kernel_launches()).
+// Counts kernel launches of this library (qdd_kernel_launches()); graph
+// replays add the launches their capture recorded.
 void note_launch(unsigned n = 1);
+void note_launch_adjust(long long n);
+unsigned long long launch_count();
 
 // Per-kernel-class GPU time, measured with CUDA events on the lattice stream
 // around every launch while profiling is on (qdd_set_profiling).
@@ -39,6 +42,10 @@ enum Epi {
     EPI_TS = 4,        // out = D in, omega = <out, y> / |out|^2 (BiCGStab, y = s)
 };
 
+// Every kernel works on nrhs right-hand sides at once: fields hold nrhs
+// vectors one after the other, sc points at nrhs Scalars, and the grid covers
+// (site block x right-hand side) with the right-hand side fastest, so that
+// consecutive CTAs read the same links and clover (served from L2).
 struct DslashArgs {
     Geom g;
     SpinorView out, in, y;
@@ -48,13 +55,16 @@ struct DslashArgs {
     ReduceScratch rs;
     Scalars *sc;
     int aux_slot;
+    int nrhs;
 };
 
 cudaError_t launch_dslash(int prec, int epi, const DslashArgs &a, cudaStream_t st);
 
 // Field conversions between the canonical FP64 layout and internal layouts.
-cudaError_t launch_import_spinor(const Geom &g, int prec, SpinorView dst, const double *src, cudaStream_t st);
-cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorView src, cudaStream_t st);
+// Canonical multi-RHS layout: double[nrhs][V][4][3][2].
+cudaError_t launch_import_spinor(const Geom &g, int prec, SpinorView dst, const double *src, int nrhs,
+                                 cudaStream_t st);
+cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorView src, int nrhs, cudaStream_t st);
 
 // Gauge conversion; writes max(|U^dag U - 1|, |det U - 1|) as the bit
 // pattern of a non-negative double into *maxdev (device, zeroed first).
@@ -73,6 +83,8 @@ struct BlasArgs {
     ReduceScratch rs;
     int aux_slot;
     double tol2_rel;   // bicg_init: tol^2
+    int nrhs;
+    unsigned long long active;  // B_INIT: bit r set = right-hand side r is solved (others start converged)
 };
 
 enum BlasOp {
@@ -89,14 +101,14 @@ enum BlasOp {
 cudaError_t launch_blas(int prec, int op, const BlasArgs &a, cudaStream_t st);
 
 // Precision changes around the inner solve (outer defect correction).
-// dst(prec) = src64 / sqrt(aux[slot])
+// dst(prec) = src64 / sqrt(aux[slot]) of each right-hand side
 cudaError_t launch_convert_scaled(long long V, int prec, SpinorView dst, SpinorView src64, const Scalars *sc,
-                                  int slot, cudaStream_t st);
-// phi64 += sqrt(aux[slot]) * x(prec)
+                                  int slot, int nrhs, cudaStream_t st);
+// phi64 += sqrt(aux[slot]) * x(prec) of each right-hand side
 cudaError_t launch_accum_scaled(long long V, int prec, SpinorView phi64, SpinorView x, const Scalars *sc, int slot,
-                                cudaStream_t st);
+                                int nrhs, cudaStream_t st);
 // dst(pd) = src(ps)
-cudaError_t launch_convert(long long V, int pd, SpinorView dst, int ps, SpinorView src, cudaStream_t st);
+cudaError_t launch_convert(long long V, int pd, SpinorView dst, int ps, SpinorView src, int nrhs, cudaStream_t st);
 
 // RAS block solve (Alg. 1 lines 4-8) over every domain.
 struct RasArgs {
@@ -113,6 +125,7 @@ struct RasArgs {
     const Scalars *sc;  // may be null; a non-running solver status skips the work
     float2 *scratch;    // general kernel: per-slot rho, q, v
     int slots;
+    int nrhs;
 };
 
 // Sites of an extended domain up to which the shared-memory kernel is used.
@@ -122,7 +135,7 @@ cudaError_t launch_ras_block(int prec, const RasArgs &a, cudaStream_t st);
 // The general (global-scratch) sweep kernel for any domain size, with the
 // scratch and slot count given in a (FP32 and FP16 only).
 cudaError_t launch_ras_block_gmem(int prec, const RasArgs &a, cudaStream_t st);
-size_t ras_scratch_bytes(const DomainGeom &dg, int slots);
+size_t ras_scratch_bytes(const DomainGeom &dg, int slots, int nrhs);
 int ras_default_slots();
 
 bool domain_geom(const Geom &g, const int block[4], int s, DomainGeom *dg, std::string *why);
@@ -142,6 +155,7 @@ struct qdd_work;
 
 struct qdd_lattice {
     qdd::Geom g;
+    int nrhs;  // right-hand sides held by every spinor field of this lattice
     int device;
     cudaStream_t stream;
     // links (Udf: double-float copy, float4 (re.hi, re.lo, im.hi, im.lo) [4][9][V])
@@ -195,6 +209,9 @@ qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params 
                             const Scalars *sc);
 qdd_status solve_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, double kappa, double csw, double tol,
                       const qdd_solver_params *p, qdd_solve_info *info);
+qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, const double *const *eta_dev, int n,
+                            const double *kappa, const double *csw, double tol, const qdd_solver_params *p,
+                            qdd_solve_info *const *infos);
 void work_free(qdd_work *w);
 qdd_status autotune_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, double kappa, double csw,
                          double tol, qdd_solver_params *p, int max_trials, double *best_ms);

@@ -122,7 +122,9 @@ extern "C" qdd_status qdd_ras_field_noalloc(qdd_lattice *lat, qdd_field *out, co
     ra.n_iter = params->n_dominv;
     ra.sc = nullptr;
     ra.scratch = reinterpret_cast<float2 *>(scratch);
-    ra.slots = (int)(fit < (size_t)dg.ndom ? fit : (size_t)dg.ndom);
+    ra.nrhs = lat->nrhs;
+    const size_t items = (size_t)dg.ndom * (size_t)lat->nrhs;
+    ra.slots = (int)(fit < items ? fit : items);
 
     DslashArgs da;
     memset(&da, 0, sizeof(da));
@@ -132,6 +134,7 @@ extern "C" qdd_status qdd_ras_field_noalloc(qdd_lattice *lat, qdd_field *out, co
     da.kappa = kappa;
     da.rs = lat->rs;
     da.sc = lat->sc;
+    da.nrhs = lat->nrhs;
 
     for (int j = 0; j < params->n_ras; j++) {
         const bool last = j == params->n_ras - 1;

@@ -25,6 +25,8 @@
 //  * ras_gmem_kernel: any domain size.  A persistent grid of `slots` CTAs
 //    loops over the domains; rho, q and v of the current domain live in a
 //    per-CTA slot of global scratch (L2-resident for moderate domains).
+#include <atomic>
+
 #include "device.cuh"
 #include "lib.h"
 
@@ -254,9 +256,13 @@ __device__ __forceinline__ void smem_hops(const LocSite &s, int l, const float2 
 }
 
 template <int P, int NT, bool SC, bool EXP>
-__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(const RasArgs a)
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(RasArgs a)
 {
-    if (a.sc && a.sc->status != S_RUN) return;
+    const int rr = blockIdx.x % a.nrhs, dom = blockIdx.x / a.nrhs;
+    if (a.sc && a.sc[rr].status != S_RUN) return;
+    a.in = rhs_view<P>(a.in, a.g.V, rr);
+    a.vout = rhs_view<P>(a.vout, a.g.V, rr);
+    a.acc = rhs_view<P>(a.acc, a.g.V, rr);
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float wpart[3][NT / 32];
     float2 *srho = reinterpret_cast<float2 *>(smem);
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(const R
     const long long V = a.g.V;
     const int l = threadIdx.x;
     LocSite s;
-    loc_site(a.g, a.dg, blockIdx.x, l, s);
+    loc_site(a.g, a.dg, dom, l, s);
     const bool act = s.m & M_ACT;
 
     // stage the projection P_{Omega'} r, and the domain's links and clover
@@ -406,15 +412,21 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(const R
 constexpr int RAS_GMEM_NT = 256;
 
 template <int P>
-__global__ void __launch_bounds__(RAS_GMEM_NT) ras_gmem_kernel(const RasArgs a)
+__global__ void __launch_bounds__(RAS_GMEM_NT) ras_gmem_kernel(const RasArgs a0)
 {
-    if (a.sc && a.sc->status != S_RUN) return;
     __shared__ double red_sm[3 * 32 + 3];
-    const int n = a.dg.nloc;
-    float2 *rho = a.scratch + (size_t)blockIdx.x * 36 * n;
+    const int n = a0.dg.nloc;
+    float2 *rho = a0.scratch + (size_t)blockIdx.x * 36 * n;
     float2 *q = rho + 12 * (size_t)n;
     float2 *vv = q + 12 * (size_t)n;
-    for (int dom = blockIdx.x; dom < a.dg.ndom; dom += gridDim.x) {
+    // work items are (domain, right-hand side) pairs, right-hand side fastest
+    for (int item = blockIdx.x; item < a0.dg.ndom * a0.nrhs; item += gridDim.x) {
+        const int dom = item / a0.nrhs, rr = item % a0.nrhs;
+        if (a0.sc && a0.sc[rr].status != S_RUN) continue;  // uniform over the CTA
+        RasArgs a = a0;
+        a.in = rhs_view<P>(a0.in, a0.g.V, rr);
+        a.vout = rhs_view<P>(a0.vout, a0.g.V, rr);
+        a.acc = rhs_view<P>(a0.acc, a0.g.V, rr);
         for (int l = threadIdx.x; l < n; l += RAS_GMEM_NT) {
             DomSite ds;
             dom_site(a.g, a.dg, dom, l, a.kappa, ds);
@@ -481,10 +493,18 @@ template <int P, int NT, bool SC, bool EXP = false>
 static cudaError_t launch_smem(const RasArgs &a, cudaStream_t st)
 {
     const size_t smem = RasSmem<P, EXP>::bytes(NT, SC || EXP);
-    cudaError_t e = cudaFuncSetAttribute(ras_smem_kernel<P, NT, SC || EXP, EXP>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    ras_smem_kernel<P, NT, SC || EXP, EXP><<<a.dg.ndom, NT, smem, st>>>(a);
+    // the shared-memory opt-in is set once per device (before any capture:
+    // the first launch of a solve is never captured)
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !((done.load() >> dev) & 1ull)) {
+        cudaError_t e = cudaFuncSetAttribute(ras_smem_kernel<P, NT, SC || EXP, EXP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) done.fetch_or(1ull << dev);
+    }
+    ras_smem_kernel<P, NT, SC || EXP, EXP><<<a.dg.ndom * a.nrhs, NT, smem, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
@@ -505,7 +525,8 @@ static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
         if (n <= RAS_SMEM_MAX_SITES) return launch_smem<P, 512, P == P16>(a, st);
     }
     if (!a.scratch || a.slots < 1) return cudaErrorInvalidValue;
-    const int grid = a.slots < a.dg.ndom ? a.slots : a.dg.ndom;
+    const long long items = (long long)a.dg.ndom * a.nrhs;
+    const int grid = a.slots < items ? a.slots : (int)items;
     ras_gmem_kernel<P><<<grid, RAS_GMEM_NT, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
@@ -514,6 +535,7 @@ static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
 cudaError_t launch_ras_block(int prec, const RasArgs &a, cudaStream_t st)
 {
     if (a.dg.ndom <= 0) return cudaSuccess;
+    if (a.nrhs < 1) return cudaErrorInvalidValue;
     switch (prec) {
     case P64: return launch_p<P64>(a, st);
     case P32: return launch_p<P32>(a, st);
@@ -526,7 +548,8 @@ template <int P>
 static cudaError_t launch_gmem_p(const RasArgs &a, cudaStream_t st)
 {
     if (!a.scratch || a.slots < 1) return cudaErrorInvalidValue;
-    const int grid = a.slots < a.dg.ndom ? a.slots : a.dg.ndom;
+    const long long items = (long long)a.dg.ndom * a.nrhs;
+    const int grid = a.slots < items ? a.slots : (int)items;
     ras_gmem_kernel<P><<<grid, RAS_GMEM_NT, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
@@ -535,6 +558,7 @@ static cudaError_t launch_gmem_p(const RasArgs &a, cudaStream_t st)
 cudaError_t launch_ras_block_gmem(int prec, const RasArgs &a, cudaStream_t st)
 {
     if (a.dg.ndom <= 0) return cudaSuccess;
+    if (a.nrhs < 1) return cudaErrorInvalidValue;
     switch (prec) {
     case P32: return launch_gmem_p<P32>(a, st);
     case P16: return launch_gmem_p<P16>(a, st);
@@ -544,10 +568,11 @@ cudaError_t launch_ras_block_gmem(int prec, const RasArgs &a, cudaStream_t st)
 
 int ras_default_slots() { return 2 * 152; }
 
-size_t ras_scratch_bytes(const DomainGeom &dg, int slots)
+size_t ras_scratch_bytes(const DomainGeom &dg, int slots, int nrhs)
 {
     if (dg.nloc <= RAS_SMEM_MAX_SITES) return 0;
-    const int s = slots < dg.ndom ? slots : dg.ndom;
+    const long long items = (long long)dg.ndom * nrhs;
+    const int s = slots < items ? slots : (int)items;
     return (size_t)s * 36 * (size_t)dg.nloc * sizeof(float2);
 }
 

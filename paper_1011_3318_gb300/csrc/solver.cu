@@ -2,17 +2,26 @@
 // defect correction around an inner BiCGStab in FP32 or FP16 storage, right-
 // preconditioned by K_RAS (Eq. 3, Alg. 1); and the plain FP64 BiCGStab.
 //
-// Every vector operation runs in a kernel of this library; the host only
-// enqueues launches on the lattice's stream and reads the solver status and
-// residual norms (a few dozen bytes) to decide when to stop.
+// A solve is a lockstep batch: one or more lattices, each with nrhs right-
+// hand sides, each lattice on its own stream with its own device scalars and
+// reduction scratch.  Every vector operation runs in a kernel of this
+// library; the host enqueues work and reads the solver status and residual
+// norms (a few dozen bytes per right-hand side) to decide when to stop.
+//
+// The inner iterations of all lattices are captured once into a CUDA graph
+// (forked across the lattices' streams) and replayed; kernels of a right-hand
+// side that has converged return at once, so the host can run several
+// iterations between status reads.  With per-kernel profiling on, or when a
+// lattice uses the legacy default stream, the same work is launched eagerly.
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "lib.h"
 
 struct qdd_work {
-    // FP64 outer vectors: eta, phi, r
+    // FP64 outer vectors: eta, phi, r (nrhs each)
     void *o_d[3] = {nullptr, nullptr, nullptr};
     // inner vectors per precision: b x r rhat p v s t phat shat rho_ras v_ras
     static constexpr int NIN = 12;
@@ -25,6 +34,9 @@ namespace qdd {
 
 enum { W_B, W_X, W_R, W_RHAT, W_P, W_V, W_S, W_T, W_PHAT, W_SHAT, W_RHO, W_VR };
 
+// aux slots of the device scalars
+enum { AUX_ETA2 = 0, AUX_R2 = 1, AUX_TOL2 = 7 };
+
 void work_free(qdd_work *w)
 {
     if (!w) return;
@@ -34,6 +46,8 @@ void work_free(qdd_work *w)
     delete w;
 }
 
+static long long nsites(const qdd_lattice *lat) { return lat->g.V * lat->nrhs; }
+
 static qdd_status ensure_outer(qdd_lattice *lat)
 {
     if (!lat->work) lat->work = new qdd_work();
@@ -41,7 +55,7 @@ static qdd_status ensure_outer(qdd_lattice *lat)
     for (int k = 0; k < 3; k++)
         if (!w->o_d[k]) {
             float *n = nullptr;
-            qdd_status st = field_alloc(lat->g.V, P64, &w->o_d[k], &n);
+            qdd_status st = field_alloc(nsites(lat), P64, &w->o_d[k], &n);
             if (st != QDD_OK) return st;
         }
     return QDD_OK;
@@ -53,7 +67,7 @@ static qdd_status ensure_inner(qdd_lattice *lat, int prec)
     qdd_work *w = lat->work;
     if (w->in_ok[prec]) return QDD_OK;
     for (int k = 0; k < qdd_work::NIN; k++) {
-        qdd_status st = field_alloc(lat->g.V, prec, &w->in_d[prec][k], &w->in_n[prec][k]);
+        qdd_status st = field_alloc(nsites(lat), prec, &w->in_d[prec][k], &w->in_n[prec][k]);
         if (st != QDD_OK) return st;
     }
     w->in_ok[prec] = true;
@@ -68,7 +82,7 @@ static SpinorView inner(qdd_lattice *lat, int prec, int k)
 static SpinorView outer(qdd_lattice *lat, int k) { return SpinorView{lat->work->o_d[k], nullptr}; }
 
 static qdd_status blas(qdd_lattice *lat, int prec, int op, std::initializer_list<SpinorView> fs, int aux_slot = 0,
-                       double tol2 = 0.0)
+                       double tol2 = 0.0, unsigned long long active = ~0ull)
 {
     BlasArgs a;
     memset(&a, 0, sizeof(a));
@@ -79,17 +93,27 @@ static qdd_status blas(qdd_lattice *lat, int prec, int op, std::initializer_list
     a.rs = lat->rs;
     a.aux_slot = aux_slot;
     a.tol2_rel = tol2;
+    a.nrhs = lat->nrhs;
+    a.active = active;
     ProfScope ps(lat, QDD_K_BLAS);
     cudaError_t e = launch_blas(prec, op, a, lat->stream);
     return e == cudaSuccess ? QDD_OK : cuda_fail(e, "blas kernel");
 }
 
-static qdd_status read_scalars(qdd_lattice *lat)
+// Copies the device scalars of every lattice to the host and waits.
+static qdd_status read_scalars(const std::vector<qdd_lattice *> &lats)
 {
-    cudaError_t e = cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, lat->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
-    if (e == cudaSuccess && lat->prof) lat->prof->drain();
-    return e == cudaSuccess ? QDD_OK : cuda_fail(e, "reading solver scalars");
+    for (qdd_lattice *lat : lats) {
+        cudaError_t e = cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(Scalars) * lat->nrhs, cudaMemcpyDeviceToHost,
+                                        lat->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "reading solver scalars");
+    }
+    for (qdd_lattice *lat : lats) {
+        cudaError_t e = cudaStreamSynchronize(lat->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "reading solver scalars");
+        if (lat->prof) lat->prof->drain();
+    }
+    return QDD_OK;
 }
 
 qdd_status run_dslash(qdd_lattice *lat, int prec, int epi, SpinorView out, SpinorView in, SpinorView y, double kappa,
@@ -107,6 +131,7 @@ qdd_status run_dslash(qdd_lattice *lat, int prec, int epi, SpinorView out, Spino
     a.rs = lat->rs;
     a.sc = lat->sc;
     a.aux_slot = aux_slot;
+    a.nrhs = lat->nrhs;
     ProfScope ps(lat, prec == P64 ? QDD_K_DSLASH_F64 : QDD_K_DSLASH);
     cudaError_t e = launch_dslash(prec, epi, a, lat->stream);
     return e == cudaSuccess ? QDD_OK : cuda_fail(e, "dslash kernel");
@@ -114,7 +139,7 @@ qdd_status run_dslash(qdd_lattice *lat, int prec, int epi, SpinorView out, Spino
 
 static qdd_status ensure_ras_scratch(qdd_lattice *lat, const DomainGeom &dg)
 {
-    const size_t need = ras_scratch_bytes(dg, ras_default_slots());
+    const size_t need = ras_scratch_bytes(dg, ras_default_slots(), lat->nrhs);
     if (need <= lat->ras_scratch_bytes) return QDD_OK;
     cudaFree(lat->ras_scratch);
     lat->ras_scratch = nullptr;
@@ -149,6 +174,7 @@ qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params 
     ra.sc = sc;
     ra.scratch = lat->ras_scratch;
     ra.slots = ras_default_slots();
+    ra.nrhs = lat->nrhs;
     for (int j = 0; j < p->n_ras; j++) {
         const bool last = j == p->n_ras - 1;
         ra.in = j == 0 ? in : rho;
@@ -170,167 +196,394 @@ qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params 
     return QDD_OK;
 }
 
-struct InnerResult {
-    int iters = 0;
-    int dv = 0;
-    int sweeps = 0;
-    int status = S_RUN;
+// ----------------------------------------------------------------- batch solve
+
+namespace {
+
+struct Member {
+    qdd_lattice *lat;
+    double *phi_dev;
+    const double *eta_dev;
+    double kappa, csw;
+    qdd_solve_info *info;  // nrhs entries (may be null)
+    bool use_ras;
+    DomainGeom dg;
+    std::vector<double> eta2, rr, best;
+    std::vector<int> stalls, restarted, done, result;
 };
 
-// BiCGStab (van der Vorst) on D x = b, right-preconditioned by K_RAS when
-// use_ras: D K chi = b, x = K chi (Eq. 3).  b is inner(W_B); x is inner(W_X).
-static qdd_status inner_bicgstab(qdd_lattice *lat, int prec, const qdd_solver_params *p, const DomainGeom *dg,
-                                 double kappa, double tol, int maxit, InnerResult *res)
+// One BiCGStab iteration (van der Vorst) of every right-hand side of a
+// lattice, right-preconditioned by K_RAS when use_ras: D K chi = b,
+// x = K chi (Eq. 3).
+qdd_status enqueue_iteration(Member &m, int prec, const qdd_solver_params *p)
 {
+    qdd_lattice *lat = m.lat;
     auto F = [&](int k) { return inner(lat, prec, k); };
-    qdd_status st = blas(lat, prec, B_INIT, {F(W_B), F(W_R), F(W_RHAT), F(W_X), F(W_P), F(W_V)}, 0, tol * tol);
-    if (st != QDD_OK) return st;
-    const bool ras = dg != nullptr;
-    const SpinorView phat = ras ? F(W_PHAT) : F(W_P);
-    const SpinorView shat = ras ? F(W_SHAT) : F(W_S);
-    const int chunk = lat->g.V >= (1 << 18) ? 2 : 6;
-    bool restarted = false;
-    int dv_ras = 0;
-    for (;;) {
-        for (int c = 0; c < chunk; c++) {
-            if ((st = blas(lat, prec, B_P, {F(W_P), F(W_R), F(W_V)})) != QDD_OK) return st;
-            if (ras && (st = ras_apply_fields(lat, prec, p, *dg, phat, F(W_P), F(W_RHO), F(W_VR), kappa, &dv_ras,
-                                              lat->sc)) != QDD_OK)
-                return st;
-            if ((st = run_dslash(lat, prec, EPI_RV, F(W_V), phat, F(W_RHAT), kappa, 0)) != QDD_OK) return st;
-            if ((st = blas(lat, prec, B_S, {F(W_S), F(W_R), F(W_V)})) != QDD_OK) return st;
-            if (ras && (st = ras_apply_fields(lat, prec, p, *dg, shat, F(W_S), F(W_RHO), F(W_VR), kappa, &dv_ras,
-                                              lat->sc)) != QDD_OK)
-                return st;
-            if ((st = run_dslash(lat, prec, EPI_TS, F(W_T), shat, F(W_S), kappa, 0)) != QDD_OK) return st;
-            if ((st = blas(lat, prec, B_XR, {F(W_X), phat, shat, F(W_R), F(W_S), F(W_T), F(W_RHAT)})) != QDD_OK)
-                return st;
-        }
-        if ((st = read_scalars(lat)) != QDD_OK) return st;
-        const Scalars &h = *lat->sc_host;
-        res->iters = h.iter;
-        if (h.status == S_CONVERGED || h.status == S_NONFINITE) break;
-        if (h.status == S_BREAK_RV || h.status == S_BREAK_TT) {
-            if (restarted) break;
-            restarted = true;
-            if ((st = blas(lat, prec, B_RESTART, {F(W_RHAT), F(W_R), F(W_P), F(W_V)})) != QDD_OK) return st;
-            continue;
-        }
-        if (h.iter >= maxit) break;
+    const SpinorView phat = m.use_ras ? F(W_PHAT) : F(W_P);
+    const SpinorView shat = m.use_ras ? F(W_SHAT) : F(W_S);
+    qdd_status st;
+    if ((st = blas(lat, prec, B_P, {F(W_P), F(W_R), F(W_V)})) != QDD_OK) return st;
+    if (m.use_ras &&
+        (st = ras_apply_fields(lat, prec, p, m.dg, phat, F(W_P), F(W_RHO), F(W_VR), m.kappa, nullptr, lat->sc)) !=
+            QDD_OK)
+        return st;
+    if ((st = run_dslash(lat, prec, EPI_RV, F(W_V), phat, F(W_RHAT), m.kappa, 0)) != QDD_OK) return st;
+    if ((st = blas(lat, prec, B_S, {F(W_S), F(W_R), F(W_V)})) != QDD_OK) return st;
+    if (m.use_ras &&
+        (st = ras_apply_fields(lat, prec, p, m.dg, shat, F(W_S), F(W_RHO), F(W_VR), m.kappa, nullptr, lat->sc)) !=
+            QDD_OK)
+        return st;
+    if ((st = run_dslash(lat, prec, EPI_TS, F(W_T), shat, F(W_S), m.kappa, 0)) != QDD_OK) return st;
+    return blas(lat, prec, B_XR, {F(W_X), phat, shat, F(W_R), F(W_S), F(W_T), F(W_RHAT)});
+}
+
+bool graph_capable(const std::vector<Member> &ms)
+{
+    for (size_t i = 0; i < ms.size(); i++) {
+        if (!ms[i].lat->stream) return false;
+        if (ms[i].lat->prof && ms[i].lat->prof->on) return false;
+        for (size_t j = 0; j < i; j++)
+            if (ms[j].lat->stream == ms[i].lat->stream) return false;
     }
-    res->status = lat->sc_host->status;
-    res->dv = 2 * res->iters + (ras ? 2 * res->iters * (p->n_ras - 1) : 0);
-    res->sweeps = ras ? 2 * res->iters * p->n_ras : 0;
+    return true;
+}
+
+// Enqueues `chunk` iterations of every member, eagerly or as one graph launch.
+struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;
+    std::vector<cudaEvent_t> events;  // fork/join inside the capture
+    std::vector<cudaEvent_t> pre;     // member streams -> launch stream, before each launch
+    cudaEvent_t post = nullptr;       // launch stream -> member streams, after each launch
+    ~IterGraph()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        for (cudaEvent_t e : events) cudaEventDestroy(e);
+        for (cudaEvent_t e : pre) cudaEventDestroy(e);
+        if (post) cudaEventDestroy(post);
+    }
+};
+
+qdd_status build_graph(std::vector<Member> &ms, int prec, const qdd_solver_params *p, int chunk, IterGraph &g)
+{
+    cudaStream_t s0 = ms[0].lat->stream;
+    g.events.resize(ms.size() + 1, nullptr);
+    g.pre.resize(ms.size(), nullptr);
+    for (auto &e : g.events)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "event");
+    for (auto &e : g.pre)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+            return cuda_fail(cudaGetLastError(), "event");
+    if (cudaEventCreateWithFlags(&g.post, cudaEventDisableTiming) != cudaSuccess)
+        return cuda_fail(cudaGetLastError(), "event");
+    const unsigned long long c0 = launch_count();
+    cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    qdd_status st = QDD_OK;
+    cudaEventRecord(g.events[0], s0);
+    for (size_t i = 1; i < ms.size(); i++) cudaStreamWaitEvent(ms[i].lat->stream, g.events[0], 0);
+    for (int c = 0; c < chunk && st == QDD_OK; c++)
+        for (Member &m : ms)
+            if (st == QDD_OK) st = enqueue_iteration(m, prec, p);
+    for (size_t i = 1; i < ms.size(); i++) {
+        cudaEventRecord(g.events[i], ms[i].lat->stream);
+        cudaStreamWaitEvent(s0, g.events[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(s0, &graph);
+    g.launches = launch_count() - c0;
+    note_launch_adjust(-(long long)g.launches);  // counted again on every replay
+    if (st != QDD_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    e = cudaGraphInstantiate(&g.exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiation");
     return QDD_OK;
+}
+
+}  // namespace
+
+qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, const double *const *eta_dev, int n,
+                            const double *kappa, const double *csw, double tol, const qdd_solver_params *p,
+                            qdd_solve_info *const *infos)
+{
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    double t_inner = 0.0;
+    const int prec = p->inner_prec;
+    const bool plain = prec == P64;
+    std::vector<Member> ms(n);
+    std::vector<qdd_lattice *> L(n);
+    qdd_status st;
+    for (int i = 0; i < n; i++) {
+        Member &m = ms[i];
+        m.lat = L[i] = lats[i];
+        m.phi_dev = phi_dev[i];
+        m.eta_dev = eta_dev[i];
+        m.kappa = kappa[i];
+        m.csw = csw[i];
+        m.info = infos ? infos[i] : nullptr;
+        m.use_ras = !plain && p->use_ras;
+        if (m.use_ras) {
+            std::string why;
+            if (!domain_geom(m.lat->g, p->block, p->overlap, &m.dg, &why)) {
+                set_error("invalid RAS blocking: " + why);
+                return QDD_ERR_ARG;
+            }
+        }
+        const int R = m.lat->nrhs;
+        m.eta2.assign(R, 0.0);
+        m.rr.assign(R, 0.0);
+        m.best.assign(R, 0.0);
+        m.stalls.assign(R, 0);
+        m.restarted.assign(R, 0);
+        m.done.assign(R, 0);
+        m.result.assign(R, QDD_ERR_NOT_CONVERGED);
+        if (m.info) memset(m.info, 0, sizeof(qdd_solve_info) * R);
+        for (int j = 0; j < i; j++)
+            if (L[j] == L[i]) {
+                set_error("a lattice appears twice in one batch");
+                return QDD_ERR_ARG;
+            }
+    }
+    for (Member &m : ms) {
+        qdd_lattice *lat = m.lat;
+        if ((st = ensure_clover(lat, m.kappa, m.csw)) != QDD_OK) return st;
+        if ((st = ensure_outer(lat)) != QDD_OK) return st;
+        if ((st = ensure_inner(lat, prec)) != QDD_OK) return st;
+        SpinorView eta = outer(lat, 0), phi = outer(lat, 1), r = outer(lat, 2);
+        cudaError_t e;
+        {
+            ProfScope ps(lat, QDD_K_CONVERT);
+            e = launch_import_spinor(lat->g, P64, eta, m.eta_dev, lat->nrhs, lat->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "import");
+        if ((st = blas(lat, P64, B_NORM, {eta}, AUX_ETA2)) != QDD_OK) return st;
+        if ((st = blas(lat, P64, B_COPY, {r, eta})) != QDD_OK) return st;
+        if ((st = blas(lat, P64, B_ZERO, {phi})) != QDD_OK) return st;
+        if ((st = blas(lat, P64, B_NORM, {r}, AUX_R2)) != QDD_OK) return st;
+    }
+    if ((st = read_scalars(L)) != QDD_OK) return st;
+    for (Member &m : ms)
+        for (int r = 0; r < m.lat->nrhs; r++) {
+            m.eta2[r] = m.lat->sc_host[r].aux[AUX_ETA2];
+            m.rr[r] = m.best[r] = m.lat->sc_host[r].aux[AUX_R2];
+            if (!std::isfinite(m.eta2[r])) {
+                m.done[r] = 1;
+                m.result[r] = QDD_ERR_NONFINITE;
+            }
+        }
+
+    const bool graphs = graph_capable(ms);
+    long long vmax = 0;
+    for (Member &m : ms) vmax = std::max(vmax, m.lat->g.V);
+    const int chunk = vmax >= (1 << 18) ? 2 : 4;
+    IterGraph graph;
+    bool have_graph = false;
+
+    for (int outer_it = 0;; outer_it++) {
+        // which right-hand sides still need an inner solve
+        bool any = false;
+        for (Member &m : ms)
+            for (int r = 0; r < m.lat->nrhs; r++) {
+                if (m.done[r]) continue;
+                const double rel = m.eta2[r] > 0 ? std::sqrt(m.rr[r] / m.eta2[r]) : 0.0;
+                if (!std::isfinite(rel)) {
+                    m.done[r] = 1;
+                    m.result[r] = QDD_ERR_NONFINITE;
+                } else if (rel <= tol) {
+                    m.done[r] = 1;
+                    m.result[r] = QDD_OK;
+                } else if (outer_it >= p->max_outer) {
+                    m.done[r] = 1;
+                } else {
+                    any = true;
+                }
+            }
+        if (!any) break;
+        const auto ti = clk::now();
+        for (Member &m : ms) {
+            qdd_lattice *lat = m.lat;
+            const int R = lat->nrhs;
+            unsigned long long active = 0;
+            for (int r = 0; r < R; r++) {
+                // tolerance of this inner solve relative to |r|: no further than
+                // the outer target needs, with a margin for the gap between the
+                // recursive and the true residual
+                double tol_in = m.rr[r] > 0 ? 0.5 * tol * std::sqrt(m.eta2[r] / m.rr[r]) : 1.0;
+                if (!plain && p->inner_tol > tol_in) tol_in = p->inner_tol;
+                lat->sc_host[r].aux[AUX_TOL2] = tol_in * tol_in;
+                if (!m.done[r]) active |= 1ull << r;
+                m.restarted[r] = 0;
+            }
+            for (int r = 0; r < R; r++) {
+                cudaError_t e = cudaMemcpyAsync(&lat->sc[r].aux[AUX_TOL2], &lat->sc_host[r].aux[AUX_TOL2],
+                                                sizeof(double), cudaMemcpyHostToDevice, lat->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "scalar upload");
+            }
+            cudaError_t e;
+            {
+                ProfScope ps(lat, QDD_K_CONVERT);
+                e = launch_convert_scaled(lat->g.V, prec, inner(lat, prec, W_B), outer(lat, 2), lat->sc, AUX_R2, R,
+                                          lat->stream);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "convert");
+            auto F = [&](int k) { return inner(lat, prec, k); };
+            if ((st = blas(lat, prec, B_INIT, {F(W_B), F(W_R), F(W_RHAT), F(W_X), F(W_P), F(W_V)}, 0, -1.0, active)) !=
+                QDD_OK)
+                return st;
+        }
+        // inner iterations of every lattice until no right-hand side runs
+        for (;;) {
+            if (graphs) {
+                if (!have_graph) {
+                    // one eager iteration first: it sets kernel attributes and
+                    // allocates scratch outside the capture
+                    for (Member &m : ms)
+                        if ((st = enqueue_iteration(m, prec, p)) != QDD_OK) return st;
+                    if ((st = build_graph(ms, prec, p, chunk, graph)) != QDD_OK) return st;
+                    have_graph = true;
+                } else {
+                    // the graph runs on the first lattice's stream: order it after
+                    // the work already queued on the other lattices' streams, and
+                    // their next work after it
+                    cudaStream_t s0 = ms[0].lat->stream;
+                    for (size_t i = 1; i < ms.size(); i++) {
+                        cudaEventRecord(graph.pre[i], ms[i].lat->stream);
+                        cudaStreamWaitEvent(s0, graph.pre[i], 0);
+                    }
+                    cudaError_t e = cudaGraphLaunch(graph.exec, s0);
+                    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+                    note_launch_adjust((long long)graph.launches);
+                    cudaEventRecord(graph.post, s0);
+                    for (size_t i = 1; i < ms.size(); i++) cudaStreamWaitEvent(ms[i].lat->stream, graph.post, 0);
+                }
+            } else {
+                for (int c = 0; c < chunk; c++)
+                    for (Member &m : ms)
+                        if ((st = enqueue_iteration(m, prec, p)) != QDD_OK) return st;
+            }
+            if ((st = read_scalars(L)) != QDD_OK) return st;
+            bool running = false;
+            for (Member &m : ms) {
+                qdd_lattice *lat = m.lat;
+                bool restart = false;
+                for (int r = 0; r < lat->nrhs; r++) {
+                    const Scalars &h = lat->sc_host[r];
+                    if (h.status == S_RUN) {
+                        if (h.iter >= p->max_inner) {
+                            // out of inner iterations: stop this right-hand side
+                            const int conv = S_CONVERGED;
+                            cudaMemcpyAsync(&lat->sc[r].status, &conv, sizeof(int), cudaMemcpyHostToDevice,
+                                            lat->stream);
+                            cudaStreamSynchronize(lat->stream);
+                        } else {
+                            running = true;
+                        }
+                    } else if (h.status == S_BREAK_RV || h.status == S_BREAK_TT) {
+                        if (!m.restarted[r]) {
+                            m.restarted[r] = 1;
+                            restart = true;
+                            running = true;
+                        }
+                    }
+                }
+                if (restart) {
+                    auto F = [&](int k) { return inner(lat, prec, k); };
+                    if ((st = blas(lat, prec, B_RESTART, {F(W_RHAT), F(W_R), F(W_P), F(W_V)})) != QDD_OK) return st;
+                }
+            }
+            if (!running) break;
+        }
+        t_inner += std::chrono::duration<double, std::milli>(clk::now() - ti).count();
+        // phi += |r| x ; r = eta - D phi ; |r|^2
+        for (Member &m : ms) {
+            qdd_lattice *lat = m.lat;
+            const int R = lat->nrhs;
+            for (int r = 0; r < R; r++) {
+                if (m.done[r]) continue;
+                const Scalars &h = lat->sc_host[r];
+                if (m.info) {
+                    m.info[r].inner_iters += h.iter;
+                    m.info[r].dv_count += 2 * h.iter + (m.use_ras ? 2 * h.iter * (p->n_ras - 1) : 0);
+                    m.info[r].ras_sweeps += m.use_ras ? 2 * h.iter * p->n_ras : 0;
+                    m.info[r].outer_iters++;
+                }
+                if (h.status == S_NONFINITE) {
+                    m.done[r] = 1;
+                    m.result[r] = QDD_ERR_NONFINITE;
+                }
+            }
+            cudaError_t e;
+            {
+                ProfScope ps(lat, QDD_K_CONVERT);
+                e = launch_accum_scaled(lat->g.V, prec, outer(lat, 1), inner(lat, prec, W_X), lat->sc, AUX_R2, R,
+                                        lat->stream);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "accumulate");
+            if ((st = run_dslash(lat, P64, EPI_XMY_NORM, outer(lat, 2), outer(lat, 1), outer(lat, 0), m.kappa,
+                                 AUX_R2)) != QDD_OK)
+                return st;
+        }
+        if ((st = read_scalars(L)) != QDD_OK) return st;
+        for (Member &m : ms)
+            for (int r = 0; r < m.lat->nrhs; r++) {
+                if (m.done[r]) continue;
+                m.rr[r] = m.lat->sc_host[r].aux[AUX_R2];
+                if (m.rr[r] < 0.5 * m.best[r]) {
+                    m.best[r] = m.rr[r];
+                    m.stalls[r] = 0;
+                } else if (++m.stalls[r] >= 3) {
+                    m.done[r] = 1;
+                    const int s = m.lat->sc_host[r].status;
+                    m.result[r] = (s == S_BREAK_RV || s == S_BREAK_TT) ? QDD_ERR_BREAKDOWN : QDD_ERR_NOT_CONVERGED;
+                }
+            }
+    }
+    qdd_status result = QDD_OK;
+    for (Member &m : ms) {
+        qdd_lattice *lat = m.lat;
+        cudaError_t e;
+        {
+            ProfScope ps(lat, QDD_K_CONVERT);
+            e = launch_export_spinor(lat->g, P64, m.phi_dev, outer(lat, 1), lat->nrhs, lat->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "export");
+    }
+    for (Member &m : ms) {
+        cudaError_t e = cudaStreamSynchronize(m.lat->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "solve");
+    }
+    const double total = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
+    for (Member &m : ms)
+        for (int r = 0; r < m.lat->nrhs; r++) {
+            if (m.result[r] != QDD_OK && result == QDD_OK) result = (qdd_status)m.result[r];
+            if (m.info) {
+                m.info[r].status = m.result[r];
+                m.info[r].true_rel_residual = m.eta2[r] > 0 ? std::sqrt(m.rr[r] / m.eta2[r]) : 0.0;
+                m.info[r].t_total_ms = total;
+                m.info[r].t_inner_ms = t_inner;
+                m.info[r].t_outer_ms = total - t_inner;
+            }
+        }
+    if (result == QDD_ERR_NOT_CONVERGED) set_error("solve did not reach the tolerance");
+    else if (result == QDD_ERR_BREAKDOWN) set_error("BiCGStab broke down");
+    else if (result == QDD_ERR_NONFINITE) set_error("non-finite residual");
+    return result;
 }
 
 qdd_status solve_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, double kappa, double csw, double tol,
                       const qdd_solver_params *p, qdd_solve_info *info)
 {
-    using clk = std::chrono::steady_clock;
-    const auto t0 = clk::now();
-    double t_inner = 0.0;
-    qdd_solve_info inf;
-    memset(&inf, 0, sizeof(inf));
-    const int prec = p->inner_prec;
-    const bool plain = prec == P64;
-    const bool use_ras = !plain && p->use_ras;
-    DomainGeom dg;
-    if (use_ras) {
-        std::string why;
-        if (!domain_geom(lat->g, p->block, p->overlap, &dg, &why)) {
-            set_error("invalid RAS blocking: " + why);
-            return QDD_ERR_ARG;
-        }
-    }
-    qdd_status st;
-    if ((st = ensure_clover(lat, kappa, csw)) != QDD_OK) return st;
-    if ((st = ensure_outer(lat)) != QDD_OK) return st;
-    if ((st = ensure_inner(lat, prec)) != QDD_OK) return st;
-
-    const Geom &g = lat->g;
-    SpinorView eta = outer(lat, 0), phi = outer(lat, 1), r = outer(lat, 2);
-    cudaError_t e;
-    {
-        ProfScope ps(lat, QDD_K_CONVERT);
-        e = launch_import_spinor(g, P64, eta, eta_dev, lat->stream);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "import");
-    if ((st = blas(lat, P64, B_NORM, {eta}, 0)) != QDD_OK) return st;   // |eta|^2 -> aux[0]
-    if ((st = blas(lat, P64, B_COPY, {r, eta})) != QDD_OK) return st;
-    if ((st = blas(lat, P64, B_ZERO, {phi})) != QDD_OK) return st;
-    if ((st = blas(lat, P64, B_NORM, {r}, 1)) != QDD_OK) return st;     // |r|^2 -> aux[1]
-    if ((st = read_scalars(lat)) != QDD_OK) return st;
-    const double eta2 = lat->sc_host->aux[0];
-    double rr = lat->sc_host->aux[1];
-    if (!std::isfinite(eta2)) {
-        set_error("source has non-finite entries");
-        return QDD_ERR_NONFINITE;
-    }
-    qdd_status result = QDD_ERR_NOT_CONVERGED;
-    int stalls = 0;
-    double best = rr;
-    for (;;) {
-        const double rel = eta2 > 0 ? std::sqrt(rr / eta2) : 0.0;
-        inf.true_rel_residual = rel;
-        if (!std::isfinite(rel)) { result = QDD_ERR_NONFINITE; break; }
-        if (rel <= tol) { result = QDD_OK; break; }
-        if (inf.outer_iters >= p->max_outer) break;
-        // tolerance of this inner solve relative to |r|: do not solve further
-        // than the outer target needs, with a margin for the gap between the
-        // recursive and the true residual
-        double tol_in = 0.5 * tol * std::sqrt(eta2 / rr);
-        if (!plain && p->inner_tol > tol_in) tol_in = p->inner_tol;
-        const auto ti = clk::now();
-        {
-            ProfScope ps(lat, QDD_K_CONVERT);
-            e = launch_convert_scaled(g.V, prec, inner(lat, prec, W_B), r, lat->sc, 1, lat->stream);
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "convert");
-        InnerResult ir;
-        if ((st = inner_bicgstab(lat, prec, p, use_ras ? &dg : nullptr, kappa, tol_in, p->max_inner, &ir)) !=
-            QDD_OK)
-            return st;
-        t_inner += std::chrono::duration<double, std::milli>(clk::now() - ti).count();
-        inf.inner_iters += ir.iters;
-        inf.dv_count += ir.dv;
-        inf.ras_sweeps += ir.sweeps;
-        inf.outer_iters++;
-        if (ir.status == S_NONFINITE) { result = QDD_ERR_NONFINITE; break; }
-        // phi += |r| x ; r = eta - D phi ; |r|^2 -> aux[1]
-        {
-            ProfScope ps(lat, QDD_K_CONVERT);
-            e = launch_accum_scaled(g.V, prec, phi, inner(lat, prec, W_X), lat->sc, 1, lat->stream);
-        }
-        if (e != cudaSuccess) return cuda_fail(e, "accumulate");
-        if ((st = run_dslash(lat, P64, EPI_XMY_NORM, r, phi, eta, kappa, 1)) != QDD_OK) return st;
-        if ((st = read_scalars(lat)) != QDD_OK) return st;
-        rr = lat->sc_host->aux[1];
-        if (rr < 0.5 * best) { best = rr; stalls = 0; }
-        else if (++stalls >= 3) {
-            result = (ir.status == S_BREAK_RV || ir.status == S_BREAK_TT) ? QDD_ERR_BREAKDOWN : QDD_ERR_NOT_CONVERGED;
-            inf.true_rel_residual = eta2 > 0 ? std::sqrt(rr / eta2) : 0.0;
-            break;
-        }
-    }
-    {
-        ProfScope ps(lat, QDD_K_CONVERT);
-        e = launch_export_spinor(g, P64, phi_dev, phi, lat->stream);
-    }
-    if (e != cudaSuccess) return cuda_fail(e, "export");
-    e = cudaStreamSynchronize(lat->stream);
-    if (e != cudaSuccess) return cuda_fail(e, "solve");
-    inf.status = result;
-    inf.t_total_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
-    inf.t_inner_ms = t_inner;
-    inf.t_outer_ms = inf.t_total_ms - t_inner;
-    if (info) *info = inf;
-    if (result != QDD_OK) {
-        if (result == QDD_ERR_NOT_CONVERGED) set_error("solve did not reach the tolerance");
-        else if (result == QDD_ERR_BREAKDOWN) set_error("BiCGStab broke down");
-        else set_error("non-finite residual");
-    }
-    return result;
+    qdd_lattice *lats[1] = {lat};
+    double *phis[1] = {phi_dev};
+    const double *etas[1] = {eta_dev};
+    qdd_solve_info *infos[1] = {info};
+    return solve_batch_impl(lats, phis, etas, 1, &kappa, &csw, tol, p, info ? infos : nullptr);
 }
 
 }  // namespace qdd

@@ -41,7 +41,7 @@ PREC = {"f64": QDD_F64, "f32": QDD_F32, "f16": QDD_F16, QDD_F64: QDD_F64, QDD_F3
 ABI = ("qdd_version", "qdd_last_error", "qdd_default_params", "qdd_create_lattice", "qdd_destroy_lattice",
        "qdd_load_gauge", "qdd_dslash", "qdd_ras_apply", "qdd_solve", "qdd_field_create", "qdd_field_destroy",
        "qdd_field_import", "qdd_field_export", "qdd_dslash_field", "qdd_kernel_launches", "qdd_set_profiling",
-       "qdd_profile_read", "qdd_measure_fma_peak", "qdd_ras_field_noalloc", "qdd_autotune")
+       "qdd_profile_read", "qdd_measure_fma_peak", "qdd_ras_field_noalloc", "qdd_autotune", "qdd_solve_batch")
 
 # Kernel classes of the per-class GPU timers (qdd_profile).
 KCLASS = ("dslash", "dslash_f64", "ras", "blas", "convert", "clover")
@@ -97,6 +97,9 @@ def _load():
     lib.qdd_set_profiling.argtypes = [P, ctypes.c_int]
     lib.qdd_profile_read.argtypes = [P, ctypes.POINTER(Profile), ctypes.c_int]
     lib.qdd_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.qdd_solve_batch.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
+                                    ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo)]
     lib.qdd_autotune.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  ctypes.POINTER(SolverParams), ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.qdd_ras_field_noalloc.argtypes = [P, P, P, P, P, ctypes.c_double, ctypes.c_double,
@@ -158,11 +161,13 @@ def _stream_handle(stream):
 class Lattice:
     """Handle of a qdd_lattice (create with create_lattice)."""
 
-    def __init__(self, handle, dims, bc):
+    def __init__(self, handle, dims, bc, n_rhs=1, stream=None):
         self.handle = handle
         self.dims = tuple(dims)
         self.bc = tuple(bc)
         self.V = int(np.prod(dims))
+        self.n_rhs = int(n_rhs)
+        self.stream = stream  # kept alive with the lattice
 
     def __del__(self):
         try:
@@ -189,7 +194,7 @@ def create_lattice(dims, bc=(1, 1, 1, -1), n_rhs: int = 1, stream=None) -> Latti
     d = (ctypes.c_int * 4)(*[int(x) for x in dims])
     b = (ctypes.c_int * 4)(*[int(x) for x in bc])
     _check(_lib.qdd_create_lattice(ctypes.byref(h), d, b, int(n_rhs), _stream_handle(stream)), "qdd_create_lattice")
-    return Lattice(h, dims, bc)
+    return Lattice(h, dims, bc, n_rhs, stream)
 
 
 def destroy_lattice(lat: Lattice) -> None:
@@ -215,17 +220,56 @@ def ras_apply(lat: Lattice, out, inp, kappa: float, c_sw: float, params: SolverP
     _check(_lib.qdd_ras_apply(lat.handle, po, pi, float(kappa), float(c_sw), ctypes.byref(params)), "qdd_ras_apply")
 
 
+def _info_dicts(infos, st):
+    out = []
+    for info in infos:
+        d = {k: getattr(info, k) for k, _ in SolveInfo._fields_}
+        d["return_status"] = st
+        out.append(d)
+    return out
+
+
 def solve(lat: Lattice, phi, eta, kappa: float, c_sw: float, tol: float, params: SolverParams | None = None,
-          raise_on_failure: bool = True) -> dict:
+          raise_on_failure: bool = True):
+    """Solve D phi = eta; returns the info dict (a list of them, one per
+    right-hand side, when the lattice has n_rhs > 1)."""
     po, _k1 = _ptr(phi, True)
     pe, _k2 = _ptr(eta)
-    info = SolveInfo()
+    infos = (SolveInfo * lat.n_rhs)()
     st = _lib.qdd_solve(lat.handle, po, pe, float(kappa), float(c_sw), float(tol),
-                        ctypes.byref(params) if params is not None else None, ctypes.byref(info))
+                        ctypes.byref(params) if params is not None else None, infos)
     if raise_on_failure:
         _check(st, "qdd_solve")
-    out = {k: getattr(info, k) for k, _ in SolveInfo._fields_}
-    out["return_status"] = st
+    out = _info_dicts(infos, st)
+    return out[0] if lat.n_rhs == 1 else out
+
+
+def solve_batch(lats, phis, etas, kappas, c_sws, tol: float, params: SolverParams | None = None,
+                raise_on_failure: bool = True):
+    """Solve independent systems (one per lattice) in lockstep; returns one
+    list of info dicts per lattice."""
+    n = len(lats)
+    keep = []
+    ph = (ctypes.c_void_p * n)()
+    et = (ctypes.c_void_p * n)()
+    hs = (ctypes.c_void_p * n)(*[l.handle.value if isinstance(l.handle, ctypes.c_void_p) else l.handle for l in lats])
+    for i in range(n):
+        ph[i], k1 = _ptr(phis[i], True)
+        et[i], k2 = _ptr(etas[i])
+        keep += [k1, k2]
+    ka = (ctypes.c_double * n)(*[float(k) for k in kappas])
+    cs = (ctypes.c_double * n)(*[float(c) for c in c_sws])
+    total = sum(l.n_rhs for l in lats)
+    infos = (SolveInfo * total)()
+    st = _lib.qdd_solve_batch(hs, ph, et, n, ka, cs, float(tol), ctypes.byref(params) if params is not None else None,
+                              infos)
+    if raise_on_failure:
+        _check(st, "qdd_solve_batch")
+    flat = _info_dicts(infos, st)
+    out, o = [], 0
+    for l in lats:
+        out.append(flat[o:o + l.n_rhs])
+        o += l.n_rhs
     return out
 
 

@@ -59,7 +59,8 @@ def test_host_side_calls_without_gpu(libpath):
     dims = (ctypes.c_int * 4)(8, 8, 8, 8)
     bad_bc = (ctypes.c_int * 4)(1, 1, 1, 0)
     assert lib.qdd_create_lattice(ctypes.byref(h), dims, bad_bc, 1, None) == qdd.QDD_ERR_ARG
-    assert lib.qdd_create_lattice(ctypes.byref(h), dims, bc, 2, None) == qdd.QDD_ERR_ARG
+    assert lib.qdd_create_lattice(ctypes.byref(h), dims, bc, 0, None) == qdd.QDD_ERR_ARG
+    assert lib.qdd_create_lattice(ctypes.byref(h), dims, bc, 65, None) == qdd.QDD_ERR_ARG
     assert lib.qdd_destroy_lattice(None) == qdd.QDD_OK
 
 
