@@ -407,6 +407,120 @@ def run_ours(args, rank, world):
     return 0
 
 
+def run_workload(args):
+    """Batched workloads (one JSON line each; the default run is the 32^4 solve):
+      mrhs  -- 24^3 x 48, eps 0.25 (seed 1), kappa 0.124, c_sw 1, 12 unit point
+               sources at the origin (one per spin-colour) in one 12-RHS lattice,
+               FP16 inner / FP64 outer, RAS parameters autotuned;
+      batch -- 16 independent systems drawn by synth.uneven_batch(16, 1) from
+               8^4, 12^4, 16^4, 8^3 x 24, 24^4, each on its own stream, solved in
+               lockstep with one CUDA graph.
+    Every answer is checked with the oracle's FP64 D."""
+    import numpy as np
+    import torch
+
+    import oracle
+    import synth
+    from paper_1011_3318_gb300 import qdd
+    oracle.build()
+    torch.cuda.set_device(0)
+    t_all = time.perf_counter()
+    n0 = qdd.kernel_launches()
+    if args.workload == "mrhs":
+        dims, kappa, eps = (24, 24, 24, 48), 0.124, 0.25
+        U = synth.gauge_field(dims, eps, 1)
+        src = np.stack([synth.point_source(dims, s_, c_) for s_ in range(4) for c_ in range(3)])
+        st = torch.cuda.Stream()
+        lat = qdd.create_lattice(dims, BC, n_rhs=12, stream=st)
+        dU = torch.from_numpy(U).cuda()
+        qdd.load_gauge(lat, dU)
+        d_src = torch.from_numpy(src).cuda()
+        d_phi = torch.empty_like(d_src)
+        # tune on a one-RHS lattice of the same field (the parameters do not depend on the RHS count)
+        lat1 = qdd.create_lattice(dims, BC, stream=st)
+        qdd.load_gauge(lat1, dU)
+        p, best_ms = qdd.autotune(lat1, d_src[0].contiguous(), kappa, CSW, TOL, qdd.default_params(inner_prec="f16"),
+                                  max_trials=args.tune_trials)
+        qdd.destroy_lattice(lat1)
+
+        def step():
+            qdd.load_gauge(lat, dU)
+            return qdd.solve(lat, d_phi, d_src, kappa, CSW, TOL, p)
+        for _ in range(args.warmup):
+            step()
+        n0 = qdd.kernel_launches()
+        ms, infos = time_steps(torch, st, step, args.steps)
+        launches = (qdd.kernel_launches() - n0) // args.steps
+        # the multi-RHS dslash against one RHS at a time (FP16, internal fields)
+        a = qdd.field_create(lat, "f16")
+        b = qdd.field_create(lat, "f16")
+        qdd.field_import(a, d_phi)
+        ms_d, _ = time_steps(torch, st, lambda: qdd.dslash_field(lat, b, a, kappa, CSW), 20)
+        phi = d_phi.cpu().numpy()
+        op = oracle.Op(dims, BC, U, kappa, CSW, store_clover=False)
+        res = [op.true_residual(src[r], phi[r]) for r in range(12)]
+        V = int(np.prod(dims))
+        bytes_12 = 12 * (52 + 52) * V + (96 + 148) * V
+        rec = {"workload": "mrhs", "metric": "time to solve 12 point sources to 1e-10 on 24^3x48",
+               "value": round(ms / 1e3, 4), "unit": "s", "per_rhs_s": round(ms / 1e3 / 12, 5),
+               "steps": args.steps, "warmup": args.warmup,
+               "ras": {"block": list(p.block), "overlap": p.overlap, "n_dominv": p.n_dominv, "n_ras": p.n_ras,
+                       "tuned_best_ms_one_rhs": round(best_ms, 2)},
+               "inner_iters": [i["inner_iters"] for i in infos[-1]],
+               "outer_iters": [i["outer_iters"] for i in infos[-1]],
+               "oracle_true_rel_residual_max": max(res),
+               "dslash_12rhs_f16": {"us_per_launch": round(ms_d * 1e3, 1),
+                                     "us_per_rhs": round(ms_d * 1e3 / 12, 1),
+                                     "algorithmic_GB/s": round(bytes_12 / (ms_d * 1e-3) / 1e9, 1)},
+               "gpu_launches_per_step": int(launches)}
+    else:
+        draws = synth.uneven_batch(16, 1)
+        lats, etas, phis, checks = [], [], [], []
+        streams = [torch.cuda.Stream() for _ in draws]
+        dUs = []
+        for d, st in zip(draws, streams):
+            U = synth.gauge_field(d["dims"], d["eps"], d["gauge_seed"])
+            eta = synth.gaussian_source(d["dims"], d["source_seed"])
+            lat = qdd.create_lattice(d["dims"], BC, stream=st)
+            dUs.append(torch.from_numpy(U).cuda())
+            qdd.load_gauge(lat, dUs[-1])
+            lats.append(lat)
+            etas.append(torch.from_numpy(eta).cuda())
+            phis.append(torch.empty_like(etas[-1]))
+            checks.append((U, eta))
+        p = qdd.default_params(inner_prec="f16", block=(4, 4, 4, 4), n_dominv=3, n_ras=2)
+        kap = [d["kappa"] for d in draws]
+
+        def step():
+            for lat, dU in zip(lats, dUs):
+                qdd.load_gauge(lat, dU)
+            return qdd.solve_batch(lats, phis, etas, kap, [CSW] * len(lats), TOL, p)
+        for _ in range(args.warmup):
+            step()
+        torch.cuda.synchronize()
+        n0 = qdd.kernel_launches()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            infos = step()
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) / args.steps * 1e3
+        launches = (qdd.kernel_launches() - n0) // args.steps
+        res = []
+        for d, (U, eta), phi in zip(draws, checks, phis):
+            op = oracle.Op(d["dims"], BC, U, d["kappa"], CSW, store_clover=False)
+            res.append(op.true_residual(eta, phi.cpu().numpy()))
+        rec = {"workload": "batch", "metric": "time to solve 16 uneven systems to 1e-10 in one graph",
+               "value": round(ms / 1e3, 4), "unit": "s", "steps": args.steps, "warmup": args.warmup,
+               "systems": [{"dims": d["dims"], "kappa": round(d["kappa"], 4), "eps": round(d["eps"], 3)} for d in draws],
+               "inner_iters": [i[0]["inner_iters"] for i in infos],
+               "oracle_true_rel_residual_max": max(res),
+               "ras": {"block": list(p.block), "n_dominv": p.n_dominv, "n_ras": p.n_ras},
+               "gpu_launches_per_step": int(launches), "note": "graph replays count the launches they contain"}
+    rec["total_wall_s"] = round(time.perf_counter() - t_all, 1)
+    print(json.dumps(rec), flush=True)
+    return 0
+
+
 def run_kernels(spec):
     """Kernel microbenchmark for profilers: builds the 32^4 workload and runs
     one kernel a few times -- dslash:<prec>, ras:<prec> (one RAS sweep of 4^4
@@ -458,11 +572,15 @@ def main():
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
                     help="use --block/--overlap/--n-dominv/--n-ras as given instead of tuning them")
     ap.add_argument("--tune-trials", dest="tune_trials", type=int, default=36)
+    ap.add_argument("--workload", choices=("solve", "mrhs", "batch"), default="solve",
+                    help="solve: the 32^4 headline; mrhs / batch: the batched workloads")
     ap.add_argument("--kernels", default=None,
                     help="profiler workload: dslash:f16|f32|f64, ras:f16|f32 or clover, three launches at 32^4")
     args = ap.parse_args()
     if args.kernels:
         return run_kernels(args.kernels)
+    if args.workload != "solve":
+        return run_workload(args)
     args.warmup = max(3, args.warmup)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -52,8 +52,8 @@ qdd_status autotune_impl(qdd_lattice *lat, double *phi_dev, const double *eta_de
         const auto t0 = clk::now();
         qdd_status s = solve_impl(lat, phi_dev, eta_dev, kappa, csw, tol, &q, info.data());
         const double ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
-        if (s != QDD_OK && s != QDD_ERR_NOT_CONVERGED && s != QDD_ERR_BREAKDOWN) {
-            st = s;
+        if (s != QDD_OK && s != QDD_ERR_NOT_CONVERGED && s != QDD_ERR_BREAKDOWN && s != QDD_ERR_NONFINITE) {
+            st = s;  // a CUDA or allocation failure ends the search
             return;
         }
         const double score = s == QDD_OK ? ms : 1e299;

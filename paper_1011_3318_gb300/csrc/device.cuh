@@ -139,7 +139,11 @@ __device__ __forceinline__ void store_spinor(const SpinorView &f, long long V, l
         float m = 0.f;
 #pragma unroll
         for (int k = 0; k < 12; k++) m = fmaxf(m, fmaxf(fabsf((float)s[k].r), fabsf((float)s[k].i)));
-        float inv = m > 0.f ? 1.0f / m : 0.f;
+        // a site whose largest component is below 1e-30 is stored as zero: its
+        // reciprocal could overflow (FP32 denormals), and such values vanish
+        // against the O(1) vectors the solver normalises to
+        if (!(m >= 1e-30f)) m = 0.f;
+        const float inv = m > 0.f ? 1.0f / m : 0.f;
         uint4 *p = (uint4 *)f.d;
 #pragma unroll
         for (int q = 0; q < 3; q++) {

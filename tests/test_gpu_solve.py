@@ -104,3 +104,16 @@ def test_autotune_returns_converging_parameters(qdd, oracle_mod):
     phi = np.empty_like(eta)
     info = qdd.solve(lat, phi, eta, 0.12, 1.0, 1e-10, p)
     assert info["status"] == 0 and op.true_residual(eta, phi) <= 1e-10
+
+
+def test_point_source_far_field_fp16(qdd, oracle_mod):
+    """A point source on 16^4: the Krylov vectors decay like kappa^d away from
+    the source and reach FP32 denormals, which the FP16 store must flush
+    rather than turn into inf/NaN."""
+    dims = (16, 16, 16, 16)
+    op, lat, _ = setup(qdd, oracle_mod, dims, 0.25, 0.124)
+    eta = synth.point_source(dims, 0, 0)
+    phi = np.empty_like(eta)
+    for prec in ("f16", "f32"):
+        info = qdd.solve(lat, phi, eta, 0.124, 1.0, 1e-10, qdd.default_params(inner_prec=prec))
+        assert info["status"] == 0 and op.true_residual(eta, phi) <= 1e-10
