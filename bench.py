@@ -270,9 +270,11 @@ def run_ours(args, rank, world):
         params, best_ms = qdd.autotune(lat, deta, KAPPA, CSW, TOL, params, max_trials=args.tune_trials)
         tune = {"seconds": round(time.perf_counter() - t0, 2), "best_solve_ms": round(best_ms, 2),
                 "block": list(params.block), "overlap": params.overlap, "n_dominv": params.n_dominv,
-                "n_ras": params.n_ras}
+                "n_ras": params.n_ras, "ras_kernel": params.ras_kernel,
+                "inner_prec": {0: "f64", 1: "f32", 2: "f16"}[params.inner_prec]}
         log(f"autotune: {tune}")
     blk, ov, nd, nr = list(params.block), params.overlap, params.n_dominv, params.n_ras
+    args.prec = {1: "f32", 2: "f16"}.get(params.inner_prec, args.prec)
 
     def step():
         qdd.load_gauge(lat, dU)           # gauge import + invalidates the clover: rebuilt inside the solve

@@ -94,6 +94,9 @@ typedef struct {
     int use_ras;        /* 1: right-precondition the inner solve with K_RAS (default 1) */
     int outer_mode;     /* 0: FP64 defect correction (the only mode so far) */
     int autotune;       /* reserved, 0 */
+    int ras_kernel;     /* RAS sweep staging: 0 auto, 1 compact (links and clover in the field's
+                           storage format), 2 expanded (FP32 18-real links and FP32 clover,
+                           domains of at most 256 sites) */
 } qdd_solver_params;
 
 typedef struct {

@@ -181,6 +181,7 @@ void qdd_default_params(qdd_solver_params *p)
     p->use_ras = 1;
     p->outer_mode = 0;
     p->autotune = 0;
+    p->ras_kernel = 0;
 }
 
 qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc[4], int n_rhs, void *cuda_stream)

@@ -1,7 +1,8 @@
 // autotune.cu -- picks the RAS parameters that minimise time to solution.
 //
 // The paper surveys NRAS = 1..10, N_dominv = 1..20 and d = 0, 2, 4 on its
-// cluster and keeps the fastest (Sec. 5).  The best point depends on the
+// cluster and keeps the fastest (Sec. 5); this survey adds the sweep
+// kernel's staging variant and the inner precision.  The best point depends on the
 // machine: there the global D was dominated by GigE communication, here it is
 // an HBM-bound kernel, so the balance between domain work and Krylov
 // iterations moves.  This tuner times whole solves of the caller's system
@@ -9,7 +10,8 @@
 //   1. (N_dominv, NRAS) on the starting block shape,
 //   2. the block shape (16 .. 256-site blocks, one orientation per shape),
 //   3. (N_dominv, NRAS) again around the best point on the best shape,
-//   4. overlap s = 1 on the best shape when its extended domain stays small.
+//   4. overlap s = 1 on the best shape when its extended domain stays small,
+//   5. the staging variant of the sweep kernel, then the other inner precision.
 #include <chrono>
 #include <cstring>
 #include <vector>
@@ -28,7 +30,7 @@ struct Trial {
 bool same_ras(const qdd_solver_params &a, const qdd_solver_params &b)
 {
     return memcmp(a.block, b.block, sizeof(a.block)) == 0 && a.overlap == b.overlap && a.n_dominv == b.n_dominv &&
-           a.n_ras == b.n_ras;
+           a.n_ras == b.n_ras && a.ras_kernel == b.ras_kernel && a.inner_prec == b.inner_prec;
 }
 
 }  // namespace
@@ -99,6 +101,19 @@ qdd_status autotune_impl(qdd_lattice *lat, double *phi_dev, const double *eta_de
     {
         qdd_solver_params q = best.p;
         q.overlap = 1;
+        trial(q);
+        if (st != QDD_OK) return st;
+    }
+    // the staging variant of the sweep kernel, then the other inner precision
+    for (int v = 1; v <= 2; v++) {
+        qdd_solver_params q = best.p;
+        q.ras_kernel = v;
+        trial(q);
+        if (st != QDD_OK) return st;
+    }
+    {
+        qdd_solver_params q = best.p;
+        q.inner_prec = q.inner_prec == QDD_F16 ? QDD_F32 : QDD_F16;
         trial(q);
         if (st != QDD_OK) return st;
     }

@@ -84,34 +84,47 @@ __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, floa
         const int mu = (int)(t & 3);
         const double2 *u2 = reinterpret_cast<const double2 *>(U) + t * 9;
         C<double> m[9];
+        CDF d[9];
 #pragma unroll
         for (int k = 0; k < 9; k++) {
             double2 v = u2[k];
             m[k] = {v.x, v.y};
+            d[k] = CDF{df_from_double(v.x), df_from_double(v.y)};
         }
-        // unitarity: max |(U^dag U - 1)_{ab}|
+        // SU(3) check in double-float: max |(U^dag U - 1)_{ab}| and |det U - 1|
+        const CDF z = CDF{DF{0.f, 0.f}, DF{0.f, 0.f}};
 #pragma unroll
         for (int a = 0; a < 3; a++)
 #pragma unroll
             for (int b = 0; b < 3; b++) {
-                C<double> s = {a == b ? -1.0 : 0.0, 0.0};
+                CDF s = z;
+                if (a == b) s.r = DF{-1.f, 0.f};
 #pragma unroll
-                for (int k = 0; k < 3; k++) s = cadd(s, cmulc(m[k * 3 + a], m[k * 3 + b]));
-                dev = fmax(dev, sqrt(s.r * s.r + s.i * s.i));
+                for (int k = 0; k < 3; k++) s = cdf_fma_ca(d[k * 3 + a], d[k * 3 + b], s);
+                const double re = df_to_double(s.r), im = df_to_double(s.i);
+                dev = fmax(dev, sqrt(re * re + im * im));
             }
-        // determinant
-        C<double> det = cmul(m[0], csub(cmul(m[4], m[8]), cmul(m[5], m[7])));
-        det = csub(det, cmul(m[1], csub(cmul(m[3], m[8]), cmul(m[5], m[6]))));
-        det = cadd(det, cmul(m[2], csub(cmul(m[3], m[7]), cmul(m[4], m[6]))));
-        dev = fmax(dev, sqrt((det.r - 1.0) * (det.r - 1.0) + det.i * det.i));
+        {
+            // det = u00 (u11 u22 - u12 u21) - u01 (u10 u22 - u12 u20) + u02 (u10 u21 - u11 u20)
+            auto minor = [&](int a, int b, int c, int e) {  // d[a] d[b] - d[c] d[e]
+                CDF t = cdf_fma(d[a], d[b], z);
+                CDF mc = CDF{df_neg(d[c].r), df_neg(d[c].i)};
+                return cdf_fma(mc, d[e], t);
+            };
+            CDF det = cdf_fma(d[0], minor(4, 8, 5, 7), z);
+            const CDF m1 = minor(3, 8, 5, 6);
+            det = cdf_fma(CDF{df_neg(d[1].r), df_neg(d[1].i)}, m1, det);
+            det = cdf_fma(d[2], minor(3, 7, 4, 6), det);
+            const double re = df_to_double(df_add(det.r, DF{-1.f, 0.f})), im = df_to_double(det.i);
+            dev = fmax(dev, sqrt(re * re + im * im));
+        }
         if (!isfinite(dev)) dev = 1e300;
 
         const long long V = g.V;
 #pragma unroll
         for (int k = 0; k < 9; k++) {
             U64[((long long)mu * 9 + k) * V + x] = make_double2(m[k].r, m[k].i);
-            const DF re = df_from_double(m[k].r), im = df_from_double(m[k].i);
-            Udf[((long long)mu * 9 + k) * V + x] = make_float4(re.h, re.l, im.h, im.l);
+            Udf[((long long)mu * 9 + k) * V + x] = make_float4(d[k].r.h, d[k].r.l, d[k].i.h, d[k].i.l);
         }
 #pragma unroll
         for (int q = 0; q < 3; q++) {

@@ -126,6 +126,7 @@ struct RasArgs {
     float2 *scratch;    // general kernel: per-slot rho, q, v
     int slots;
     int nrhs;
+    int variant;        // qdd_solver_params::ras_kernel
 };
 
 // Sites of an extended domain up to which the shared-memory kernel is used.

@@ -518,6 +518,12 @@ static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
 {
     const int n = a.dg.nloc;
     if constexpr (P == P16 || P == P32) {
+        if (a.variant == 1) {  // compact staging at every size
+            if (n <= 32) return launch_smem<P, 32, P == P16>(a, st);
+            if (n <= 64) return launch_smem<P, 64, P == P16>(a, st);
+            if (n <= 128) return launch_smem<P, 128, P == P16>(a, st);
+        }
+        if (a.variant == 2 && n > 128 && n <= 256) return launch_smem<P, 256, true, true>(a, st);
         if (n <= 32) return launch_smem<P, 32, true, true>(a, st);
         if (n <= 64) return launch_smem<P, 64, true, true>(a, st);
         if (n <= 128) return launch_smem<P, 128, true, true>(a, st);

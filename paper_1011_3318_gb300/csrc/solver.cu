@@ -175,6 +175,7 @@ qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params 
     ra.scratch = lat->ras_scratch;
     ra.slots = ras_default_slots();
     ra.nrhs = lat->nrhs;
+    ra.variant = p->ras_kernel;
     for (int j = 0; j < p->n_ras; j++) {
         const bool last = j == p->n_ras - 1;
         ra.in = j == 0 ? in : rho;

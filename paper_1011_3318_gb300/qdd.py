@@ -57,7 +57,7 @@ class SolverParams(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int * 4), ("overlap", ctypes.c_int), ("n_dominv", ctypes.c_int),
                 ("n_ras", ctypes.c_int), ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_inner", ctypes.c_int), ("max_outer", ctypes.c_int), ("use_ras", ctypes.c_int),
-                ("outer_mode", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("outer_mode", ctypes.c_int), ("autotune", ctypes.c_int), ("ras_kernel", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):

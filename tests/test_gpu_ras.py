@@ -74,3 +74,21 @@ def test_ras_rejects_bad_blocking(qdd):
         with pytest.raises(qdd.QddError) as e:
             qdd.ras_apply(lat, np.empty_like(eta), eta, 0.12, 1.0, p)
         assert e.value.status == qdd.QDD_ERR_ARG
+
+
+@pytest.mark.parametrize("block", [(2, 2, 2, 2), (2, 2, 4, 4), (2, 4, 4, 4), (4, 4, 4, 4)])
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("prec", ["f32", "f16"])
+def test_ras_staging_variants(qdd, oracle_mod, block, variant, prec):
+    """Compact (field-format) and expanded (FP32) staging of links and clover
+    give the oracle's RAS at every domain size they apply to."""
+    dims, bc, kappa, csw = (8, 8, 8, 8), (1, 1, 1, -1), 0.125, 1.0
+    U = synth.gauge_field(dims, 0.3, 17)
+    eta = synth.gaussian_source(dims, 18)
+    ref = oracle_mod.Op(dims, bc, U, kappa, csw).ras(eta, block, s=0, n_ras=2, n_dominv=3)
+    lat = qdd.create_lattice(dims, bc)
+    qdd.load_gauge(lat, U)
+    p = qdd.default_params(block=block, n_ras=2, n_dominv=3, inner_prec=prec, ras_kernel=variant)
+    out = np.empty_like(eta)
+    qdd.ras_apply(lat, out, eta, kappa, csw, p)
+    assert rel(out, ref) <= TOL_RAS[prec]
