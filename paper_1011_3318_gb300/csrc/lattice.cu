@@ -156,83 +156,6 @@ cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void
 // ---------------------------------------------------------------- clover
 typedef C<double> Z;
 
-// 3x3 complex matrices in double-float arithmetic (df64.cuh).
-struct M3D {
-    CDF e[9];
-};
-
-__device__ __forceinline__ M3D md_load(const float4 *Udf, long long V, int mu, long long x)
-{
-    M3D m;
-    const float4 *p = Udf + (long long)mu * 9 * V;
-#pragma unroll
-    for (int k = 0; k < 9; k++) {
-        const float4 v = p[k * V + x];
-        m.e[k] = CDF{DF{v.x, v.y}, DF{v.z, v.w}};
-    }
-    return m;
-}
-
-__device__ __forceinline__ M3D md_zero()
-{
-    M3D c;
-#pragma unroll
-    for (int k = 0; k < 9; k++) c.e[k] = CDF{DF{0.f, 0.f}, DF{0.f, 0.f}};
-    return c;
-}
-
-__device__ __forceinline__ M3D md_mul(const M3D &a, const M3D &b)  // a b
-{
-    M3D c = md_zero();
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++)
-#pragma unroll
-            for (int k = 0; k < 3; k++) c.e[i * 3 + j] = cdf_fma(a.e[i * 3 + k], b.e[k * 3 + j], c.e[i * 3 + j]);
-    return c;
-}
-
-__device__ __forceinline__ M3D md_mul_d(const M3D &a, const M3D &b)  // a b^dag
-{
-    M3D c = md_zero();
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++)
-#pragma unroll
-            for (int k = 0; k < 3; k++) c.e[i * 3 + j] = cdf_fma_cb(a.e[i * 3 + k], b.e[j * 3 + k], c.e[i * 3 + j]);
-    return c;
-}
-
-__device__ __forceinline__ M3D md_dmul(const M3D &a, const M3D &b)  // a^dag b
-{
-    M3D c = md_zero();
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++)
-#pragma unroll
-            for (int k = 0; k < 3; k++) c.e[i * 3 + j] = cdf_fma_ca(a.e[k * 3 + i], b.e[k * 3 + j], c.e[i * 3 + j]);
-    return c;
-}
-
-__device__ __forceinline__ M3D md_dag(const M3D &a)
-{
-    M3D c;
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) c.e[i * 3 + j] = CDF{a.e[j * 3 + i].r, df_neg(a.e[j * 3 + i].i)};
-    return c;
-}
-
-__device__ __forceinline__ void md_acc(M3D &q, const M3D &l)
-{
-#pragma unroll
-    for (int k = 0; k < 9; k++) q.e[k] = CDF{df_add(q.e[k].r, l.e[k].r), df_add(q.e[k].i, l.e[k].i)};
-}
-
 __device__ __forceinline__ long long shifted(const Geom &g, const int c[4], int mu, int dm, int nu, int dn)
 {
     int d[4] = {c[0], c[1], c[2], c[3]};
@@ -241,143 +164,195 @@ __device__ __forceinline__ long long shifted(const Geom &g, const int c[4], int 
     return d[0] + g.stride[1] * d[1] + g.stride[2] * d[2] + g.stride[3] * d[3];
 }
 
-// Fhat_{mu nu}(x) = (Q - Q^dag) / 8 from the four counter-clockwise leaves,
-// in double-float arithmetic; returned as FP64 (18 reals, row-major re/im).
-__device__ void field_strength(const Geom &g, const float4 *Udf, long long x, const int c[4], int mu, int nu,
-                               double (&F)[18])
+// Element (a, b) of the double-float link U_mu(x).
+__device__ __forceinline__ CDF udf(const float4 *Udf, long long V, int mu, long long x, int a, int b)
 {
-    const long long V = g.V;
-    const long long xpm = shifted(g, c, mu, 1, nu, 0), xpn = shifted(g, c, mu, 0, nu, 1);
-    const long long xmm = shifted(g, c, mu, -1, nu, 0), xmn = shifted(g, c, mu, 0, nu, -1);
-    const long long xmm_pn = shifted(g, c, mu, -1, nu, 1), xmm_mn = shifted(g, c, mu, -1, nu, -1);
-    const long long xpm_mn = shifted(g, c, mu, 1, nu, -1);
-    // x -> x+mu -> x+mu+nu -> x+nu -> x
-    M3D Q = md_mul(md_load(Udf, V, mu, x), md_load(Udf, V, nu, xpm));
-    Q = md_mul_d(Q, md_load(Udf, V, mu, xpn));
-    Q = md_mul_d(Q, md_load(Udf, V, nu, x));
-    // x -> x+nu -> x-mu+nu -> x-mu -> x
-    M3D l = md_mul_d(md_load(Udf, V, nu, x), md_load(Udf, V, mu, xmm_pn));
-    l = md_mul_d(l, md_load(Udf, V, nu, xmm));
-    l = md_mul(l, md_load(Udf, V, mu, xmm));
-    md_acc(Q, l);
-    // x -> x-mu -> x-mu-nu -> x-nu -> x:  U_mu(x-mu)^dag U_nu(x-mu-nu)^dag = (U_nu(x-mu-nu) U_mu(x-mu))^dag
-    l = md_dag(md_mul(md_load(Udf, V, nu, xmm_mn), md_load(Udf, V, mu, xmm)));
-    l = md_mul(l, md_load(Udf, V, mu, xmm_mn));
-    l = md_mul(l, md_load(Udf, V, nu, xmn));
-    md_acc(Q, l);
-    // x -> x-nu -> x+mu-nu -> x+mu -> x
-    l = md_dmul(md_load(Udf, V, nu, xmn), md_load(Udf, V, mu, xmn));
-    l = md_mul(l, md_load(Udf, V, nu, xpm_mn));
-    l = md_mul_d(l, md_load(Udf, V, mu, x));
-    md_acc(Q, l);
-#pragma unroll
-    for (int i = 0; i < 3; i++)
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            const CDF q = Q.e[i * 3 + j], qt = Q.e[j * 3 + i];
-            // (Q - Q^dag)_{ij} / 8 = (q - conj(qt)) / 8
-            F[2 * (i * 3 + j)] = df_to_double(df_scale2(df_sub(q.r, qt.r), 0.125f));
-            F[2 * (i * 3 + j) + 1] = df_to_double(df_scale2(df_add(q.i, qt.i), 0.125f));
-        }
+    const float4 v = Udf[((long long)mu * 9 + a * 3 + b) * V + x];
+    return CDF{DF{v.x, v.y}, DF{v.z, v.w}};
 }
 
-// One CTA builds the clover of 32 consecutive sites in three phases:
-//  1. warp p (p = 0..5, the planes xy xz xt yz yt zt) computes Fhat_p of its
-//     site (lane) and leaves it in shared memory;
-//  2. 64 threads (site, chirality h) pack the Hermitian 6x6 block h from the
-//     six Fhat's (36 reals);
-//  3. 32 threads store each site in FP64, FP32 and FP16 (with its norm).
-// Holding one Fhat per thread instead of six keeps the FP64 leaf products
-// in registers.
-constexpr int CL_SITES = 32;
-
-__global__ void __launch_bounds__(6 * CL_SITES, 2) clover_build_kernel(Geom g, const float4 *Udf, double kappa,
-                                                                     double csw, double2 *A64, float4 *A32,
-                                                                     uint4 *A16, float *A16n)
+// v <- M v with M = U_mu(x) or U_mu(x)^dag, in double-float.
+__device__ __forceinline__ void md_apply(const float4 *Udf, long long V, int mu, long long x, bool dag, CDF (&v)[3])
 {
-    __shared__ double sF[6][18][CL_SITES];
-    __shared__ double sP[72][CL_SITES];
-    const int lane = threadIdx.x % CL_SITES;
-    const long long x = (long long)blockIdx.x * CL_SITES + lane;
-    const bool act = x < g.V;
+    const CDF z = CDF{DF{0.f, 0.f}, DF{0.f, 0.f}};
+    CDF w[3] = {z, z, z};
+#pragma unroll
+    for (int a = 0; a < 3; a++)
+#pragma unroll
+        for (int b = 0; b < 3; b++) {
+            if (dag) w[a] = cdf_fma_ca(udf(Udf, V, mu, x, b, a), v[b], w[a]);  // conj(U_ba) v_b
+            else w[a] = cdf_fma(udf(Udf, V, mu, x, a, b), v[b], w[a]);
+        }
+#pragma unroll
+    for (int a = 0; a < 3; a++) v[a] = w[a];
+}
+
+// The four counter-clockwise plaquette leaves at x in the (mu, nu) plane,
+// each a product F0 F1 F2 F3 of links: site, direction and dagger of each.
+__device__ __forceinline__ void leaf_factors(const Geom &g, const int c[4], long long x, int mu, int nu, int leaf,
+                                             long long fx[4], int fd[4], bool fdag[4])
+{
+    if (leaf == 0) {  // U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+        fx[0] = x;                             fd[0] = mu; fdag[0] = false;
+        fx[1] = shifted(g, c, mu, 1, nu, 0);   fd[1] = nu; fdag[1] = false;
+        fx[2] = shifted(g, c, mu, 0, nu, 1);   fd[2] = mu; fdag[2] = true;
+        fx[3] = x;                             fd[3] = nu; fdag[3] = true;
+    } else if (leaf == 1) {  // U_nu(x) U_mu(x-mu+nu)^dag U_nu(x-mu)^dag U_mu(x-mu)
+        fx[0] = x;                             fd[0] = nu; fdag[0] = false;
+        fx[1] = shifted(g, c, mu, -1, nu, 1);  fd[1] = mu; fdag[1] = true;
+        fx[2] = shifted(g, c, mu, -1, nu, 0);  fd[2] = nu; fdag[2] = true;
+        fx[3] = fx[2];                         fd[3] = mu; fdag[3] = false;
+    } else if (leaf == 2) {  // U_mu(x-mu)^dag U_nu(x-mu-nu)^dag U_mu(x-mu-nu) U_nu(x-nu)
+        fx[0] = shifted(g, c, mu, -1, nu, 0);  fd[0] = mu; fdag[0] = true;
+        fx[1] = shifted(g, c, mu, -1, nu, -1); fd[1] = nu; fdag[1] = true;
+        fx[2] = fx[1];                         fd[2] = mu; fdag[2] = false;
+        fx[3] = shifted(g, c, mu, 0, nu, -1);  fd[3] = nu; fdag[3] = false;
+    } else {  // U_nu(x-nu)^dag U_mu(x-nu) U_nu(x+mu-nu) U_mu(x)^dag
+        fx[0] = shifted(g, c, mu, 0, nu, -1);  fd[0] = nu; fdag[0] = true;
+        fx[1] = fx[0];                         fd[1] = mu; fdag[1] = false;
+        fx[2] = shifted(g, c, mu, 1, nu, -1);  fd[2] = nu; fdag[2] = false;
+        fx[3] = x;                             fd[3] = mu; fdag[3] = true;
+    }
+}
+
+// One CTA builds the clover of CL_SITES consecutive sites in three phases:
+//  1. thread (plane, site) forms Q = sum of the four leaves of its plane
+//     column by column: for column j of every leaf F0 F1 F2 F3, v = F3 e_j and
+//     then F2, F1, F0 are applied to v (double-float arithmetic); each warp
+//     handles one plane for 32 sites, so all its lanes take the same path;
+//  2. the entries of the two Hermitian 6x6 chiral blocks
+//     1 + i kappa c_sw [[Gz, Gx - i Gy], [Gx + i Gy, -Gz]], with
+//     Fhat = (Q - Q^dag) / 8, are packed and converted to FP64;
+//  3. the stores in FP64, FP32 and FP16 (with the site norm).
+constexpr int CL_SITES = 32;
+constexpr int CL_THREADS = 6 * CL_SITES;
+
+__global__ void __launch_bounds__(CL_THREADS) clover_build_kernel(Geom g, const float4 *Udf, double kappa, double csw,
+                                                                   double2 *A64, float4 *A32, uint4 *A16, float *A16n)
+{
+    __shared__ float sQ[6][9][4][CL_SITES];  // Q per plane: [entry][re.h re.l im.h im.l][site]
+    __shared__ double sP[72][CL_SITES];      // packed clover
+    __shared__ double sN[CL_SITES];
+    const long long V = g.V;
+    const int t = threadIdx.x;
     {
-        const int plane = threadIdx.x / CL_SITES;
-        // planes (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)
-        const int mu = (plane >= 3) + (plane >= 5);
-        const int nu = plane < 3 ? plane + 1 : plane < 5 ? plane - 1 : 3;
-        if (act) {
+        const int site = t % CL_SITES, plane = t / CL_SITES;
+        const long long x = (long long)blockIdx.x * CL_SITES + site;
+        if (x < V) {
+            // planes (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)
+            const int mu = (plane >= 3) + (plane >= 5);
+            const int nu = plane < 3 ? plane + 1 : plane < 5 ? plane - 1 : 3;
             int c[4];
             site_coords(g, x, c);
-            double F[18];
-            field_strength(g, Udf, x, c, mu, nu, F);
+            const CDF z = CDF{DF{0.f, 0.f}, DF{0.f, 0.f}};
+#pragma unroll 1
+            for (int j = 0; j < 3; j++) {
+                CDF q[3] = {z, z, z};
+#pragma unroll 1
+                for (int leaf = 0; leaf < 4; leaf++) {
+                    long long fx[4];
+                    int fd[4];
+                    bool fdag[4];
+                    leaf_factors(g, c, x, mu, nu, leaf, fx, fd, fdag);
+                    CDF v[3];
 #pragma unroll
-            for (int k = 0; k < 18; k++) sF[plane][k][lane] = F[k];
+                    for (int a = 0; a < 3; a++) {  // column j of F3
+                        if (fdag[3]) {
+                            const CDF u = udf(Udf, V, fd[3], fx[3], j, a);
+                            v[a] = CDF{u.r, df_neg(u.i)};
+                        } else {
+                            v[a] = udf(Udf, V, fd[3], fx[3], a, j);
+                        }
+                    }
+                    md_apply(Udf, V, fd[2], fx[2], fdag[2], v);
+                    md_apply(Udf, V, fd[1], fx[1], fdag[1], v);
+                    md_apply(Udf, V, fd[0], fx[0], fdag[0], v);
+#pragma unroll
+                    for (int a = 0; a < 3; a++) q[a] = CDF{df_add(q[a].r, v[a].r), df_add(q[a].i, v[a].i)};
+                }
+#pragma unroll
+                for (int a = 0; a < 3; a++) {
+                    sQ[plane][a * 3 + j][0][site] = q[a].r.h;
+                    sQ[plane][a * 3 + j][1][site] = q[a].r.l;
+                    sQ[plane][a * 3 + j][2][site] = q[a].i.h;
+                    sQ[plane][a * 3 + j][3][site] = q[a].i.l;
+                }
+            }
         }
     }
     __syncthreads();
-    if (threadIdx.x < 2 * CL_SITES && act) {
-        // block h: 1 + i kc [[Gz, Gx - i Gy], [Gx + i Gy, -Gz]] with
-        //   Gz = F_xy -+ F_zt, Gy = F_xz +- F_yt, Gx = F_yz -+ F_xt (upper / lower)
-        const int h = threadIdx.x / CL_SITES;
-        const double sg = h == 0 ? -1.0 : 1.0;
-        const double kc = kappa * csw;
-        auto G = [&](int which, int a, int b) -> Z {
-            const int k = a * 3 + b;
-            int p0, p1;
-            double w;
-            if (which == 0) { p0 = 0; p1 = 5; w = sg; }          // Gz = F_xy + sg F_zt
-            else if (which == 1) { p0 = 1; p1 = 4; w = -sg; }    // Gy = F_xz - sg F_yt
-            else { p0 = 3; p1 = 2; w = sg; }                     // Gx = F_yz + sg F_xt
-            return Z{sF[p0][2 * k][lane] + w * sF[p1][2 * k][lane], sF[p0][2 * k + 1][lane] + w * sF[p1][2 * k + 1][lane]};
+    // packed blocks: h = 0 (spins 0,1) and 1 (spins 2,3), 6 diagonal reals and
+    // 15 complex lower entries each
+    const DF kc = df_from_double(kappa * csw);
+    for (int w = t; w < 2 * 21 * CL_SITES; w += CL_THREADS) {
+        const int site = w % CL_SITES, item = (w / CL_SITES) % 21, h = w / (21 * CL_SITES);
+        int i, j;
+        if (item < 6) {
+            i = j = item;
+        } else {  // lower entries in the packing order (1,0) (2,0) (2,1) (3,0) ...
+            int r = item - 6;
+            i = 1;
+            while (r >= i) { r -= i; i++; }
+            j = r;
+        }
+        const float sg = h == 0 ? -1.f : 1.f;
+        const int s1 = i / 3, a = i % 3, s2 = j / 3, b = j % 3, k = a * 3 + b, kt = b * 3 + a;
+        // Fhat_plane[a][b] = (Q_ab - conj(Q_ba)) / 8
+        auto Fp = [&](int plane, int part) -> DF {
+            const DF qa = DF{sQ[plane][k][2 * part][site], sQ[plane][k][2 * part + 1][site]};
+            const DF qb = DF{sQ[plane][kt][2 * part][site], sQ[plane][kt][2 * part + 1][site]};
+            return df_scale2(part == 0 ? df_sub(qa, qb) : df_add(qa, qb), 0.125f);
         };
-        auto M = [&](int i, int j) -> Z {
-            const int s = i / 3, a = i % 3, t = j / 3, b = j % 3;
-            Z bst;
-            if (s == 0 && t == 0) bst = G(0, a, b);
-            else if (s == 1 && t == 1) bst = cneg(G(0, a, b));
-            else if (s == 0) bst = csub(G(2, a, b), ci(G(1, a, b)));
-            else bst = cadd(G(2, a, b), ci(G(1, a, b)));
-            Z m = cscale(ci(bst), kc);
-            if (i == j) m.r += 1.0;
-            return m;
+        auto G = [&](int which, int part) -> DF {  // Gz = F_xy + sg F_zt, Gy = F_xz - sg F_yt, Gx = F_yz + sg F_xt
+            if (which == 0) return df_add(Fp(0, part), df_scale2(Fp(5, part), sg));
+            if (which == 1) return df_add(Fp(1, part), df_scale2(Fp(4, part), -sg));
+            return df_add(Fp(3, part), df_scale2(Fp(2, part), sg));
         };
+        DF br, bi;  // B_{s1 s2}[a][b]
+        if (s1 == 0 && s2 == 0) { br = G(0, 0); bi = G(0, 1); }
+        else if (s1 == 1 && s2 == 1) { br = df_neg(G(0, 0)); bi = df_neg(G(0, 1)); }
+        else if (s1 == 0) { br = df_add(G(2, 0), G(1, 1)); bi = df_sub(G(2, 1), G(1, 0)); }   // Gx - i Gy
+        else { br = df_sub(G(2, 0), G(1, 1)); bi = df_add(G(2, 1), G(1, 0)); }                // Gx + i Gy
+        // M = delta + i kc B = delta + kc (-B.i + i B.r)
+        DF mr = df_fma(kc, df_neg(bi), DF{0.f, 0.f});
+        const DF mi = df_fma(kc, br, DF{0.f, 0.f});
+        if (i == j) mr = df_add(mr, DF{1.f, 0.f});
         const int base = 36 * h;
-#pragma unroll 1
-        for (int i = 0; i < 6; i++) sP[base + i][lane] = M(i, i).r;
-#pragma unroll 1
-        for (int i = 1; i < 6; i++)
-#pragma unroll 1
-            for (int j = 0; j < i; j++) {
-                const Z m = M(i, j);
-                sP[base + cl_off(i, j)][lane] = m.r;
-                sP[base + cl_off(i, j) + 1][lane] = m.i;
-            }
+        if (i == j) {
+            sP[base + i][site] = df_to_double(mr);
+        } else {
+            sP[base + cl_off(i, j)][site] = df_to_double(mr);
+            sP[base + cl_off(i, j) + 1][site] = df_to_double(mi);
+        }
     }
     __syncthreads();
-    if (threadIdx.x < CL_SITES && act) {
-        const long long V = g.V;
+    if (t < CL_SITES) {
         double nrm = 0.0;
-#pragma unroll 1
-        for (int k = 0; k < 72; k++) nrm = fmax(nrm, fabs(sP[k][lane]));
-        const double inv = nrm > 0 ? 1.0 / nrm : 0.0;
-#pragma unroll 1
-        for (int k = 0; k < 36; k++) A64[k * V + x] = make_double2(sP[2 * k][lane], sP[2 * k + 1][lane]);
-#pragma unroll 1
-        for (int k = 0; k < 18; k++)
-            A32[k * V + x] = make_float4((float)sP[4 * k][lane], (float)sP[4 * k + 1][lane], (float)sP[4 * k + 2][lane],
-                                         (float)sP[4 * k + 3][lane]);
-#pragma unroll 1
-        for (int k = 0; k < 9; k++) {
-            unsigned w[4];
+        for (int k = 0; k < 72; k++) nrm = fmax(nrm, fabs(sP[k][t]));
+        sN[t] = nrm;
+    }
+    __syncthreads();
+    for (int w = t; w < 36 * CL_SITES; w += CL_THREADS) {
+        const int site = w % CL_SITES, k = w / CL_SITES;
+        const long long x = (long long)blockIdx.x * CL_SITES + site;
+        if (x >= V) continue;
+        A64[k * V + x] = make_double2(sP[2 * k][site], sP[2 * k + 1][site]);
+        if (k < 18)
+            A32[k * V + x] = make_float4((float)sP[4 * k][site], (float)sP[4 * k + 1][site], (float)sP[4 * k + 2][site],
+                                         (float)sP[4 * k + 3][site]);
+        if (k < 9) {
+            const double nrm = sN[site];
+            const float inv = nrm > 0 ? (float)(1.0 / nrm) : 0.f;
+            unsigned wv[4];
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                __half2 hh = __floats2half2_rn((float)(sP[8 * k + 2 * j][lane] * inv),
-                                               (float)(sP[8 * k + 2 * j + 1][lane] * inv));
-                w[j] = *reinterpret_cast<unsigned *>(&hh);
+            for (int q = 0; q < 4; q++) {
+                __half2 hh = __floats2half2_rn((float)sP[8 * k + 2 * q][site] * inv,
+                                               (float)sP[8 * k + 2 * q + 1][site] * inv);
+                wv[q] = *reinterpret_cast<unsigned *>(&hh);
             }
-            A16[k * V + x] = make_uint4(w[0], w[1], w[2], w[3]);
+            A16[k * V + x] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
         }
-        A16n[x] = (float)nrm;
+        if (k == 0) A16n[x] = (float)sN[site];
     }
 }
 
@@ -385,7 +360,7 @@ cudaError_t launch_clover_build(const Geom &g, const void *Udf, double kappa, do
                                 void *A16, float *A16n, cudaStream_t st)
 {
     const unsigned nb = (unsigned)((g.V + CL_SITES - 1) / CL_SITES);
-    clover_build_kernel<<<nb, 6 * CL_SITES, 0, st>>>(g, (const float4 *)Udf, kappa, csw, (double2 *)A64, (float4 *)A32,
+    clover_build_kernel<<<nb, CL_THREADS, 0, st>>>(g, (const float4 *)Udf, kappa, csw, (double2 *)A64, (float4 *)A32,
                                             (uint4 *)A16, A16n);
     note_launch();
     return cudaGetLastError();
