@@ -342,6 +342,58 @@ __device__ __forceinline__ void clover_apply(const T (&a)[72], const C<T> (&s)[1
     }
 }
 
+// ---------------------------------------------------------------- D at one site
+// (D in)(x) = A(x) in(x) - kappa sum_mu [hops], all fields read from global
+// memory in the precision P; FP16 norms are folded into the coefficients.
+template <int P, int MU, typename T>
+__device__ __forceinline__ void hop_pair(const Geom &g, const SpinorView &in, const LinkView &Ul, long long x,
+                                         const int c[4], C<T> (&acc)[12], T mk)
+{
+    const long long V = g.V;
+    {
+        const long long xf = fwd_site(g, x, c, MU);
+        const T sf = (c[MU] == g.L[MU] - 1 && g.bc[MU] < 0) ? -mk : mk;
+        C<T> s[12], U[9];
+        const T nf = load_spinor_u<P>(in, V, xf, s);
+        load_link<P>(Ul, V, MU, x, U);
+        hop<MU, true>(acc, s, U, sf * nf);
+    }
+    {
+        const long long xb = bwd_site(g, x, c, MU);
+        const T sb = (c[MU] == 0 && g.bc[MU] < 0) ? -mk : mk;
+        C<T> s[12], U[9];
+        const T nb = load_spinor_u<P>(in, V, xb, s);
+        load_link<P>(Ul, V, MU, xb, U);
+        hop<MU, false>(acc, s, U, sb * nb);
+    }
+}
+
+template <int P, typename T>
+__device__ __forceinline__ void apply_D_site(const Geom &g, const SpinorView &in, const LinkView &Ul,
+                                             const CloverView &A, T kappa, long long x, C<T> (&acc)[12])
+{
+    const long long V = g.V;
+    int c[4];
+    site_coords(g, x, c);
+    {
+        T av[72];
+        C<T> s[12];
+        const T na = load_clover_u<P>(A, V, x, av);
+        const T ns = load_spinor_u<P>(in, V, x, s);
+        clover_apply(av, s, acc);
+        if constexpr (P == P16) {
+            const T sc = na * ns;
+#pragma unroll
+            for (int k = 0; k < 12; k++) acc[k] = cscale(acc[k], sc);
+        }
+    }
+    const T mk = -kappa;
+    hop_pair<P, 0>(g, in, Ul, x, c, acc, mk);
+    hop_pair<P, 1>(g, in, Ul, x, c, acc, mk);
+    hop_pair<P, 2>(g, in, Ul, x, c, acc, mk);
+    hop_pair<P, 3>(g, in, Ul, x, c, acc, mk);
+}
+
 // ---------------------------------------------------------------- reductions
 // Sum of N doubles over the block; the total ends up in every lane of warp 0
 // (thread 0 in particular).  All threads of the block must call it.

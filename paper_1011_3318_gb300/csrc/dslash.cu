@@ -15,28 +15,6 @@
 
 namespace qdd {
 
-template <int P, int MU, typename T>
-__device__ __forceinline__ void hop_pair(const DslashArgs &a, long long x, const int c[4], C<T> (&acc)[12], T mk)
-{
-    const long long V = a.g.V;
-    {
-        const long long xf = fwd_site(a.g, x, c, MU);
-        const T sf = (c[MU] == a.g.L[MU] - 1 && a.g.bc[MU] < 0) ? -mk : mk;
-        C<T> s[12], U[9];
-        const T nf = load_spinor_u<P>(a.in, V, xf, s);
-        load_link<P>(a.U, V, MU, x, U);
-        hop<MU, true>(acc, s, U, sf * nf);
-    }
-    {
-        const long long xb = bwd_site(a.g, x, c, MU);
-        const T sb = (c[MU] == 0 && a.g.bc[MU] < 0) ? -mk : mk;
-        C<T> s[12], U[9];
-        const T nb = load_spinor_u<P>(a.in, V, xb, s);
-        load_link<P>(a.U, V, MU, xb, U);
-        hop<MU, false>(acc, s, U, sb * nb);
-    }
-}
-
 template <int P, int EPI, int NT>
 __global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
 {
@@ -57,26 +35,8 @@ __global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
     double red[NRED > 0 ? NRED : 1] = {0.0};
 
     if (active) {
-        int c[4];
-        site_coords(a.g, x, c);
         C<T> acc[12];
-        {
-            T av[72];
-            C<T> s[12];
-            const T na = load_clover_u<P>(a.A, V, x, av);
-            const T ns = load_spinor_u<P>(a.in, V, x, s);
-            clover_apply(av, s, acc);
-            if constexpr (P == P16) {
-                const T sc = na * ns;
-#pragma unroll
-                for (int k = 0; k < 12; k++) acc[k] = cscale(acc[k], sc);
-            }
-        }
-        const T mk = (T)(-a.kappa);
-        hop_pair<P, 0>(a, x, c, acc, mk);
-        hop_pair<P, 1>(a, x, c, acc, mk);
-        hop_pair<P, 2>(a, x, c, acc, mk);
-        hop_pair<P, 3>(a, x, c, acc, mk);
+        apply_D_site<P>(a.g, a.in, a.U, a.A, (T)a.kappa, x, acc);
 
         if constexpr (EPI == EPI_XMY || EPI == EPI_XMY_NORM) {
             C<T> y[12];

@@ -74,6 +74,9 @@ cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorVie
 }
 
 // ---------------------------------------------------------------- gauge
+// max(a, b) where a NaN b counts as the largest deviation (fmaxf would drop it)
+__device__ __forceinline__ float dev_max(float a, float b) { return (b <= 3.0e38f) ? fmaxf(a, b) : 3.0e38f; }
+
 __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, float4 *U32, uint2 *U16, float4 *Udf,
                                      unsigned long long *maxdev)
 {
@@ -91,7 +94,10 @@ __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, floa
             m[k] = {v.x, v.y};
             d[k] = CDF{df_from_double(v.x), df_from_double(v.y)};
         }
-        // SU(3) check in double-float: max |(U^dag U - 1)_{ab}| and |det U - 1|
+        // SU(3) check in double-float: max |(U^dag U - 1)_{ab}| and |det U - 1|.
+        // The deviations are formed in double-float; their high words carry
+        // them to ~1e-22 absolute, so the magnitudes are taken in FP32.
+        float devf = 0.f;
         const CDF z = CDF{DF{0.f, 0.f}, DF{0.f, 0.f}};
 #pragma unroll
         for (int a = 0; a < 3; a++)
@@ -101,8 +107,7 @@ __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, floa
                 if (a == b) s.r = DF{-1.f, 0.f};
 #pragma unroll
                 for (int k = 0; k < 3; k++) s = cdf_fma_ca(d[k * 3 + a], d[k * 3 + b], s);
-                const double re = df_to_double(s.r), im = df_to_double(s.i);
-                dev = fmax(dev, sqrt(re * re + im * im));
+                devf = dev_max(devf, sqrtf(s.r.h * s.r.h + s.i.h * s.i.h));
             }
         {
             // det = u00 (u11 u22 - u12 u21) - u01 (u10 u22 - u12 u20) + u02 (u10 u21 - u11 u20)
@@ -115,10 +120,10 @@ __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, floa
             const CDF m1 = minor(3, 8, 5, 6);
             det = cdf_fma(CDF{df_neg(d[1].r), df_neg(d[1].i)}, m1, det);
             det = cdf_fma(d[2], minor(3, 7, 4, 6), det);
-            const double re = df_to_double(df_add(det.r, DF{-1.f, 0.f})), im = df_to_double(det.i);
-            dev = fmax(dev, sqrt(re * re + im * im));
+            const DF dr = df_add(det.r, DF{-1.f, 0.f});
+            devf = dev_max(devf, sqrtf(dr.h * dr.h + det.i.h * det.i.h));
         }
-        if (!isfinite(dev)) dev = 1e300;
+        dev = isfinite(devf) ? (double)devf : 1e300;
 
         const long long V = g.V;
 #pragma unroll

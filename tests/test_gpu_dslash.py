@@ -96,3 +96,13 @@ def test_load_gauge_rejects_non_su3(qdd):
     with pytest.raises(qdd.QddError) as e:
         qdd.dslash(lat, np.empty_like(psi), psi, 0.1, 1.0, "f32")
     assert e.value.status == qdd.QDD_ERR_STATE
+
+
+def test_load_gauge_rejects_nan_links(qdd):
+    dims = (4, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, 1)
+    U[5, 1, 2, 0] = np.nan
+    lat = qdd.create_lattice(dims)
+    with pytest.raises(qdd.QddError) as e:
+        qdd.load_gauge(lat, U)
+    assert e.value.status == qdd.QDD_ERR_ARG
