@@ -71,6 +71,9 @@ typedef enum { QDD_F64 = 0, QDD_F32 = 1, QDD_F16 = 2 } qdd_prec;
 
 /* Right-hand sides a lattice can hold (qdd_create_lattice n_rhs). */
 #define QDD_MAX_RHS 64
+/* Largest lattice volume: every device field plane index (at most 36 planes
+ * of V sites) fits in 32 bits. */
+#define QDD_MAX_SITES 119304647LL
 
 /* Opaque lattice: geometry, boundary signs, links, clover cache, stream. */
 typedef struct qdd_lattice qdd_lattice;
@@ -128,7 +131,8 @@ void qdd_default_params(qdd_solver_params *p);
  * every kernel of this lattice runs on it, and solves can be captured into
  * CUDA graphs only on a non-default stream.  Allocates the lattice's device
  * memory (about 2.2 KB per site).  Errors: QDD_ERR_ARG for extents outside
- * 1..4096, bc not +-1, n_rhs out of range; QDD_ERR_NOMEM. */
+ * 1..4096, a volume above QDD_MAX_SITES, bc not +-1, n_rhs out of range;
+ * QDD_ERR_NOMEM. */
 qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc[4], int n_rhs,
                               void *cuda_stream);
 

@@ -204,8 +204,8 @@ qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc
         }
         V *= dims[mu];
     }
-    if (V > (1LL << 31)) {
-        set_error("lattice too large");
+    if (V > QDD_MAX_SITES) {
+        set_error("lattice volume above 119304647 sites (device field planes are indexed in 32 bits)");
         return QDD_ERR_ARG;
     }
     if (n_rhs < 1 || n_rhs > QDD_MAX_RHS) {

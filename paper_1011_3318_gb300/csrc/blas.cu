@@ -39,9 +39,9 @@ __global__ void __launch_bounds__(BLAS_NT) blas_kernel(BlasArgs a)
     const long long V = a.V;
 #pragma unroll
     for (int i = 0; i < 8; i++) a.f[i] = rhs_view<P>(a.f[i], V, r);
-    double red[NRED > 0 ? NRED : 1];
+    T part[NRED > 0 ? NRED : 1];
 #pragma unroll
-    for (int k = 0; k < (NRED > 0 ? NRED : 1); k++) red[k] = 0.0;
+    for (int k = 0; k < (NRED > 0 ? NRED : 1); k++) part[k] = 0;
 
     // coefficients read once per thread from the device scalars
     C<T> c1 = {0, 0}, c2 = {0, 0};
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(BLAS_NT) blas_kernel(BlasArgs a)
             T n2 = 0;
 #pragma unroll
             for (int k = 0; k < 12; k++) n2 += b[k].r * b[k].r + b[k].i * b[k].i;
-            red[0] += (double)n2;
+            part[0] += n2;
         } else if constexpr (OP == B_P) {
             C<T> p[12], r[12], v[12];
             load_spinor<P>(a.f[0], V, x, p);
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(BLAS_NT) blas_kernel(BlasArgs a)
             T n2 = 0;
 #pragma unroll
             for (int k = 0; k < 12; k++) n2 += f[k].r * f[k].r + f[k].i * f[k].i;
-            red[0] += (double)n2;
+            part[0] += n2;
         } else if constexpr (OP == B_COPY) {
             C<T> f[12];
             load_spinor<P>(a.f[1], V, x, f);
@@ -106,12 +106,13 @@ __global__ void __launch_bounds__(BLAS_NT) blas_kernel(BlasArgs a)
             T n2 = 0;
 #pragma unroll
             for (int k = 0; k < 12; k++) n2 += r[k].r * r[k].r + r[k].i * r[k].i;
-            red[0] += (double)n2;
+            part[0] += n2;
         }
     }
 
     if constexpr (NRED > 0) {
-        if (grid_sum<NRED>(red, rs_partials(a.rs, r), rs_counter(a.rs, r), bid, nblk)) {
+        double red[NRED];
+        if (grid_sum<NRED, T>(part, red, rs_partials(a.rs, r), rs_counter(a.rs, r), bid, nblk)) {
             if constexpr (OP == B_INIT) {
                 sc->rho = make_double2(red[0], 0.0);
                 sc->alpha = sc->omega = sc->beta = make_double2(1.0, 0.0);
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(BLAS_NT) bicg_xr_kernel(BlasArgs a)
     for (int i = 0; i < 8; i++) a.f[i] = rhs_view<P>(a.f[i], V, r);
     const C<T> al = {(T)sc->alpha.x, (T)sc->alpha.y};
     const C<T> om = {(T)sc->omega.x, (T)sc->omega.y};
-    double red[3] = {0.0, 0.0, 0.0};
+    T part[3] = {0, 0, 0};
     for (long long x = (long long)bid * BLAS_NT + threadIdx.x; x < V; x += (long long)nblk * BLAS_NT) {
         C<T> xx[12], ph[12], sh[12];
         load_spinor<P>(a.f[0], V, x, xx);
@@ -172,11 +173,12 @@ __global__ void __launch_bounds__(BLAS_NT) bicg_xr_kernel(BlasArgs a)
             n2 += s[k].r * s[k].r + s[k].i * s[k].i;
         }
         store_spinor<P>(a.f[3], V, x, s);
-        red[0] += (double)dr;
-        red[1] += (double)di;
-        red[2] += (double)n2;
+        part[0] += dr;
+        part[1] += di;
+        part[2] += n2;
     }
-    if (grid_sum<3>(red, rs_partials(a.rs, r), rs_counter(a.rs, r), bid, nblk)) {
+    double red[3];
+    if (grid_sum<3, T>(part, red, rs_partials(a.rs, r), rs_counter(a.rs, r), bid, nblk)) {
         const double2 rn = make_double2(red[0], red[1]);
         if (!isfinite(red[0]) || !isfinite(red[1]) || !isfinite(red[2])) {
             sc->status = S_NONFINITE;

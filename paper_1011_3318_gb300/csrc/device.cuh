@@ -43,50 +43,65 @@ template <typename T> __device__ __forceinline__ C<T> cneg(C<T> a) { return {-a.
 template <typename T> __device__ __forceinline__ C<T> cconj(C<T> a) { return {a.r, -a.i}; }
 
 // ---------------------------------------------------------------- geometry
+// Coordinates of site x.  Site indices fit in 32 bits (the lattice volume
+// is capped at 2^31), so the divisions are 32-bit: 64-bit integer division is
+// emulated by a long instruction sequence on the GPU.
 __device__ __forceinline__ void site_coords(const Geom &g, long long x, int c[4])
 {
-    long long r = x;
-    c[0] = (int)(r % g.L[0]); r /= g.L[0];
-    c[1] = (int)(r % g.L[1]); r /= g.L[1];
-    c[2] = (int)(r % g.L[2]); r /= g.L[2];
-    c[3] = (int)r;
+    unsigned r = (unsigned)x;
+    const unsigned l0 = (unsigned)g.L[0], l1 = (unsigned)g.L[1], l2 = (unsigned)g.L[2];
+    unsigned q = r / l0;
+    c[0] = (int)(r - q * l0);
+    r = q;
+    q = r / l1;
+    c[1] = (int)(r - q * l1);
+    r = q;
+    q = r / l2;
+    c[2] = (int)(r - q * l2);
+    c[3] = (int)q;
 }
 
 __device__ __forceinline__ long long fwd_site(const Geom &g, long long x, const int c[4], int mu)
 {
-    return c[mu] == g.L[mu] - 1 ? x - (long long)(g.L[mu] - 1) * g.stride[mu] : x + g.stride[mu];
+    const unsigned xi = (unsigned)x, st = (unsigned)g.stride[mu];
+    return c[mu] == g.L[mu] - 1 ? xi - (unsigned)(g.L[mu] - 1) * st : xi + st;
 }
 
 __device__ __forceinline__ long long bwd_site(const Geom &g, long long x, const int c[4], int mu)
 {
-    return c[mu] == 0 ? x + (long long)(g.L[mu] - 1) * g.stride[mu] : x - g.stride[mu];
+    const unsigned xi = (unsigned)x, st = (unsigned)g.stride[mu];
+    return c[mu] == 0 ? xi + (unsigned)(g.L[mu] - 1) * st : xi - st;
 }
 
 // ---------------------------------------------------------------- spinors
+// Field planes are indexed in 32 bits: the library caps the volume so that
+// the largest field (36 planes of V sites) stays below 2^32 elements, and a
+// 32-bit index costs fewer integer instructions per load than a 64-bit one.
 template <int P, typename T>
 __device__ __forceinline__ void load_spinor(const SpinorView &f, long long V, long long x, C<T> (&s)[12])
 {
+    const unsigned v = (unsigned)V, i = (unsigned)x;
     if constexpr (P == P64) {
         const double2 *p = (const double2 *)f.d;
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-            double2 a = p[k * V + x];
+            double2 a = p[k * v + i];
             s[k] = {(T)a.x, (T)a.y};
         }
     } else if constexpr (P == P32) {
         const float4 *p = (const float4 *)f.d;
 #pragma unroll
         for (int q = 0; q < 6; q++) {
-            float4 a = p[q * V + x];
+            float4 a = p[q * v + i];
             s[2 * q] = {(T)a.x, (T)a.y};
             s[2 * q + 1] = {(T)a.z, (T)a.w};
         }
     } else {
         const uint4 *p = (const uint4 *)f.d;
-        float n = f.n[x];
+        float n = f.n[i];
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-            uint4 a = p[q * V + x];
+            uint4 a = p[q * v + i];
             unsigned w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
             for (int j = 0; j < 4; j++) {
@@ -103,11 +118,12 @@ __device__ __forceinline__ void load_spinor(const SpinorView &f, long long V, lo
 template <int P, typename T>
 __device__ __forceinline__ T load_spinor_u(const SpinorView &f, long long V, long long x, C<T> (&s)[12])
 {
+    const unsigned v = (unsigned)V, i = (unsigned)x;
     if constexpr (P == P16) {
         const uint4 *p = (const uint4 *)f.d;
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-            uint4 a = p[q * V + x];
+            uint4 a = p[q * v + i];
             unsigned w[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
             for (int j = 0; j < 4; j++) {
@@ -115,7 +131,7 @@ __device__ __forceinline__ T load_spinor_u(const SpinorView &f, long long V, lon
                 s[4 * q + j] = {(T)f2.x, (T)f2.y};
             }
         }
-        return (T)f.n[x];
+        return (T)f.n[i];
     } else {
         load_spinor<P>(f, V, x, s);
         return (T)1;
@@ -125,15 +141,16 @@ __device__ __forceinline__ T load_spinor_u(const SpinorView &f, long long V, lon
 template <int P, typename T>
 __device__ __forceinline__ void store_spinor(const SpinorView &f, long long V, long long x, const C<T> (&s)[12])
 {
+    const unsigned v = (unsigned)V, i = (unsigned)x;
     if constexpr (P == P64) {
         double2 *p = (double2 *)f.d;
 #pragma unroll
-        for (int k = 0; k < 12; k++) p[k * V + x] = make_double2((double)s[k].r, (double)s[k].i);
+        for (int k = 0; k < 12; k++) p[k * v + i] = make_double2((double)s[k].r, (double)s[k].i);
     } else if constexpr (P == P32) {
         float4 *p = (float4 *)f.d;
 #pragma unroll
         for (int q = 0; q < 6; q++)
-            p[q * V + x] = make_float4((float)s[2 * q].r, (float)s[2 * q].i, (float)s[2 * q + 1].r,
+            p[q * v + i] = make_float4((float)s[2 * q].r, (float)s[2 * q].i, (float)s[2 * q + 1].r,
                                        (float)s[2 * q + 1].i);
     } else {
         float m = 0.f;
@@ -153,9 +170,9 @@ __device__ __forceinline__ void store_spinor(const SpinorView &f, long long V, l
                 __half2 h = __floats2half2_rn((float)s[4 * q + j].r * inv, (float)s[4 * q + j].i * inv);
                 w[j] = *reinterpret_cast<unsigned *>(&h);
             }
-            p[q * V + x] = make_uint4(w[0], w[1], w[2], w[3]);
+            p[q * v + i] = make_uint4(w[0], w[1], w[2], w[3]);
         }
-        f.n[x] = m;
+        f.n[i] = m;
     }
 }
 
@@ -172,27 +189,28 @@ __device__ __forceinline__ void rebuild_row2(C<T> (&U)[9])
 template <int P, typename T>
 __device__ __forceinline__ void load_link(const LinkView &u, long long V, int mu, long long x, C<T> (&U)[9])
 {
+    const unsigned v = (unsigned)V, i = (unsigned)x;
     if constexpr (P == P64) {
-        const double2 *p = (const double2 *)u.d + (long long)mu * 9 * V;
+        const double2 *p = (const double2 *)u.d + mu * 9 * v;
 #pragma unroll
         for (int k = 0; k < 9; k++) {
-            double2 a = p[k * V + x];
+            double2 a = p[k * v + i];
             U[k] = {(T)a.x, (T)a.y};
         }
     } else if constexpr (P == P32) {
-        const float4 *p = (const float4 *)u.d + (long long)mu * 3 * V;
+        const float4 *p = (const float4 *)u.d + mu * 3 * v;
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-            float4 a = p[q * V + x];
+            float4 a = p[q * v + i];
             U[2 * q] = {(T)a.x, (T)a.y};
             U[2 * q + 1] = {(T)a.z, (T)a.w};
         }
         rebuild_row2(U);
     } else {
-        const uint2 *p = (const uint2 *)u.d + (long long)mu * 3 * V;
+        const uint2 *p = (const uint2 *)u.d + mu * 3 * v;
 #pragma unroll
         for (int q = 0; q < 3; q++) {
-            uint2 a = p[q * V + x];
+            uint2 a = p[q * v + i];
             unsigned w[2] = {a.x, a.y};
 #pragma unroll
             for (int j = 0; j < 2; j++) {
@@ -258,28 +276,29 @@ __device__ __forceinline__ void hop(C<T> (&acc)[12], const C<T> (&s)[12], const 
 template <int P, typename T>
 __device__ __forceinline__ void load_clover(const CloverView &A, long long V, long long x, T (&a)[72])
 {
+    const unsigned v = (unsigned)V, i = (unsigned)x;
     if constexpr (P == P64) {
         const double2 *p = (const double2 *)A.d;
 #pragma unroll
         for (int k = 0; k < 36; k++) {
-            double2 v = p[k * V + x];
-            a[2 * k] = (T)v.x;
-            a[2 * k + 1] = (T)v.y;
+            const double2 e = p[k * v + i];
+            a[2 * k] = (T)e.x;
+            a[2 * k + 1] = (T)e.y;
         }
     } else if constexpr (P == P32) {
         const float4 *p = (const float4 *)A.d;
 #pragma unroll
         for (int k = 0; k < 18; k++) {
-            float4 v = p[k * V + x];
-            a[4 * k] = (T)v.x; a[4 * k + 1] = (T)v.y; a[4 * k + 2] = (T)v.z; a[4 * k + 3] = (T)v.w;
+            const float4 e = p[k * v + i];
+            a[4 * k] = (T)e.x; a[4 * k + 1] = (T)e.y; a[4 * k + 2] = (T)e.z; a[4 * k + 3] = (T)e.w;
         }
     } else {
         const uint4 *p = (const uint4 *)A.d;
-        float n = A.n[x];
+        float n = A.n[i];
 #pragma unroll
         for (int k = 0; k < 9; k++) {
-            uint4 v = p[k * V + x];
-            unsigned w[4] = {v.x, v.y, v.z, v.w};
+            const uint4 e = p[k * v + i];
+            unsigned w[4] = {e.x, e.y, e.z, e.w};
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 float2 f2 = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
@@ -294,12 +313,13 @@ __device__ __forceinline__ void load_clover(const CloverView &A, long long V, lo
 template <int P, typename T>
 __device__ __forceinline__ T load_clover_u(const CloverView &A, long long V, long long x, T (&a)[72])
 {
+    const unsigned v = (unsigned)V, i = (unsigned)x;
     if constexpr (P == P16) {
         const uint4 *p = (const uint4 *)A.d;
 #pragma unroll
         for (int k = 0; k < 9; k++) {
-            uint4 v = p[k * V + x];
-            unsigned w[4] = {v.x, v.y, v.z, v.w};
+            const uint4 e = p[k * v + i];
+            unsigned w[4] = {e.x, e.y, e.z, e.w};
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 float2 f2 = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
@@ -307,7 +327,7 @@ __device__ __forceinline__ T load_clover_u(const CloverView &A, long long V, lon
                 a[8 * k + 2 * j + 1] = (T)f2.y;
             }
         }
-        return (T)A.n[x];
+        return (T)A.n[i];
     } else {
         load_clover<P>(A, V, x, a);
         return (T)1;
@@ -395,20 +415,25 @@ __device__ __forceinline__ void apply_D_site(const Geom &g, const SpinorView &in
 }
 
 // ---------------------------------------------------------------- reductions
-// Sum of N doubles over the block; the total ends up in every lane of warp 0
-// (thread 0 in particular).  All threads of the block must call it.
-template <int N>
-__device__ __forceinline__ void block_sum(double (&v)[N], double *sm /* N * 32 */)
+// Sum over the block of one value per thread and component; the total ends
+// up in v in every lane of warp 0 (thread 0 in particular).  The warp stage
+// runs in the callers' type T: FP32 in the FP32/FP16 kernels, whose per-site
+// terms are FP32 already, because FP64 adds and conversions run at a small
+// fraction of the FP32 rate on this GPU and would otherwise cost more than
+// the site arithmetic of a bandwidth-bound kernel.  The warp totals are added
+// in FP64.  in and v may be the same array.  All threads must call it.
+template <int N, typename T>
+__device__ __forceinline__ void block_sum(T (&in)[N], double (&v)[N], double *sm /* N * 32 */)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
 #pragma unroll
     for (int k = 0; k < N; k++)
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+        for (int o = 16; o > 0; o >>= 1) in[k] += __shfl_xor_sync(0xffffffffu, in[k], o);
     __syncthreads();  // sm may be in use by a previous call
     if (lane == 0)
 #pragma unroll
-        for (int k = 0; k < N; k++) sm[k * 32 + warp] = v[k];
+        for (int k = 0; k < N; k++) sm[k * 32 + warp] = (double)in[k];
     __syncthreads();
     if (warp == 0) {
 #pragma unroll
@@ -418,6 +443,12 @@ __device__ __forceinline__ void block_sum(double (&v)[N], double *sm /* N * 32 *
             for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
         }
     }
+}
+
+template <int N>
+__device__ __forceinline__ void block_sum(double (&v)[N], double *sm /* N * 32 */)
+{
+    block_sum<N, double>(v, v, sm);
 }
 
 // Block sum that leaves the total in every thread of the block.
@@ -437,14 +468,15 @@ __device__ __forceinline__ void block_allsum(double (&v)[N], double *sm /* N * 3
 // one reduction (one right-hand side): every block stores its partial sums,
 // and the block that arrives last adds them in block order (so the result
 // does not depend on scheduling) and returns true in thread 0 with the
-// totals in v.  No block waits for another.
-template <int N>
-__device__ __forceinline__ bool grid_sum(double (&v)[N], double *partials, unsigned int *counter, unsigned bid,
-                                         unsigned nblk)
+// totals in v.  No block waits for another.  The per-thread values t are of
+// the kernel's type T (see block_sum).
+template <int N, typename T>
+__device__ __forceinline__ bool grid_sum(T (&t)[N], double (&v)[N], double *partials, unsigned int *counter,
+                                         unsigned bid, unsigned nblk)
 {
     __shared__ double sm[N * 32];
     __shared__ int last;
-    block_sum<N>(v, sm);
+    block_sum<N, T>(t, v, sm);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int k = 0; k < N; k++) partials[(long long)bid * N + k] = v[k];
@@ -458,6 +490,9 @@ __device__ __forceinline__ bool grid_sum(double (&v)[N], double *partials, unsig
     double acc[N];
 #pragma unroll
     for (int k = 0; k < N; k++) acc[k] = 0.0;
+    // unrolled so that several L2 loads are in flight per thread: this block
+    // runs alone at the end of the kernel, so its latency is the kernel's tail
+#pragma unroll 8
     for (unsigned b = threadIdx.x; b < nblk; b += blockDim.x)
 #pragma unroll
         for (int k = 0; k < N; k++) acc[k] += __ldcg(partials + (long long)b * N + k);

@@ -16,7 +16,7 @@
 namespace qdd {
 
 template <int P, int EPI, int NT>
-__global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
+__device__ __forceinline__ void dslash_body(DslashArgs a)
 {
     typedef typename RealOf<P>::T T;
     constexpr int NRED = (EPI == EPI_XMY_NORM) ? 1 : (EPI == EPI_RV || EPI == EPI_TS) ? 3 : 0;
@@ -32,15 +32,23 @@ __global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
     a.y = rhs_view<P>(a.y, V, r);
     const long long x = (long long)bid * NT + threadIdx.x;
     const bool active = x < V;
-    double red[NRED > 0 ? NRED : 1] = {0.0};
+    T part[NRED > 0 ? NRED : 1] = {0};
 
     if (active) {
+        // the epilogue's second vector: in FP16 it is loaded before the
+        // stencil so that its latency overlaps the site arithmetic (it costs
+        // 13 registers there; in FP32/FP64 it would cost occupancy).  It is
+        // always loaded before out is stored, which the compiler must
+        // assume may alias it.
+        constexpr bool HAS_Y = EPI != EPI_D;
+        constexpr bool EARLY_Y = HAS_Y && P == P16;
+        C<T> y[12];
+        if constexpr (EARLY_Y) load_spinor<P>(a.y, V, x, y);
         C<T> acc[12];
         apply_D_site<P>(a.g, a.in, a.U, a.A, (T)a.kappa, x, acc);
+        if constexpr (HAS_Y && !EARLY_Y) load_spinor<P>(a.y, V, x, y);
 
         if constexpr (EPI == EPI_XMY || EPI == EPI_XMY_NORM) {
-            C<T> y[12];
-            load_spinor<P>(a.y, V, x, y);
 #pragma unroll
             for (int k = 0; k < 12; k++) acc[k] = csub(y[k], acc[k]);
         }
@@ -50,10 +58,8 @@ __global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
             T n2 = 0;
 #pragma unroll
             for (int k = 0; k < 12; k++) n2 += acc[k].r * acc[k].r + acc[k].i * acc[k].i;
-            red[0] = (double)n2;
+            part[0] = n2;
         } else if constexpr (EPI == EPI_RV || EPI == EPI_TS) {
-            C<T> y[12];
-            load_spinor<P>(a.y, V, x, y);
             T dr = 0, di = 0, n2 = 0;
 #pragma unroll
             for (int k = 0; k < 12; k++) {
@@ -63,14 +69,15 @@ __global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
                 di += p.i;
                 n2 += acc[k].r * acc[k].r + acc[k].i * acc[k].i;
             }
-            red[0] = (double)dr;
-            red[1] = (double)di;
-            red[2] = (double)n2;
+            part[0] = dr;
+            part[1] = di;
+            part[2] = n2;
         }
     }
 
     if constexpr (NRED > 0) {
-        if (grid_sum<NRED>(red, rs_partials(a.rs, r), rs_counter(a.rs, r), bid, nblk)) {
+        double red[NRED];
+        if (grid_sum<NRED, T>(part, red, rs_partials(a.rs, r), rs_counter(a.rs, r), bid, nblk)) {
             if constexpr (EPI == EPI_XMY_NORM) {
                 sc->aux[a.aux_slot] = red[0];
             } else if constexpr (EPI == EPI_RV) {
@@ -97,6 +104,21 @@ __global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
     }
 }
 
+// FP16 sites with an epilogue fit in 80 registers, which allows 3 resident
+// blocks of 256 threads per SM instead of 2; the other kernels keep the
+// compiler's choice (a register bound there makes it spill).
+template <int P, int EPI, int NT>
+__global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
+{
+    dslash_body<P, EPI, NT>(a);
+}
+
+template <int EPI, int NT>
+__global__ void __launch_bounds__(NT, 3) dslash_f16_kernel(DslashArgs a)
+{
+    dslash_body<P16, EPI, NT>(a);
+}
+
 template <int P, int EPI>
 static cudaError_t launch_one(const DslashArgs &a, cudaStream_t st)
 {
@@ -106,7 +128,10 @@ static cudaError_t launch_one(const DslashArgs &a, cudaStream_t st)
     if (EPI == EPI_XMY_NORM || EPI == EPI_RV || EPI == EPI_TS) {
         if (nb > a.rs.max_blocks) return cudaErrorInvalidConfiguration;
     }
-    dslash_kernel<P, EPI, NT><<<(unsigned)(nb * a.nrhs), NT, 0, st>>>(a);
+    if constexpr (P == P16 && EPI != EPI_D)
+        dslash_f16_kernel<EPI, NT><<<(unsigned)(nb * a.nrhs), NT, 0, st>>>(a);
+    else
+        dslash_kernel<P, EPI, NT><<<(unsigned)(nb * a.nrhs), NT, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }

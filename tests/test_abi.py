@@ -61,6 +61,10 @@ def test_host_side_calls_without_gpu(libpath):
     assert lib.qdd_create_lattice(ctypes.byref(h), dims, bad_bc, 1, None) == qdd.QDD_ERR_ARG
     assert lib.qdd_create_lattice(ctypes.byref(h), dims, bc, 0, None) == qdd.QDD_ERR_ARG
     assert lib.qdd_create_lattice(ctypes.byref(h), dims, bc, 65, None) == qdd.QDD_ERR_ARG
+    # 4096 x 4096 x 8 x 1 = 134M sites: above the 32-bit plane-index cap
+    big = (ctypes.c_int * 4)(4096, 4096, 8, 1)
+    assert lib.qdd_create_lattice(ctypes.byref(h), big, bc, 1, None) == qdd.QDD_ERR_ARG
+    assert "119304647" in qdd.last_error()
     assert lib.qdd_destroy_lattice(None) == qdd.QDD_OK
 
 
