@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(BLAS_NT) blas_kernel(BlasArgs a)
             store_spinor<P>(a.f[5], V, x, z);
             T n2 = 0;
 #pragma unroll
-            for (int k = 0; k < 12; k++) n2 += b[k].r * b[k].r + b[k].i * b[k].i;
+            for (int k = 0; k < 12; k++) cnorm_acc(b[k], n2);
             part[0] += n2;
         } else if constexpr (OP == B_P) {
             C<T> p[12], r[12], v[12];
@@ -72,21 +72,21 @@ __global__ void __launch_bounds__(BLAS_NT) blas_kernel(BlasArgs a)
             load_spinor<P>(a.f[1], V, x, r);
             load_spinor<P>(a.f[2], V, x, v);
 #pragma unroll
-            for (int k = 0; k < 12; k++) p[k] = cadd(r[k], cmul(c1, csub(p[k], cmul(c2, v[k]))));
+            for (int k = 0; k < 12; k++) p[k] = cfma(c1, cfma(cneg(c2), v[k], p[k]), r[k]);
             store_spinor<P>(a.f[0], V, x, p);
         } else if constexpr (OP == B_S) {
             C<T> r[12], v[12];
             load_spinor<P>(a.f[1], V, x, r);
             load_spinor<P>(a.f[2], V, x, v);
 #pragma unroll
-            for (int k = 0; k < 12; k++) r[k] = csub(r[k], cmul(c1, v[k]));
+            for (int k = 0; k < 12; k++) r[k] = cfma(cneg(c1), v[k], r[k]);
             store_spinor<P>(a.f[0], V, x, r);
         } else if constexpr (OP == B_NORM) {
             C<T> f[12];
             load_spinor<P>(a.f[0], V, x, f);
             T n2 = 0;
 #pragma unroll
-            for (int k = 0; k < 12; k++) n2 += f[k].r * f[k].r + f[k].i * f[k].i;
+            for (int k = 0; k < 12; k++) cnorm_acc(f[k], n2);
             part[0] += n2;
         } else if constexpr (OP == B_COPY) {
             C<T> f[12];
@@ -105,7 +105,7 @@ __global__ void __launch_bounds__(BLAS_NT) blas_kernel(BlasArgs a)
             store_spinor<P>(a.f[3], V, x, z);
             T n2 = 0;
 #pragma unroll
-            for (int k = 0; k < 12; k++) n2 += r[k].r * r[k].r + r[k].i * r[k].i;
+            for (int k = 0; k < 12; k++) cnorm_acc(r[k], n2);
             part[0] += n2;
         }
     }
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(BLAS_NT) bicg_xr_kernel(BlasArgs a)
         load_spinor<P>(a.f[1], V, x, ph);
         load_spinor<P>(a.f[2], V, x, sh);
 #pragma unroll
-        for (int k = 0; k < 12; k++) xx[k] = cadd(xx[k], cadd(cmul(al, ph[k]), cmul(om, sh[k])));
+        for (int k = 0; k < 12; k++) xx[k] = cfma(om, sh[k], cfma(al, ph[k], xx[k]));
         store_spinor<P>(a.f[0], V, x, xx);
         C<T> s[12], t[12], rh[12];
         load_spinor<P>(a.f[4], V, x, s);
@@ -166,11 +166,9 @@ __global__ void __launch_bounds__(BLAS_NT) bicg_xr_kernel(BlasArgs a)
         T dr = 0, di = 0, n2 = 0;
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-            s[k] = csub(s[k], cmul(om, t[k]));
-            C<T> p = cmulc(rh[k], s[k]);
-            dr += p.r;
-            di += p.i;
-            n2 += s[k].r * s[k].r + s[k].i * s[k].i;
+            s[k] = cfma(cneg(om), t[k], s[k]);
+            cdot_acc(rh[k], s[k], dr, di);
+            cnorm_acc(s[k], n2);
         }
         store_spinor<P>(a.f[3], V, x, s);
         part[0] += dr;

@@ -36,6 +36,38 @@ template <typename T> __device__ __forceinline__ C<T> cmulc(C<T> a, C<T> b)
 {
     return {a.r * b.r + a.i * b.i, a.r * b.i - a.i * b.r};
 }
+// c + a b and c + conj(a) b as chains of four fused multiply-adds: written
+// as cadd(c, cmul(a, b)) the compiler, which does not reassociate, emits two
+// multiplies, two fused multiply-adds and two adds.
+template <typename T> __device__ __forceinline__ C<T> cfma(C<T> a, C<T> b, C<T> c)
+{
+    c.r = fma(a.r, b.r, c.r);
+    c.r = fma(-a.i, b.i, c.r);
+    c.i = fma(a.r, b.i, c.i);
+    c.i = fma(a.i, b.r, c.i);
+    return c;
+}
+template <typename T> __device__ __forceinline__ C<T> cfmac(C<T> a, C<T> b, C<T> c)
+{
+    c.r = fma(a.r, b.r, c.r);
+    c.r = fma(a.i, b.i, c.r);
+    c.i = fma(a.r, b.i, c.i);
+    c.i = fma(-a.i, b.r, c.i);
+    return c;
+}
+// (re, im) += conj(a) b and n += |a|^2, also as fused multiply-add chains
+template <typename T> __device__ __forceinline__ void cdot_acc(C<T> a, C<T> b, T &re, T &im)
+{
+    re = fma(a.r, b.r, re);
+    re = fma(a.i, b.i, re);
+    im = fma(a.r, b.i, im);
+    im = fma(-a.i, b.r, im);
+}
+template <typename T> __device__ __forceinline__ void cnorm_acc(C<T> a, T &n)
+{
+    n = fma(a.r, a.r, n);
+    n = fma(a.i, a.i, n);
+}
 template <typename T> __device__ __forceinline__ C<T> cscale(C<T> a, T s) { return {a.r * s, a.i * s}; }
 template <typename T> __device__ __forceinline__ C<T> ci(C<T> a) { return {-a.i, a.r}; }    // i a
 template <typename T> __device__ __forceinline__ C<T> cmi(C<T> a) { return {a.i, -a.r}; }   // -i a
@@ -181,9 +213,9 @@ template <typename T>
 __device__ __forceinline__ void rebuild_row2(C<T> (&U)[9])
 {
     // row2 = conj(row0 x row1) for an SU(3) matrix
-    U[6] = cconj(csub(cmul(U[1], U[5]), cmul(U[2], U[4])));
-    U[7] = cconj(csub(cmul(U[2], U[3]), cmul(U[0], U[5])));
-    U[8] = cconj(csub(cmul(U[0], U[4]), cmul(U[1], U[3])));
+    U[6] = cconj(cfma(U[1], U[5], cneg(cmul(U[2], U[4]))));
+    U[7] = cconj(cfma(U[2], U[3], cneg(cmul(U[0], U[5]))));
+    U[8] = cconj(cfma(U[0], U[4], cneg(cmul(U[1], U[3]))));
 }
 
 template <int P, typename T>
@@ -243,15 +275,22 @@ __device__ __forceinline__ void hop(C<T> (&acc)[12], const C<T> (&s)[12], const 
     C<T> w0[3], w1[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        C<T> p = {0, 0}, q = {0, 0};
+        C<T> p, q;
+        if constexpr (FWD) {
+            p = cmul(U[a * 3], h0[0]);
+            q = cmul(U[a * 3], h1[0]);
+        } else {
+            p = cmulc(U[a], h0[0]);
+            q = cmulc(U[a], h1[0]);
+        }
 #pragma unroll
-        for (int b = 0; b < 3; b++) {
+        for (int b = 1; b < 3; b++) {
             if constexpr (FWD) {
-                p = cadd(p, cmul(U[a * 3 + b], h0[b]));
-                q = cadd(q, cmul(U[a * 3 + b], h1[b]));
+                p = cfma(U[a * 3 + b], h0[b], p);
+                q = cfma(U[a * 3 + b], h1[b], q);
             } else {
-                p = cadd(p, cmulc(U[b * 3 + a], h0[b]));
-                q = cadd(q, cmulc(U[b * 3 + a], h1[b]));
+                p = cfmac(U[b * 3 + a], h0[b], p);
+                q = cfmac(U[b * 3 + a], h1[b], q);
             }
         }
         w0[a] = p;
@@ -351,10 +390,10 @@ __device__ __forceinline__ void clover_apply(const T (&a)[72], const C<T> (&s)[1
             for (int j = 0; j < 6; j++) {
                 if (j < i) {
                     C<T> l = {a[base + cl_off(i, j)], a[base + cl_off(i, j) + 1]};
-                    acc = cadd(acc, cmul(l, s[6 * h + j]));
+                    acc = cfma(l, s[6 * h + j], acc);
                 } else if (j > i) {
                     C<T> l = {a[base + cl_off(j, i)], a[base + cl_off(j, i) + 1]};
-                    acc = cadd(acc, cmulc(l, s[6 * h + j]));
+                    acc = cfmac(l, s[6 * h + j], acc);
                 }
             }
             o[6 * h + i] = acc;

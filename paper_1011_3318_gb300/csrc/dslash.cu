@@ -57,17 +57,16 @@ __device__ __forceinline__ void dslash_body(DslashArgs a)
         if constexpr (EPI == EPI_XMY_NORM) {
             T n2 = 0;
 #pragma unroll
-            for (int k = 0; k < 12; k++) n2 += acc[k].r * acc[k].r + acc[k].i * acc[k].i;
+            for (int k = 0; k < 12; k++) cnorm_acc(acc[k], n2);
             part[0] = n2;
         } else if constexpr (EPI == EPI_RV || EPI == EPI_TS) {
             T dr = 0, di = 0, n2 = 0;
 #pragma unroll
             for (int k = 0; k < 12; k++) {
                 // EPI_RV: <y, out> = sum conj(y) out ; EPI_TS: <out, y> = sum conj(out) y
-                C<T> p = (EPI == EPI_RV) ? cmulc(y[k], acc[k]) : cmulc(acc[k], y[k]);
-                dr += p.r;
-                di += p.i;
-                n2 += acc[k].r * acc[k].r + acc[k].i * acc[k].i;
+                if constexpr (EPI == EPI_RV) cdot_acc(y[k], acc[k], dr, di);
+                else cdot_acc(acc[k], y[k], dr, di);
+                cnorm_acc(acc[k], n2);
             }
             part[0] = dr;
             part[1] = di;

@@ -360,10 +360,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(RasArgs
             float qr = 0.f, qi = 0.f, qq = 0.f;
 #pragma unroll
             for (int k = 0; k < 12; k++) {
-                C<float> t = cmulc(q[k], own[k]);
-                qr += t.r;
-                qi += t.i;
-                qq += q[k].r * q[k].r + q[k].i * q[k].i;
+                cdot_acc(q[k], own[k], qr, qi);
+                cnorm_acc(q[k], qq);
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -395,8 +393,8 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(RasArgs
             ld_local(sv, NT, l, vv);
 #pragma unroll
             for (int k = 0; k < 12; k++) {
-                vv[k] = cadd(vv[k], cmul(al, own[k]));
-                own[k] = csub(own[k], cmul(al, q[k]));
+                vv[k] = cfma(al, own[k], vv[k]);
+                own[k] = cfma(cneg(al), q[k], own[k]);
             }
             st_local(sv, NT, l, vv);
             st_local(srho, NT, l, own);
@@ -450,10 +448,8 @@ __global__ void __launch_bounds__(RAS_GMEM_NT) ras_gmem_kernel(const RasArgs a0)
                 float s0 = 0.f, s1 = 0.f, s2 = 0.f;
 #pragma unroll
                 for (int k = 0; k < 12; k++) {
-                    C<float> t = cmulc(qq[k], own[k]);
-                    s0 += t.r;
-                    s1 += t.i;
-                    s2 += qq[k].r * qq[k].r + qq[k].i * qq[k].i;
+                    cdot_acc(qq[k], own[k], s0, s1);
+                    cnorm_acc(qq[k], s2);
                 }
                 red[0] += s0;
                 red[1] += s1;
@@ -467,8 +463,8 @@ __global__ void __launch_bounds__(RAS_GMEM_NT) ras_gmem_kernel(const RasArgs a0)
                     for (int k = 0; k < 12; k++) {
                         float2 r2 = rho[k * n + l], q2 = q[k * n + l], v2 = vv[k * n + l];
                         C<float> r = {r2.x, r2.y}, qc = {q2.x, q2.y}, vc = {v2.x, v2.y};
-                        vc = cadd(vc, cmul(al, r));
-                        r = csub(r, cmul(al, qc));
+                        vc = cfma(al, r, vc);
+                        r = cfma(cneg(al), qc, r);
                         rho[k * n + l] = make_float2(r.r, r.i);
                         vv[k * n + l] = make_float2(vc.r, vc.i);
                     }
