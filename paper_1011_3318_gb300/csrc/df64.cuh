@@ -10,7 +10,8 @@
 // compiler neither contracts nor reorders the error-free transformations.
 //
 // Used where FP64 accuracy is needed but GB300's FP64 rate (about 1/74 of its
-// FP32 rate) would dominate: the clover-term build.
+// FP32 rate) would dominate: the clover-term build and the SU(3) check of
+// the gauge import.
 #pragma once
 
 namespace qdd {
@@ -69,6 +70,36 @@ __device__ __forceinline__ DF df_fma(DF a, DF b, DF c)
 
 // Scaling by a power of two is exact.
 __device__ __forceinline__ DF df_scale2(DF a, float pow2) { return DF{a.h * pow2, a.l * pow2}; }
+
+// Accumulator for a sum of double-float products, after the Dot2 algorithm
+// of Ogita, Rump and Oishi (same paper): the products' high parts are summed
+// with two_sum, and every rounding error, together with the products' cross
+// terms, is gathered in one FP32 correction that is folded in at the end.
+// 12 instructions per product instead of 14 for a chain of df_fma.
+struct DFAcc {
+    float s, c;
+};
+
+__device__ __forceinline__ void dfacc_init(DFAcc &a, DF x, DF y)  // a = x y
+{
+    a.s = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -a.s);
+    e = __fmaf_rn(x.h, y.l, e);
+    a.c = __fmaf_rn(x.l, y.h, e);
+}
+
+__device__ __forceinline__ void dfacc_add(DFAcc &a, DF x, DF y)  // a += x y
+{
+    const float p = __fmul_rn(x.h, y.h);
+    float e = __fmaf_rn(x.h, y.h, -p);
+    e = __fmaf_rn(x.h, y.l, e);
+    e = __fmaf_rn(x.l, y.h, e);
+    const DF t = two_sum(a.s, p);
+    a.s = t.h;
+    a.c = __fadd_rn(a.c, __fadd_rn(t.l, e));
+}
+
+__device__ __forceinline__ DF dfacc_result(const DFAcc &a) { return two_sum(a.s, a.c); }
 
 struct CDF {
     DF r, i;

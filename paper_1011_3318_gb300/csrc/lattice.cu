@@ -169,25 +169,54 @@ __device__ __forceinline__ long long shifted(const Geom &g, const int c[4], int 
     return d[0] + g.stride[1] * d[1] + g.stride[2] * d[2] + g.stride[3] * d[3];
 }
 
-// Element (a, b) of the double-float link U_mu(x).
-__device__ __forceinline__ CDF udf(const float4 *Udf, long long V, int mu, long long x, int a, int b)
+// A link factor of a plaquette leaf, M = U_mu(y) or U_mu(y)^dag, as an
+// element accessor: M_ab is the double-float element at Udf[off + a sa + b sb]
+// with its imaginary part multiplied by sg (the dagger swaps the strides and
+// conjugates).  Offsets are 32-bit (the volume cap keeps 36 V below 2^32).
+struct LinkFactor {
+    unsigned off, sa, sb;
+    float sg;
+};
+
+__device__ __forceinline__ LinkFactor link_factor(unsigned V, int mu, long long y, bool dag)
 {
-    const float4 v = Udf[((long long)mu * 9 + a * 3 + b) * V + x];
-    return CDF{DF{v.x, v.y}, DF{v.z, v.w}};
+    LinkFactor f;
+    f.off = (unsigned)(mu * 9) * V + (unsigned)y;
+    f.sa = dag ? V : 3 * V;
+    f.sb = dag ? 3 * V : V;
+    f.sg = dag ? -1.f : 1.f;
+    return f;
 }
 
-// v <- M v with M = U_mu(x) or U_mu(x)^dag, in double-float.
-__device__ __forceinline__ void md_apply(const float4 *Udf, long long V, int mu, long long x, bool dag, CDF (&v)[3])
+__device__ __forceinline__ CDF lf_elem(const float4 *Udf, const LinkFactor &f, int a, int b)
 {
-    const CDF z = CDF{DF{0.f, 0.f}, DF{0.f, 0.f}};
-    CDF w[3] = {z, z, z};
+    const float4 e = Udf[f.off + a * f.sa + b * f.sb];
+    return CDF{DF{e.x, e.y}, DF{e.z * f.sg, e.w * f.sg}};
+}
+
+// v <- M v in double-float: each output component is two real dot products
+// of length 6, summed with DFAcc.
+__device__ __forceinline__ void md_apply(const float4 *Udf, const LinkFactor &f, CDF (&v)[3])
+{
+    CDF w[3];
 #pragma unroll
-    for (int a = 0; a < 3; a++)
+    for (int a = 0; a < 3; a++) {
+        DFAcc re, im;
 #pragma unroll
         for (int b = 0; b < 3; b++) {
-            if (dag) w[a] = cdf_fma_ca(udf(Udf, V, mu, x, b, a), v[b], w[a]);  // conj(U_ba) v_b
-            else w[a] = cdf_fma(udf(Udf, V, mu, x, a, b), v[b], w[a]);
+            const CDF u = lf_elem(Udf, f, a, b);
+            if (b == 0) {
+                dfacc_init(re, u.r, v[b].r);
+                dfacc_init(im, u.r, v[b].i);
+            } else {
+                dfacc_add(re, u.r, v[b].r);
+                dfacc_add(im, u.r, v[b].i);
+            }
+            dfacc_add(re, df_neg(u.i), v[b].i);
+            dfacc_add(im, u.i, v[b].r);
         }
+        w[a] = CDF{dfacc_result(re), dfacc_result(im)};
+    }
 #pragma unroll
     for (int a = 0; a < 3; a++) v[a] = w[a];
 }
@@ -221,10 +250,12 @@ __device__ __forceinline__ void leaf_factors(const Geom &g, const int c[4], long
 }
 
 // One CTA builds the clover of CL_SITES consecutive sites in three phases:
-//  1. thread (plane, site) forms Q = sum of the four leaves of its plane
-//     column by column: for column j of every leaf F0 F1 F2 F3, v = F3 e_j and
-//     then F2, F1, F0 are applied to v (double-float arithmetic); each warp
-//     handles one plane for 32 sites, so all its lanes take the same path;
+//  1. thread (plane, site) forms Q = sum of the four leaves of its plane,
+//     leaf by leaf and column by column: for column j of leaf F0 F1 F2 F3,
+//     v = F3 e_j and then F2, F1, F0 are applied to v (double-float
+//     arithmetic), and v is added to column j of Q, kept in shared memory;
+//     each warp handles one plane for 32 sites, so all its lanes take the
+//     same path;
 //  2. the entries of the two Hermitian 6x6 chiral blocks
 //     1 + i kappa c_sw [[Gz, Gx - i Gy], [Gx + i Gy, -Gz]], with
 //     Fhat = (Q - Q^dag) / 8, are packed and converted to FP64;
@@ -249,38 +280,38 @@ __global__ void __launch_bounds__(CL_THREADS) clover_build_kernel(Geom g, const 
             const int nu = plane < 3 ? plane + 1 : plane < 5 ? plane - 1 : 3;
             int c[4];
             site_coords(g, x, c);
-            const CDF z = CDF{DF{0.f, 0.f}, DF{0.f, 0.f}};
-#pragma unroll 1
-            for (int j = 0; j < 3; j++) {
-                CDF q[3] = {z, z, z};
-#pragma unroll 1
-                for (int leaf = 0; leaf < 4; leaf++) {
-                    long long fx[4];
-                    int fd[4];
-                    bool fdag[4];
-                    leaf_factors(g, c, x, mu, nu, leaf, fx, fd, fdag);
-                    CDF v[3];
 #pragma unroll
-                    for (int a = 0; a < 3; a++) {  // column j of F3
-                        if (fdag[3]) {
-                            const CDF u = udf(Udf, V, fd[3], fx[3], j, a);
-                            v[a] = CDF{u.r, df_neg(u.i)};
-                        } else {
-                            v[a] = udf(Udf, V, fd[3], fx[3], a, j);
-                        }
+            for (int k = 0; k < 9; k++)
+#pragma unroll
+                for (int q = 0; q < 4; q++) sQ[plane][k][q][site] = 0.f;
+#pragma unroll 1
+            for (int leaf = 0; leaf < 4; leaf++) {
+                long long fx[4];
+                int fd[4];
+                bool fdag[4];
+                leaf_factors(g, c, x, mu, nu, leaf, fx, fd, fdag);
+                LinkFactor lf[4];
+#pragma unroll
+                for (int f = 0; f < 4; f++) lf[f] = link_factor((unsigned)V, fd[f], fx[f], fdag[f]);
+#pragma unroll 1
+                for (int j = 0; j < 3; j++) {
+                    CDF v[3];  // column j of F3, then F2, F1, F0 applied to it
+#pragma unroll
+                    for (int a = 0; a < 3; a++) v[a] = lf_elem(Udf, lf[3], a, j);
+                    // one copy of md_apply in the loop body keeps the hot code
+                    // small enough for the instruction cache
+#pragma unroll 1
+                    for (int f = 2; f >= 0; f--) md_apply(Udf, lf[f], v);
+#pragma unroll
+                    for (int a = 0; a < 3; a++) {
+                        float *e = &sQ[plane][a * 3 + j][0][site];
+                        const DF qr = df_add(DF{e[0], e[CL_SITES]}, v[a].r);
+                        const DF qi = df_add(DF{e[2 * CL_SITES], e[3 * CL_SITES]}, v[a].i);
+                        e[0] = qr.h;
+                        e[CL_SITES] = qr.l;
+                        e[2 * CL_SITES] = qi.h;
+                        e[3 * CL_SITES] = qi.l;
                     }
-                    md_apply(Udf, V, fd[2], fx[2], fdag[2], v);
-                    md_apply(Udf, V, fd[1], fx[1], fdag[1], v);
-                    md_apply(Udf, V, fd[0], fx[0], fdag[0], v);
-#pragma unroll
-                    for (int a = 0; a < 3; a++) q[a] = CDF{df_add(q[a].r, v[a].r), df_add(q[a].i, v[a].i)};
-                }
-#pragma unroll
-                for (int a = 0; a < 3; a++) {
-                    sQ[plane][a * 3 + j][0][site] = q[a].r.h;
-                    sQ[plane][a * 3 + j][1][site] = q[a].r.l;
-                    sQ[plane][a * 3 + j][2][site] = q[a].i.h;
-                    sQ[plane][a * 3 + j][3][site] = q[a].i.l;
                 }
             }
         }
