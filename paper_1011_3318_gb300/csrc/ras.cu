@@ -84,19 +84,25 @@ __device__ __forceinline__ void dom_site(const Geom &g, const DomainGeom &dg, in
 }
 
 // Local spinor from a planar float2 [12][stride] array (shared or global).
+// Domain-local FP32 spinors: 6 planes of float4 (two complex each), so that
+// a spinor moves in 6 wide accesses.  base must be 16-byte aligned; the
+// buffers are declared as float2 [12][stride], the same footprint.
 __device__ __forceinline__ void ld_local(const float2 *base, int stride, int l, C<float> (&s)[12])
 {
+    const float4 *b = reinterpret_cast<const float4 *>(base);
 #pragma unroll
-    for (int k = 0; k < 12; k++) {
-        float2 v = base[k * stride + l];
-        s[k] = {v.x, v.y};
+    for (int q = 0; q < 6; q++) {
+        const float4 v = b[q * stride + l];
+        s[2 * q] = {v.x, v.y};
+        s[2 * q + 1] = {v.z, v.w};
     }
 }
 
 __device__ __forceinline__ void st_local(float2 *base, int stride, int l, const C<float> (&s)[12])
 {
+    float4 *b = reinterpret_cast<float4 *>(base);
 #pragma unroll
-    for (int k = 0; k < 12; k++) base[k * stride + l] = make_float2(s[k].r, s[k].i);
+    for (int q = 0; q < 6; q++) b[q * stride + l] = make_float4(s[2 * q].r, s[2 * q].i, s[2 * q + 1].r, s[2 * q + 1].i);
 }
 
 template <int P, int MU>
@@ -200,8 +206,8 @@ __device__ __forceinline__ void loc_site(const Geom &g, const DomainGeom &dg, in
 }
 
 // Shared-memory layout of one CTA (one domain, NT threads):
-//   rho  float2[12][NT]   MR residual (read by the neighbours' hops)
-//   v    float2[12][NT]   MR solution
+//   rho  float4[6][NT]    MR residual (read by the neighbours' hops)
+//   v    float4[6][NT]    MR solution
 //   U    links of the domain's sites, 4 directions, in the storage format of
 //        the field (FP16: uint2[12][NT], FP32: float4[12][NT]); the backward hop
 //        from a site uses the forward link of its neighbour, which is inside
