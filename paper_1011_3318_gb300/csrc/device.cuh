@@ -427,6 +427,70 @@ __device__ __forceinline__ void hop_pair(const Geom &g, const SpinorView &in, co
     }
 }
 
+// Clover block H (0: spins 0,1; 1: spins 2,3) of the packed site clover,
+// the 36 reals [36 H, 36 H + 36): 6 diagonal reals, then the 15 complex
+// lower entries.  FP16 values are left unscaled (the site norm is applied by
+// the caller).
+template <int P, int H, typename T>
+__device__ __forceinline__ void load_clover_block(const CloverView &A, long long V, long long x, T (&a)[36])
+{
+    const unsigned v = (unsigned)V, i = (unsigned)x;
+    if constexpr (P == P64) {
+        const double2 *p = (const double2 *)A.d;
+#pragma unroll
+        for (int k = 0; k < 18; k++) {
+            const double2 e = p[(18 * H + k) * v + i];
+            a[2 * k] = (T)e.x;
+            a[2 * k + 1] = (T)e.y;
+        }
+    } else if constexpr (P == P32) {
+        const float4 *p = (const float4 *)A.d;
+#pragma unroll
+        for (int k = 0; k < 9; k++) {
+            const float4 e = p[(9 * H + k) * v + i];
+            a[4 * k] = (T)e.x; a[4 * k + 1] = (T)e.y; a[4 * k + 2] = (T)e.z; a[4 * k + 3] = (T)e.w;
+        }
+    } else {
+        // halves [36 H, 36 H + 36) lie in the uint4 words 4 H .. 4 H + 4
+        const uint4 *p = (const uint4 *)A.d;
+#pragma unroll
+        for (int k = 0; k < 5; k++) {
+            const uint4 e = p[(4 * H + k) * v + i];
+            unsigned w[4] = {e.x, e.y, e.z, e.w};
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int pos = 8 * k + 2 * j - 4 * H;
+                if (pos >= 0 && pos < 36) {
+                    const float2 f2 = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
+                    a[pos] = (T)f2.x;
+                    a[pos + 1] = (T)f2.y;
+                }
+            }
+        }
+    }
+}
+
+// o += sc * B s for one packed Hermitian 6x6 block B.
+template <typename T>
+__device__ __forceinline__ void clover_block_acc(const T (&a)[36], const C<T> *s, C<T> *o, T sc)
+{
+#pragma unroll
+    for (int i = 0; i < 6; i++) {
+        C<T> t = cscale(s[i], a[i]);
+#pragma unroll
+        for (int j = 0; j < 6; j++) {
+            if (j < i) t = cfma(C<T>{a[cl_off(i, j)], a[cl_off(i, j) + 1]}, s[j], t);
+            else if (j > i) t = cfmac(C<T>{a[cl_off(j, i)], a[cl_off(j, i) + 1]}, s[j], t);
+        }
+        o[i].r = fma(sc, t.r, o[i].r);
+        o[i].i = fma(sc, t.i, o[i].i);
+    }
+}
+
+// D at site x.  FP32/FP64: clover term first, then the hops.  FP16: the hops
+// first, then the clover block by block, so that the clover's 72 reals are
+// never live together with the hop temporaries (the FP16 kernels are bounded
+// to 80 registers for occupancy).
 template <int P, typename T>
 __device__ __forceinline__ void apply_D_site(const Geom &g, const SpinorView &in, const LinkView &Ul,
                                              const CloverView &A, T kappa, long long x, C<T> (&acc)[12])
@@ -434,23 +498,39 @@ __device__ __forceinline__ void apply_D_site(const Geom &g, const SpinorView &in
     const long long V = g.V;
     int c[4];
     site_coords(g, x, c);
-    {
-        T av[72];
-        C<T> s[12];
-        const T na = load_clover_u<P>(A, V, x, av);
-        const T ns = load_spinor_u<P>(in, V, x, s);
-        clover_apply(av, s, acc);
-        if constexpr (P == P16) {
-            const T sc = na * ns;
-#pragma unroll
-            for (int k = 0; k < 12; k++) acc[k] = cscale(acc[k], sc);
-        }
-    }
     const T mk = -kappa;
-    hop_pair<P, 0>(g, in, Ul, x, c, acc, mk);
-    hop_pair<P, 1>(g, in, Ul, x, c, acc, mk);
-    hop_pair<P, 2>(g, in, Ul, x, c, acc, mk);
-    hop_pair<P, 3>(g, in, Ul, x, c, acc, mk);
+    if constexpr (P == P16) {
+#pragma unroll
+        for (int k = 0; k < 12; k++) acc[k] = {0, 0};
+        hop_pair<P, 0>(g, in, Ul, x, c, acc, mk);
+        hop_pair<P, 1>(g, in, Ul, x, c, acc, mk);
+        hop_pair<P, 2>(g, in, Ul, x, c, acc, mk);
+        hop_pair<P, 3>(g, in, Ul, x, c, acc, mk);
+        C<T> s[12];
+        const T sc = load_spinor_u<P>(in, V, x, s) * (T)A.n[(unsigned)x];
+        {
+            T ab[36];
+            load_clover_block<P, 0>(A, V, x, ab);
+            clover_block_acc(ab, s, acc, sc);
+        }
+        {
+            T ab[36];
+            load_clover_block<P, 1>(A, V, x, ab);
+            clover_block_acc(ab, s + 6, acc + 6, sc);
+        }
+    } else {
+        {
+            T av[72];
+            C<T> s[12];
+            load_clover<P>(A, V, x, av);
+            load_spinor<P>(in, V, x, s);
+            clover_apply(av, s, acc);
+        }
+        hop_pair<P, 0>(g, in, Ul, x, c, acc, mk);
+        hop_pair<P, 1>(g, in, Ul, x, c, acc, mk);
+        hop_pair<P, 2>(g, in, Ul, x, c, acc, mk);
+        hop_pair<P, 3>(g, in, Ul, x, c, acc, mk);
+    }
 }
 
 // ---------------------------------------------------------------- reductions

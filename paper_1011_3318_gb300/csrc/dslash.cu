@@ -103,9 +103,9 @@ __device__ __forceinline__ void dslash_body(DslashArgs a)
     }
 }
 
-// FP16 sites with an epilogue fit in 80 registers, which allows 3 resident
-// blocks of 256 threads per SM instead of 2; the other kernels keep the
-// compiler's choice (a register bound there makes it spill).
+// FP16 sites fit in 80 registers (with a few bytes of spill), which allows 3
+// resident blocks of 256 threads per SM instead of 2; FP32 and FP64 keep the
+// compiler's choice (a register bound there makes them spill heavily).
 template <int P, int EPI, int NT>
 __global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
 {
@@ -127,7 +127,7 @@ static cudaError_t launch_one(const DslashArgs &a, cudaStream_t st)
     if (EPI == EPI_XMY_NORM || EPI == EPI_RV || EPI == EPI_TS) {
         if (nb > a.rs.max_blocks) return cudaErrorInvalidConfiguration;
     }
-    if constexpr (P == P16 && EPI != EPI_D)
+    if constexpr (P == P16)
         dslash_f16_kernel<EPI, NT><<<(unsigned)(nb * a.nrhs), NT, 0, st>>>(a);
     else
         dslash_kernel<P, EPI, NT><<<(unsigned)(nb * a.nrhs), NT, 0, st>>>(a);
