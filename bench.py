@@ -23,6 +23,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -102,26 +103,56 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ helpers
+# the files that define device code: a change to any of them invalidates the
+# committed ncu traffic figures
+KERNEL_SOURCES = ("device.cuh", "df64.cuh", "qdd_internal.h", "lib.h", "dslash.cu", "ras.cu", "blas.cu", "lattice.cu")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1011_3318_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel_class):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources (else None)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch of a kernel class from the committed ncu summary
+    profiles/traffic.md, if it was taken on the current kernel sources (its
+    'sources hash' line matches), else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(p):
         return None
-    d = json.load(open(p))
-    e = d.get(kernel_class)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    text = open(p).read()
+    m = re.search(r"sources hash: `([0-9a-f]+)`", text)
+    if not m or m.group(1) != kernel_source_hash():
         return None
-    return e.get("dram_bytes_per_launch")
+    for line in text.splitlines():
+        cells = [c.strip() for c in line.strip().strip("|").split("|")]
+        if len(cells) >= 3 and cells[0] == kernel_class:
+            try:
+                return int(cells[2])
+            except ValueError:
+                return None
+    return None
+
+
+def ras_sweep_flops(blk, ov, n_dominv):
+    """Algorithmic flops of one RAS sweep over the 32^4 lattice: per domain
+    and MR iteration, the clover term and combine on every site of the
+    extended domain, only the hops that stay inside it (the Dirichlet
+    operator drops the others), and the two dot products and two axpys."""
+    ext = [b if b == L else b + 2 * ov for b, L in zip(blk, DIMS)]
+    nloc = 1
+    for e in ext:
+        nloc *= e
+    ndom = 1
+    for b, L in zip(blk, DIMS):
+        ndom *= L // b
+    kept_hops = sum(2 * nloc * ((e - 1) / e if b < L else 1.0) for e, b, L in zip(ext, blk, DIMS))
+    hop = (FLOPS_PER_SITE_D - 504 - 48) / 8
+    per_iter = nloc * (504 + 48 + 96 + 48) + kept_hops * hop
+    return ndom * n_dominv * per_iter
 
 
 def oracle_counts():
@@ -271,10 +302,11 @@ def run_ours(args, rank, world):
         tune = {"seconds": round(time.perf_counter() - t0, 2), "best_solve_ms": round(best_ms, 2),
                 "block": list(params.block), "overlap": params.overlap, "n_dominv": params.n_dominv,
                 "n_ras": params.n_ras, "ras_kernel": params.ras_kernel,
-                "inner_prec": {0: "f64", 1: "f32", 2: "f16"}[params.inner_prec]}
+                "inner_prec": {0: "f64", 1: "f32", 2: "f16"}[params.inner_prec], "inner_tol": params.inner_tol}
         log(f"autotune: {tune}")
     blk, ov, nd, nr = list(params.block), params.overlap, params.n_dominv, params.n_ras
     args.prec = {1: "f32", 2: "f16"}.get(params.inner_prec, args.prec)
+    args.inner_tol = params.inner_tol
 
     def step():
         qdd.load_gauge(lat, dU)           # gauge import + invalidates the clover: rebuilt inside the solve
@@ -331,13 +363,7 @@ def run_ours(args, rank, world):
     fp32_alu_peak = NOMINAL["sms"] * NOMINAL["fp32_lanes"] * 2 * NOMINAL["sm_max_mhz"] * 1e6 / 1e12
     if dom == "ras":
         ms_l = prof["ras"][0] / max(1, prof["ras"][1])
-        nloc = 1
-        for b, L in zip(blk, DIMS):
-            nloc *= b if b == L else b + 2 * ov
-        ndom = 1
-        for b, L in zip(blk, DIMS):
-            ndom *= L // b
-        flops = ndom * nloc * nd * (FLOPS_PER_SITE_D + 96 + 48)
+        flops = ras_sweep_flops(blk, ov, nd)
         ach = flops / (ms_l * 1e-3) / 1e12
         roof = {"kernel": "ras_smem_kernel (RAS sweep)", "bound": "alu", "achieved": round(ach, 2),
                 "peak": round(fp32_alu_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_alu_peak, 3),
@@ -590,7 +616,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
                     help="use --block/--overlap/--n-dominv/--n-ras as given instead of tuning them")
-    ap.add_argument("--tune-trials", dest="tune_trials", type=int, default=36)
+    ap.add_argument("--tune-trials", dest="tune_trials", type=int, default=40)
     ap.add_argument("--workload", choices=("solve", "mrhs", "batch"), default="solve",
                     help="solve: the 32^4 headline; mrhs / batch: the batched workloads")
     ap.add_argument("--kernels", default=None,

@@ -11,7 +11,8 @@
 //   2. the block shape (16 .. 256-site blocks, one orientation per shape),
 //   3. (N_dominv, NRAS) again around the best point on the best shape,
 //   4. overlap s = 1 on the best shape when its extended domain stays small,
-//   5. the staging variant of the sweep kernel, then the other inner precision.
+//   5. the staging variant of the sweep kernel, then the other inner precision,
+//   6. FP32 inner storage with a tighter inner tolerance (fewer outer steps).
 #include <chrono>
 #include <cstring>
 #include <vector>
@@ -30,7 +31,8 @@ struct Trial {
 bool same_ras(const qdd_solver_params &a, const qdd_solver_params &b)
 {
     return memcmp(a.block, b.block, sizeof(a.block)) == 0 && a.overlap == b.overlap && a.n_dominv == b.n_dominv &&
-           a.n_ras == b.n_ras && a.ras_kernel == b.ras_kernel && a.inner_prec == b.inner_prec;
+           a.n_ras == b.n_ras && a.ras_kernel == b.ras_kernel && a.inner_prec == b.inner_prec &&
+           a.inner_tol == b.inner_tol;
 }
 
 }  // namespace
@@ -116,6 +118,21 @@ qdd_status autotune_impl(qdd_lattice *lat, double *phi_dev, const double *eta_de
         q.inner_prec = q.inner_prec == QDD_F16 ? QDD_F32 : QDD_F16;
         trial(q);
         if (st != QDD_OK) return st;
+    }
+    // a tighter inner tolerance trades inner iterations for fewer outer
+    // steps (each one an FP64 D): worth it only with FP32 storage, whose
+    // iterates resolve residuals far below FP16's 2^-11
+    {
+        const double tols[] = {1e-4, 1e-5};
+        const qdd_solver_params base_t = best.p;
+        for (double t : tols) {
+            qdd_solver_params q = base_t;
+            q.inner_prec = QDD_F32;
+            if (t >= q.inner_tol) continue;
+            q.inner_tol = t;
+            trial(q);
+            if (st != QDD_OK) return st;
+        }
     }
     if (best.ms >= 1e299) {
         set_error("autotune: no candidate converged");
