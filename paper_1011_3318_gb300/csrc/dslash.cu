@@ -10,10 +10,57 @@
 // served by L1/L2, leaving the compulsory traffic (spinor in, links, clover,
 // spinor out) for HBM.  Epilogues fuse the residual update and the dot
 // products of BiCGStab, so those need no separate pass over memory.
+#include <atomic>
+
 #include "device.cuh"
 #include "lib.h"
 
 namespace qdd {
+
+// D at site x followed by the epilogue; the epilogue's dot products are added
+// to part.
+template <int P, int EPI>
+__device__ __forceinline__ void dslash_site(const DslashArgs &a, long long V, long long x,
+                                            typename RealOf<P>::T (&part)[3])
+{
+    typedef typename RealOf<P>::T T;
+    // the epilogue's second vector: in FP16 it is loaded before the stencil
+    // so that its latency overlaps the site arithmetic (in FP32/FP64 the
+    // registers would cost occupancy).  It is always loaded before out is
+    // stored, which the compiler must assume may alias it.
+    constexpr bool HAS_Y = EPI != EPI_D;
+    constexpr bool EARLY_Y = HAS_Y && P == P16;
+    C<T> y[12];
+    if constexpr (EARLY_Y) load_spinor<P>(a.y, V, x, y);
+    C<T> acc[12];
+    apply_D_site<P>(a.g, a.in, a.U, a.A, (T)a.kappa, x, acc);
+    if constexpr (HAS_Y && !EARLY_Y) load_spinor<P>(a.y, V, x, y);
+
+    if constexpr (EPI == EPI_XMY || EPI == EPI_XMY_NORM) {
+#pragma unroll
+        for (int k = 0; k < 12; k++) acc[k] = csub(y[k], acc[k]);
+    }
+    store_spinor<P>(a.out, V, x, acc);
+
+    if constexpr (EPI == EPI_XMY_NORM) {
+        T n2 = 0;
+#pragma unroll
+        for (int k = 0; k < 12; k++) cnorm_acc(acc[k], n2);
+        part[0] += n2;
+    } else if constexpr (EPI == EPI_RV || EPI == EPI_TS) {
+        T dr = 0, di = 0, n2 = 0;
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            // EPI_RV: <y, out> = sum conj(y) out ; EPI_TS: <out, y> = sum conj(out) y
+            if constexpr (EPI == EPI_RV) cdot_acc(y[k], acc[k], dr, di);
+            else cdot_acc(acc[k], y[k], dr, di);
+            cnorm_acc(acc[k], n2);
+        }
+        part[0] += dr;
+        part[1] += di;
+        part[2] += n2;
+    }
+}
 
 template <int P, int EPI, int NT>
 __device__ __forceinline__ void dslash_body(DslashArgs a)
@@ -30,53 +77,25 @@ __device__ __forceinline__ void dslash_body(DslashArgs a)
     a.out = rhs_view<P>(a.out, V, r);
     a.in = rhs_view<P>(a.in, V, r);
     a.y = rhs_view<P>(a.y, V, r);
-    const long long x = (long long)bid * NT + threadIdx.x;
-    const bool active = x < V;
-    T part[NRED > 0 ? NRED : 1] = {0};
+    T part[3] = {0, 0, 0};
 
-    if (active) {
-        // the epilogue's second vector: in FP16 it is loaded before the
-        // stencil so that its latency overlaps the site arithmetic (it costs
-        // 13 registers there; in FP32/FP64 it would cost occupancy).  It is
-        // always loaded before out is stored, which the compiler must
-        // assume may alias it.
-        constexpr bool HAS_Y = EPI != EPI_D;
-        constexpr bool EARLY_Y = HAS_Y && P == P16;
-        C<T> y[12];
-        if constexpr (EARLY_Y) load_spinor<P>(a.y, V, x, y);
-        C<T> acc[12];
-        apply_D_site<P>(a.g, a.in, a.U, a.A, (T)a.kappa, x, acc);
-        if constexpr (HAS_Y && !EARLY_Y) load_spinor<P>(a.y, V, x, y);
-
-        if constexpr (EPI == EPI_XMY || EPI == EPI_XMY_NORM) {
-#pragma unroll
-            for (int k = 0; k < 12; k++) acc[k] = csub(y[k], acc[k]);
-        }
-        store_spinor<P>(a.out, V, x, acc);
-
-        if constexpr (EPI == EPI_XMY_NORM) {
-            T n2 = 0;
-#pragma unroll
-            for (int k = 0; k < 12; k++) cnorm_acc(acc[k], n2);
-            part[0] = n2;
-        } else if constexpr (EPI == EPI_RV || EPI == EPI_TS) {
-            T dr = 0, di = 0, n2 = 0;
-#pragma unroll
-            for (int k = 0; k < 12; k++) {
-                // EPI_RV: <y, out> = sum conj(y) out ; EPI_TS: <out, y> = sum conj(out) y
-                if constexpr (EPI == EPI_RV) cdot_acc(y[k], acc[k], dr, di);
-                else cdot_acc(acc[k], y[k], dr, di);
-                cnorm_acc(acc[k], n2);
-            }
-            part[0] = dr;
-            part[1] = di;
-            part[2] = n2;
-        }
+    // one site per thread for the plain epilogues; the reducing ones run on a
+    // grid of resident blocks that strides over the lattice, so that each
+    // block reduces (and waits at its barrier) once for many sites
+    if constexpr (NRED > 0) {
+        for (long long x = (long long)bid * NT + threadIdx.x; x < V; x += (long long)nblk * NT)
+            dslash_site<P, EPI>(a, V, x, part);
+    } else {
+        const long long x = (long long)bid * NT + threadIdx.x;
+        if (x < V) dslash_site<P, EPI>(a, V, x, part);
     }
 
     if constexpr (NRED > 0) {
         double red[NRED];
-        if (grid_sum<NRED, T>(part, red, rs_partials(a.rs, r), rs_counter(a.rs, r), bid, nblk)) {
+        T pr[NRED];
+#pragma unroll
+        for (int k = 0; k < NRED; k++) pr[k] = part[k];
+        if (grid_sum<NRED, T>(pr, red, rs_partials(a.rs, r), rs_counter(a.rs, r), bid, nblk)) {
             if constexpr (EPI == EPI_XMY_NORM) {
                 sc->aux[a.aux_slot] = red[0];
             } else if constexpr (EPI == EPI_RV) {
@@ -104,8 +123,10 @@ __device__ __forceinline__ void dslash_body(DslashArgs a)
 }
 
 // FP16 sites fit in 80 registers (with a few bytes of spill), which allows 3
-// resident blocks of 256 threads per SM instead of 2; FP32 and FP64 keep the
-// compiler's choice (a register bound there makes them spill heavily).
+// resident blocks of 256 threads per SM instead of 2; the reducing FP16
+// epilogues, whose threads loop over sites, keep 2 blocks (at 80 registers
+// their loop spills).  FP32 and FP64 keep the compiler's register choice (a
+// register bound there makes them spill heavily).
 template <int P, int EPI, int NT>
 __global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
 {
@@ -113,24 +134,49 @@ __global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
 }
 
 template <int EPI, int NT>
-__global__ void __launch_bounds__(NT, 3) dslash_f16_kernel(DslashArgs a)
+__global__ void __launch_bounds__(NT, (EPI == EPI_RV || EPI == EPI_TS) ? 2 : 3) dslash_f16_kernel(DslashArgs a)
 {
     dslash_body<P16, EPI, NT>(a);
+}
+
+// SMs x resident blocks per SM of one kernel on the current device, queried
+// once per device (the values are the same for every caller).
+template <int P, int EPI>
+static long long resident_blocks(void (*kernel)(DslashArgs), int nt)
+{
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v == 0) {
+        int sms = 0, per = 0;
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, nt, 0) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        v = sms * (per > 0 ? per : 1);
+        cache[dev].store(v, std::memory_order_relaxed);
+    }
+    return v;
 }
 
 template <int P, int EPI>
 static cudaError_t launch_one(const DslashArgs &a, cudaStream_t st)
 {
     constexpr int NT = (P == P64) ? 128 : 256;
-    const long long nb = (a.g.V + NT - 1) / NT;
+    constexpr bool RED = EPI == EPI_XMY_NORM || EPI == EPI_RV || EPI == EPI_TS;
+    void (*kernel)(DslashArgs);
+    if constexpr (P == P16) kernel = dslash_f16_kernel<EPI, NT>;
+    else kernel = dslash_kernel<P, EPI, NT>;
+    long long nb = (a.g.V + NT - 1) / NT;
     if (a.nrhs < 1) return cudaErrorInvalidValue;
-    if (EPI == EPI_XMY_NORM || EPI == EPI_RV || EPI == EPI_TS) {
+    if constexpr (RED) {
+        const long long cap = resident_blocks<P, EPI>(kernel, NT);
+        if (cap > 0 && nb > cap) nb = cap;
         if (nb > a.rs.max_blocks) return cudaErrorInvalidConfiguration;
     }
-    if constexpr (P == P16)
-        dslash_f16_kernel<EPI, NT><<<(unsigned)(nb * a.nrhs), NT, 0, st>>>(a);
-    else
-        dslash_kernel<P, EPI, NT><<<(unsigned)(nb * a.nrhs), NT, 0, st>>>(a);
+    kernel<<<(unsigned)(nb * a.nrhs), NT, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
