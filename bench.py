@@ -616,7 +616,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
                     help="use --block/--overlap/--n-dominv/--n-ras as given instead of tuning them")
-    ap.add_argument("--tune-trials", dest="tune_trials", type=int, default=40)
+    ap.add_argument("--tune-trials", dest="tune_trials", type=int, default=42)
     ap.add_argument("--workload", choices=("solve", "mrhs", "batch"), default="solve",
                     help="solve: the 32^4 headline; mrhs / batch: the batched workloads")
     ap.add_argument("--kernels", default=None,

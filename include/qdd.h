@@ -193,8 +193,9 @@ qdd_status qdd_solve_batch(qdd_lattice *const *lats, double *const *phi, const d
 /* Chooses the RAS parameters that minimise the time of a whole solve of
  * D phi = eta (the paper's parameter survey of Sec. 5, done by timing):
  * coordinate search over (n_dominv, n_ras), block shapes of 16 to 256 sites,
- * overlap 1, the sweep kernel's staging variant, the inner precision and,
- * with FP32 inner storage, inner tolerances 1e-4 and 1e-5; at most
+ * overlap 1, the sweep kernel's staging variant, the inner precision and
+ * tighter inner tolerances (3e-4 with FP16 storage, 1e-4 and 1e-5 with
+ * FP32 storage); at most
  * max_trials solves.  params is the starting point
  * (inner_prec QDD_F32 or QDD_F16, use_ras = 1) and receives the best
  * parameters; best_ms (may be NULL) receives the best solve time.  eta is a

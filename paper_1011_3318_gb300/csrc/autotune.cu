@@ -12,7 +12,8 @@
 //   3. (N_dominv, NRAS) again around the best point on the best shape,
 //   4. overlap s = 1 on the best shape when its extended domain stays small,
 //   5. the staging variant of the sweep kernel, then the other inner precision,
-//   6. FP32 inner storage with a tighter inner tolerance (fewer outer steps).
+//   6. tighter inner tolerances (fewer outer steps): 3e-4 with FP16 storage,
+//      1e-4 and 1e-5 with FP32 storage.
 #include <chrono>
 #include <cstring>
 #include <vector>
@@ -120,16 +121,19 @@ qdd_status autotune_impl(qdd_lattice *lat, double *phi_dev, const double *eta_de
         if (st != QDD_OK) return st;
     }
     // a tighter inner tolerance trades inner iterations for fewer outer
-    // steps (each one an FP64 D): worth it only with FP32 storage, whose
-    // iterates resolve residuals far below FP16's 2^-11
+    // steps (each one an FP64 D): FP16 storage resolves residuals only a
+    // little below 1e-3 (its 2^-11 rounding), FP32 storage far below
     {
-        const double tols[] = {1e-4, 1e-5};
         const qdd_solver_params base_t = best.p;
-        for (double t : tols) {
+        const struct {
+            int prec;
+            double tol;
+        } cands[] = {{QDD_F16, 3e-4}, {QDD_F32, 1e-4}, {QDD_F32, 1e-5}};
+        for (const auto &c : cands) {
             qdd_solver_params q = base_t;
-            q.inner_prec = QDD_F32;
-            if (t >= q.inner_tol) continue;
-            q.inner_tol = t;
+            q.inner_prec = c.prec;
+            if (c.tol >= q.inner_tol) continue;
+            q.inner_tol = c.tol;
             trial(q);
             if (st != QDD_OK) return st;
         }

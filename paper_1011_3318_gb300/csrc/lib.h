@@ -127,7 +127,16 @@ struct RasArgs {
     int slots;
     int nrhs;
     int variant;        // qdd_solver_params::ras_kernel
+    // Fused BiCGStab update (shared-memory kernel only): instead of reading
+    // `in`, the sweep stages in = fr + b fy + c fz with the coefficients of
+    // the solver scalars, and writes that vector to `in` on its bulk sites.
+    //   RAS_FUSE_P: p = r + beta (p - omega v)  (fr = r, fy = p = in, fz = v)
+    //   RAS_FUSE_S: s = r - alpha v             (fr = r, fz = v)
+    int fuse;
+    SpinorView fr, fz;
 };
+
+enum { RAS_FUSE_NONE = 0, RAS_FUSE_P = 1, RAS_FUSE_S = 2 };
 
 // Sites of an extended domain up to which the shared-memory kernel is used.
 constexpr int RAS_SMEM_MAX_SITES = 512;
@@ -207,7 +216,14 @@ qdd_status run_dslash(qdd_lattice *lat, int prec, int epi, SpinorView out, Spino
                       int aux_slot);
 qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params *p, const DomainGeom &dg,
                             SpinorView out, SpinorView in, SpinorView rho, SpinorView v, double kappa, int *dv,
-                            const Scalars *sc);
+                            const Scalars *sc,
+                            int fuse = RAS_FUSE_NONE, SpinorView fr = SpinorView{nullptr, nullptr},
+                            SpinorView fz = SpinorView{nullptr, nullptr});
+// Whether the first sweep of ras_apply_fields can form the BiCGStab update
+// `fuse` while staging (shared-memory kernel; the in-place p update also
+// needs domains without overlap, whose halo would read p after another
+// domain has written it).
+bool ras_can_fuse(int prec, const DomainGeom &dg, int fuse);
 qdd_status solve_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, double kappa, double csw, double tol,
                       const qdd_solver_params *p, qdd_solve_info *info);
 qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, const double *const *eta_dev, int n,

@@ -155,6 +155,44 @@ __device__ __forceinline__ void write_outputs(const RasArgs &a, long long x, con
     }
 }
 
+// The sweep's input at site x: `in`, or with a fused BiCGStab update
+// r + b y + c v (y = in for RAS_FUSE_P, absent for RAS_FUSE_S) in FP32.
+template <int P>
+__device__ __forceinline__ void staged_input(const RasArgs &a, long long V, long long x, C<float> b, C<float> c,
+                                             C<float> (&out)[12])
+{
+    if (a.fuse == RAS_FUSE_NONE) {
+        load_spinor<P>(a.in, V, x, out);
+        return;
+    }
+    C<float> t[12];
+    load_spinor<P>(a.fr, V, x, out);
+    load_spinor<P>(a.fz, V, x, t);
+#pragma unroll
+    for (int k = 0; k < 12; k++) out[k] = cfma(c, t[k], out[k]);
+    if (a.fuse == RAS_FUSE_P) {
+        load_spinor<P>(a.in, V, x, t);
+#pragma unroll
+        for (int k = 0; k < 12; k++) out[k] = cfma(b, t[k], out[k]);
+    }
+}
+
+// Coefficients (b, c) of the fused update from the solver scalars.
+__device__ __forceinline__ void fuse_coefs(const RasArgs &a, int rr, C<float> &b, C<float> &c)
+{
+    b = {0.f, 0.f};
+    c = {0.f, 0.f};
+    if (a.fuse == RAS_FUSE_P) {
+        const double2 be = a.sc[rr].beta, om = a.sc[rr].omega;
+        b = {(float)be.x, (float)be.y};
+        const double2 bo = zmul(be, om);
+        c = {(float)-bo.x, (float)-bo.y};
+    } else if (a.fuse == RAS_FUSE_S) {
+        const double2 al = a.sc[rr].alpha;
+        c = {(float)-al.x, (float)-al.y};
+    }
+}
+
 // Compact description of one site of the extended domain held by a thread
 // of the shared-memory kernel.
 struct LocSite {
@@ -269,6 +307,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(RasArgs
     a.in = rhs_view<P>(a.in, a.g.V, rr);
     a.vout = rhs_view<P>(a.vout, a.g.V, rr);
     a.acc = rhs_view<P>(a.acc, a.g.V, rr);
+    a.fr = rhs_view<P>(a.fr, a.g.V, rr);
+    a.fz = rhs_view<P>(a.fz, a.g.V, rr);
+    C<float> fb, fc;
+    fuse_coefs(a, rr, fb, fc);
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ float wpart[3][NT / 32];
     float2 *srho = reinterpret_cast<float2 *>(smem);
@@ -289,7 +331,11 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(RasArgs
         C<float> r[12], z[12];
 #pragma unroll
         for (int k = 0; k < 12; k++) { r[k] = {0.f, 0.f}; z[k] = {0.f, 0.f}; }
-        if (act) load_spinor<P>(a.in, V, s.x, r);
+        if (act) {
+            staged_input<P>(a, V, s.x, fb, fc, r);
+            // the fused update's result, on the bulk sites (each written once)
+            if (a.fuse != RAS_FUSE_NONE && (s.m & M_BULK)) store_spinor<P>(a.in, V, s.x, r);
+        }
         st_local(srho, NT, l, r);
         st_local(sv, NT, l, z);
         if (act) {
@@ -532,7 +578,8 @@ static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
         if (n <= 256) return launch_smem<P, 256, P == P16>(a, st);
         if (n <= RAS_SMEM_MAX_SITES) return launch_smem<P, 512, P == P16>(a, st);
     }
-    if (!a.scratch || a.slots < 1) return cudaErrorInvalidValue;
+    // the general kernel has no fused update (the caller checks ras_can_fuse)
+    if (a.fuse != RAS_FUSE_NONE || !a.scratch || a.slots < 1) return cudaErrorInvalidValue;
     const long long items = (long long)a.dg.ndom * a.nrhs;
     const int grid = a.slots < items ? a.slots : (int)items;
     ras_gmem_kernel<P><<<grid, RAS_GMEM_NT, 0, st>>>(a);
@@ -555,7 +602,8 @@ cudaError_t launch_ras_block(int prec, const RasArgs &a, cudaStream_t st)
 template <int P>
 static cudaError_t launch_gmem_p(const RasArgs &a, cudaStream_t st)
 {
-    if (!a.scratch || a.slots < 1) return cudaErrorInvalidValue;
+    // the general kernel has no fused update (the caller checks ras_can_fuse)
+    if (a.fuse != RAS_FUSE_NONE || !a.scratch || a.slots < 1) return cudaErrorInvalidValue;
     const long long items = (long long)a.dg.ndom * a.nrhs;
     const int grid = a.slots < items ? a.slots : (int)items;
     ras_gmem_kernel<P><<<grid, RAS_GMEM_NT, 0, st>>>(a);

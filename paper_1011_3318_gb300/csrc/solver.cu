@@ -157,9 +157,18 @@ static qdd_status ensure_ras_scratch(qdd_lattice *lat, const DomainGeom &dg)
 // out = K_RAS in (Alg. 1): sweep j projects, solves and restricts on every
 // domain (one launch), accumulates phi += v, and updates rho = rho - D v
 // except after the last sweep, where phi no longer depends on rho.
+bool ras_can_fuse(int prec, const DomainGeom &dg, int fuse)
+{
+    if (prec == P64 || dg.nloc > RAS_SMEM_MAX_SITES) return false;
+    if (fuse == RAS_FUSE_P)
+        for (int mu = 0; mu < 4; mu++)
+            if (dg.e[mu] != dg.b[mu]) return false;
+    return true;
+}
+
 qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params *p, const DomainGeom &dg,
                             SpinorView out, SpinorView in, SpinorView rho, SpinorView v, double kappa, int *dv,
-                            const Scalars *sc)
+                            const Scalars *sc, int fuse, SpinorView fr, SpinorView fz)
 {
     qdd_status st = ensure_ras_scratch(lat, dg);
     if (st != QDD_OK) return st;
@@ -182,6 +191,10 @@ qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params 
         ra.vout = last ? SpinorView{nullptr, nullptr} : v;
         ra.acc = out;
         ra.accumulate = j > 0;
+        // the first sweep may form its input (written to `in`) from fr, in, fz
+        ra.fuse = j == 0 ? fuse : RAS_FUSE_NONE;
+        ra.fr = fr;
+        ra.fz = fz;
         cudaError_t e;
         {
             ProfScope ps(lat, QDD_K_RAS);
@@ -222,17 +235,20 @@ qdd_status enqueue_iteration(Member &m, int prec, const qdd_solver_params *p)
     auto F = [&](int k) { return inner(lat, prec, k); };
     const SpinorView phat = m.use_ras ? F(W_PHAT) : F(W_P);
     const SpinorView shat = m.use_ras ? F(W_SHAT) : F(W_S);
+    // with RAS, the updates p = r + beta (p - omega v) and s = r - alpha v are
+    // formed by the sweeps that precondition them, while they stage their
+    // input, instead of by separate passes over memory
+    const bool fuse_p = m.use_ras && ras_can_fuse(prec, m.dg, RAS_FUSE_P);
+    const bool fuse_s = m.use_ras && ras_can_fuse(prec, m.dg, RAS_FUSE_S);
     qdd_status st;
-    if ((st = blas(lat, prec, B_P, {F(W_P), F(W_R), F(W_V)})) != QDD_OK) return st;
-    if (m.use_ras &&
-        (st = ras_apply_fields(lat, prec, p, m.dg, phat, F(W_P), F(W_RHO), F(W_VR), m.kappa, nullptr, lat->sc)) !=
-            QDD_OK)
+    if (!fuse_p && (st = blas(lat, prec, B_P, {F(W_P), F(W_R), F(W_V)})) != QDD_OK) return st;
+    if (m.use_ras && (st = ras_apply_fields(lat, prec, p, m.dg, phat, F(W_P), F(W_RHO), F(W_VR), m.kappa, nullptr,
+                                            lat->sc, fuse_p ? RAS_FUSE_P : RAS_FUSE_NONE, F(W_R), F(W_V))) != QDD_OK)
         return st;
     if ((st = run_dslash(lat, prec, EPI_RV, F(W_V), phat, F(W_RHAT), m.kappa, 0)) != QDD_OK) return st;
-    if ((st = blas(lat, prec, B_S, {F(W_S), F(W_R), F(W_V)})) != QDD_OK) return st;
-    if (m.use_ras &&
-        (st = ras_apply_fields(lat, prec, p, m.dg, shat, F(W_S), F(W_RHO), F(W_VR), m.kappa, nullptr, lat->sc)) !=
-            QDD_OK)
+    if (!fuse_s && (st = blas(lat, prec, B_S, {F(W_S), F(W_R), F(W_V)})) != QDD_OK) return st;
+    if (m.use_ras && (st = ras_apply_fields(lat, prec, p, m.dg, shat, F(W_S), F(W_RHO), F(W_VR), m.kappa, nullptr,
+                                            lat->sc, fuse_s ? RAS_FUSE_S : RAS_FUSE_NONE, F(W_R), F(W_V))) != QDD_OK)
         return st;
     if ((st = run_dslash(lat, prec, EPI_TS, F(W_T), shat, F(W_S), m.kappa, 0)) != QDD_OK) return st;
     return blas(lat, prec, B_XR, {F(W_X), phat, shat, F(W_R), F(W_S), F(W_T), F(W_RHAT)});
