@@ -63,7 +63,8 @@ typedef enum {
     QDD_ERR_NOT_CONVERGED = 4,  /* iteration budget exhausted; phi holds the best iterate */
     QDD_ERR_BREAKDOWN = 5,      /* BiCGStab broke down twice (after one restart) */
     QDD_ERR_NONFINITE = 6,      /* NaN or Inf in a residual norm */
-    QDD_ERR_TIMEOUT = 7,        /* reserved: a bounded device-side wait gave up */
+    QDD_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up (a RAS sweep waiting for its
+                                   bulk-copied domain data); the results of the call are undefined */
     QDD_ERR_STATE = 8           /* call out of order (e.g. no gauge field loaded) */
 } qdd_status;
 

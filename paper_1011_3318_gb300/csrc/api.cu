@@ -233,7 +233,7 @@ qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc
         {&lat->A64, (size_t)V * 36 * 16},    {&lat->A32, (size_t)V * 18 * 16},    {&lat->A16, (size_t)V * 9 * 16},
         {(void **)&lat->A16n, (size_t)V * 4}, {(void **)&lat->rs.partials, (size_t)max_blocks * 4 * sizeof(double) * n_rhs},
         {(void **)&lat->rs.counter, (size_t)64 * n_rhs},     {(void **)&lat->sc, sizeof(Scalars) * n_rhs},
-        {(void **)&lat->maxdev, 64},
+        {(void **)&lat->maxdev, 64},         {(void **)&lat->ras_err, 64},
     };
     for (auto &a : allocs) {
         cudaError_t e = cudaMalloc(a.p, a.bytes);
@@ -245,6 +245,7 @@ qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc
     lat->rs.max_blocks = max_blocks;
     cudaError_t e = cudaMemset(lat->rs.counter, 0, (size_t)64 * n_rhs);
     if (e == cudaSuccess) e = cudaMemset(lat->sc, 0, sizeof(Scalars) * n_rhs);
+    if (e == cudaSuccess) e = cudaMemset(lat->ras_err, 0, 64);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&lat->sc_host, sizeof(Scalars) * n_rhs);
     if (e != cudaSuccess) {
         qdd_destroy_lattice(lat);
@@ -259,7 +260,8 @@ qdd_status qdd_destroy_lattice(qdd_lattice *lat)
     if (!lat) return QDD_OK;
     cudaStreamSynchronize(lat->stream);
     void *ptrs[] = {lat->U64, lat->Udf, lat->U32, lat->U16, lat->A64, lat->A32, lat->A16, lat->A16n, lat->rs.partials,
-                    lat->rs.counter, lat->sc, lat->maxdev, lat->stage_a, lat->stage_b, lat->ras_scratch};
+                    lat->rs.counter, lat->sc, lat->maxdev, lat->ras_err, lat->stage_a, lat->stage_b,
+                    lat->ras_scratch};
     for (void *p : ptrs) cudaFree(p);
     if (lat->sc_host) cudaFreeHost(lat->sc_host);
     work_free(lat->work);
@@ -337,6 +339,18 @@ qdd_status qdd_dslash(qdd_lattice *lat, double *out, const double *in, double ka
     return finish_out(lat, out, dout, host);
 }
 
+// Reads (and clears) the lattice's RAS wait-timeout word; the stream must be idle.
+static qdd_status check_ras_err(qdd_lattice *lat)
+{
+    unsigned flag = 0;
+    cudaError_t e = cudaMemcpy(&flag, lat->ras_err, sizeof(flag), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the RAS status word");
+    if (!flag) return QDD_OK;
+    cudaMemset(lat->ras_err, 0, sizeof(flag));
+    set_error("a RAS sweep gave up waiting for its staged data; the output is undefined");
+    return QDD_ERR_TIMEOUT;
+}
+
 qdd_status qdd_ras_apply(qdd_lattice *lat, double *out, const double *in, double kappa, double c_sw,
                          const qdd_solver_params *params)
 {
@@ -390,6 +404,7 @@ qdd_status qdd_ras_apply(qdd_lattice *lat, double *out, const double *in, double
     if (st == QDD_OK) st = finish_out(lat, out, dout, host);
     cudaStreamSynchronize(lat->stream);
     for (int j = 0; j < 2; j++) field_free(wd[j], wn[j]);
+    if (st == QDD_OK) st = check_ras_err(lat);
     return st;
 }
 

@@ -134,6 +134,7 @@ struct RasArgs {
     //   RAS_FUSE_S: s = r - alpha v             (fr = r, fz = v)
     int fuse;
     SpinorView fr, fz;
+    unsigned *err;  // may be null: set to 1 when a bounded wait for staged data gives up
 };
 
 enum { RAS_FUSE_NONE = 0, RAS_FUSE_P = 1, RAS_FUSE_S = 2 };
@@ -181,6 +182,7 @@ struct qdd_lattice {
     qdd::Scalars *sc;       // device
     qdd::Scalars *sc_host;  // pinned mirror
     unsigned long long *maxdev;
+    unsigned *ras_err;  // device word: a RAS sweep's bounded wait gave up
     // canonical staging buffers for host pointers
     double *stage_a, *stage_b;
     // RAS scratch

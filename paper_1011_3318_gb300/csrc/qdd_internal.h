@@ -77,7 +77,8 @@ struct Scalars {
     double aux[8];   // plain reduction results (norms)
 };
 
-enum ScalarStatus { S_RUN = 0, S_CONVERGED = 1, S_BREAK_RV = 2, S_BREAK_TT = 3, S_NONFINITE = 4 };
+// S_TIMEOUT: a bounded device-side wait gave up (reported as QDD_ERR_TIMEOUT).
+enum ScalarStatus { S_RUN = 0, S_CONVERGED = 1, S_BREAK_RV = 2, S_BREAK_TT = 3, S_NONFINITE = 4, S_TIMEOUT = 5 };
 
 // Grid-reduction scratch: per-block partial sums and the arrival counter of
 // the last-block pattern.

@@ -26,8 +26,10 @@
 //    loops over the domains; rho, q and v of the current domain live in a
 //    per-CTA slot of global scratch (L2-resident for moderate domains).
 #include <atomic>
+#include <cstring>
 
 #include "device.cuh"
+#include "tma.cuh"
 #include "lib.h"
 
 namespace qdd {
@@ -299,82 +301,17 @@ __device__ __forceinline__ void smem_hops(const LocSite &s, int l, const float2 
     }
 }
 
+// The N_dominv minimal-residual iterations of one domain on its staged
+// residual (srho, FP32), with v (sv) starting at zero, and the restriction of
+// v to the bulk sites.  All NT threads of the CTA call it.
 template <int P, int NT, bool SC, bool EXP>
-__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(RasArgs a)
+__device__ __forceinline__ void ras_mr_domain(const RasArgs &a, const LocSite &s, float2 *srho, float2 *sv,
+                                              unsigned char *sA, const LinkView &lU, const CloverView &lA,
+                                              float (&wpart)[3][NT / 32])
 {
-    const int rr = blockIdx.x % a.nrhs, dom = blockIdx.x / a.nrhs;
-    if (a.sc && a.sc[rr].status != S_RUN) return;
-    a.in = rhs_view<P>(a.in, a.g.V, rr);
-    a.vout = rhs_view<P>(a.vout, a.g.V, rr);
-    a.acc = rhs_view<P>(a.acc, a.g.V, rr);
-    a.fr = rhs_view<P>(a.fr, a.g.V, rr);
-    a.fz = rhs_view<P>(a.fz, a.g.V, rr);
-    C<float> fb, fc;
-    fuse_coefs(a, rr, fb, fc);
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ float wpart[3][NT / 32];
-    float2 *srho = reinterpret_cast<float2 *>(smem);
-    float2 *sv = srho + 12 * NT;
-    unsigned char *sU = reinterpret_cast<unsigned char *>(sv + 12 * NT);
-    unsigned char *sA = sU + (size_t)NT * RasSmem<P, EXP>::link_bytes;
-    float *sAn = reinterpret_cast<float *>(sA + (size_t)NT * RasSmem<P, EXP>::clover_data);
-    const LinkView lU{sU};
-    const CloverView lA = SC ? CloverView{sA, sAn} : a.A;
     const long long V = a.g.V;
     const int l = threadIdx.x;
-    LocSite s;
-    loc_site(a.g, a.dg, dom, l, s);
     const bool act = s.m & M_ACT;
-
-    // stage the projection P_{Omega'} r, and the domain's links and clover
-    {
-        C<float> r[12], z[12];
-#pragma unroll
-        for (int k = 0; k < 12; k++) { r[k] = {0.f, 0.f}; z[k] = {0.f, 0.f}; }
-        if (act) {
-            staged_input<P>(a, V, s.x, fb, fc, r);
-            // the fused update's result, on the bulk sites (each written once)
-            if (a.fuse != RAS_FUSE_NONE && (s.m & M_BULK)) store_spinor<P>(a.in, V, s.x, r);
-        }
-        st_local(srho, NT, l, r);
-        st_local(sv, NT, l, z);
-        if (act) {
-            if constexpr (EXP) {
-#pragma unroll 1
-                for (int mu = 0; mu < 4; mu++) {
-                    C<float> U[9];
-                    load_link<P>(a.U, V, mu, s.x, U);
-#pragma unroll
-                    for (int k = 0; k < 9; k++) ((float2 *)sU)[(mu * 9 + k) * NT + l] = make_float2(U[k].r, U[k].i);
-                }
-                float av[72];
-                load_clover<P>(a.A, V, s.x, av);
-#pragma unroll
-                for (int k = 0; k < 18; k++)
-                    ((float4 *)sA)[k * NT + l] = make_float4(av[4 * k], av[4 * k + 1], av[4 * k + 2], av[4 * k + 3]);
-            } else if constexpr (P == P16) {
-                const uint2 *g = (const uint2 *)a.U.d;
-#pragma unroll
-                for (int k = 0; k < 12; k++) ((uint2 *)sU)[k * NT + l] = g[(long long)k * V + s.x];
-                if constexpr (SC) {
-                    const uint4 *ga = (const uint4 *)a.A.d;
-#pragma unroll
-                    for (int k = 0; k < 9; k++) ((uint4 *)sA)[k * NT + l] = ga[(long long)k * V + s.x];
-                    sAn[l] = a.A.n[s.x];
-                }
-            } else {
-                const float4 *g = (const float4 *)a.U.d;
-#pragma unroll
-                for (int k = 0; k < 12; k++) ((float4 *)sU)[k * NT + l] = g[(long long)k * V + s.x];
-                if constexpr (SC) {
-                    const float4 *ga = (const float4 *)a.A.d;
-#pragma unroll
-                    for (int k = 0; k < 18; k++) ((float4 *)sA)[k * NT + l] = ga[(long long)k * V + s.x];
-                }
-            }
-        }
-    }
-
     for (int it = 0; it < a.n_iter; it++) {
         __syncthreads();
         C<float> q[12];
@@ -457,6 +394,198 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(RasArgs
         ld_local(sv, NT, l, vv);
         write_outputs<P>(a, s.x, vv);
     }
+}
+
+template <int P, int NT, bool SC, bool EXP>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(RasArgs a)
+{
+    const int rr = blockIdx.x % a.nrhs, dom = blockIdx.x / a.nrhs;
+    if (a.sc && a.sc[rr].status != S_RUN) return;
+    a.in = rhs_view<P>(a.in, a.g.V, rr);
+    a.vout = rhs_view<P>(a.vout, a.g.V, rr);
+    a.acc = rhs_view<P>(a.acc, a.g.V, rr);
+    a.fr = rhs_view<P>(a.fr, a.g.V, rr);
+    a.fz = rhs_view<P>(a.fz, a.g.V, rr);
+    C<float> fb, fc;
+    fuse_coefs(a, rr, fb, fc);
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float wpart[3][NT / 32];
+    float2 *srho = reinterpret_cast<float2 *>(smem);
+    float2 *sv = srho + 12 * NT;
+    unsigned char *sU = reinterpret_cast<unsigned char *>(sv + 12 * NT);
+    unsigned char *sA = sU + (size_t)NT * RasSmem<P, EXP>::link_bytes;
+    float *sAn = reinterpret_cast<float *>(sA + (size_t)NT * RasSmem<P, EXP>::clover_data);
+    const LinkView lU{sU};
+    const CloverView lA = SC ? CloverView{sA, sAn} : a.A;
+    const long long V = a.g.V;
+    const int l = threadIdx.x;
+    LocSite s;
+    loc_site(a.g, a.dg, dom, l, s);
+    const bool act = s.m & M_ACT;
+
+    // stage the projection P_{Omega'} r, and the domain's links and clover
+    {
+        C<float> r[12], z[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) { r[k] = {0.f, 0.f}; z[k] = {0.f, 0.f}; }
+        if (act) {
+            staged_input<P>(a, V, s.x, fb, fc, r);
+            // the fused update's result, on the bulk sites (each written once)
+            if (a.fuse != RAS_FUSE_NONE && (s.m & M_BULK)) store_spinor<P>(a.in, V, s.x, r);
+        }
+        st_local(srho, NT, l, r);
+        st_local(sv, NT, l, z);
+        if (act) {
+            if constexpr (EXP) {
+#pragma unroll 1
+                for (int mu = 0; mu < 4; mu++) {
+                    C<float> U[9];
+                    load_link<P>(a.U, V, mu, s.x, U);
+#pragma unroll
+                    for (int k = 0; k < 9; k++) ((float2 *)sU)[(mu * 9 + k) * NT + l] = make_float2(U[k].r, U[k].i);
+                }
+                float av[72];
+                load_clover<P>(a.A, V, s.x, av);
+#pragma unroll
+                for (int k = 0; k < 18; k++)
+                    ((float4 *)sA)[k * NT + l] = make_float4(av[4 * k], av[4 * k + 1], av[4 * k + 2], av[4 * k + 3]);
+            } else if constexpr (P == P16) {
+                const uint2 *g = (const uint2 *)a.U.d;
+#pragma unroll
+                for (int k = 0; k < 12; k++) ((uint2 *)sU)[k * NT + l] = g[(long long)k * V + s.x];
+                if constexpr (SC) {
+                    const uint4 *ga = (const uint4 *)a.A.d;
+#pragma unroll
+                    for (int k = 0; k < 9; k++) ((uint4 *)sA)[k * NT + l] = ga[(long long)k * V + s.x];
+                    sAn[l] = a.A.n[s.x];
+                }
+            } else {
+                const float4 *g = (const float4 *)a.U.d;
+#pragma unroll
+                for (int k = 0; k < 12; k++) ((float4 *)sU)[k * NT + l] = g[(long long)k * V + s.x];
+                if constexpr (SC) {
+                    const float4 *ga = (const float4 *)a.A.d;
+#pragma unroll
+                    for (int k = 0; k < 18; k++) ((float4 *)sA)[k * NT + l] = ga[(long long)k * V + s.x];
+                }
+            }
+        }
+    }
+
+    ras_mr_domain<P, NT, SC, EXP>(a, s, srho, sv, sA, lU, lA, wpart);
+}
+
+// ---------------------------------------------------------------- TMA staging
+// Tensor maps of one sweep for ras_tma_kernel: every field is described as a
+// 5-D tensor of 32-bit words (W words per site along x, then y, z, t, and the
+// field's planes), and one box of the block's extent delivers a whole plane
+// group of a domain in the kernel's shared-memory layout [plane][site].
+struct RasTma {
+    CUtensorMap links, clover, clover_n;
+    CUtensorMap in[3], in_n[3];
+    unsigned bytes;  // bytes delivered per domain by all the copies
+    int nin;         // input vectors: 1, or r, v (and p) of a fused update
+};
+
+// The sweep of ras_smem_kernel (compact staging) for blocks without overlap
+// whose extended domain has exactly NT sites, with the staging done by TMA:
+// one thread issues a bulk tensor copy per plane group (links, clover, its
+// norm, and each input vector with its norm), completing on an mbarrier,
+// instead of every thread loading its site's 24 values through registers.
+// Input vectors land in the rho/v area as raw FP16 (or FP32) planes and are
+// combined (fused update) and widened there.
+template <int P, int NT>
+__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_tma_kernel(RasArgs a, const __grid_constant__ RasTma tm)
+{
+    constexpr bool SC = P == P16;
+    constexpr int RAW = P == P16 ? 52 : 96;      // bytes per site of one staged input vector
+    constexpr int LW = P == P16 ? 2 : 4;         // 32-bit words per site of a link plane
+    constexpr int INP = P == P16 ? 3 : 6;        // planes of an input vector
+    const int rr = blockIdx.x % a.nrhs, dom = blockIdx.x / a.nrhs;
+    if (a.sc && a.sc[rr].status != S_RUN) return;
+    a.in = rhs_view<P>(a.in, a.g.V, rr);
+    a.vout = rhs_view<P>(a.vout, a.g.V, rr);
+    a.acc = rhs_view<P>(a.acc, a.g.V, rr);
+    C<float> fb, fc;
+    fuse_coefs(a, rr, fb, fc);
+    extern __shared__ __align__(128) unsigned char smem_dyn[];
+    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<size_t>(smem_dyn) + 127) & ~(size_t)127);
+    __shared__ float wpart[3][NT / 32];
+    __shared__ __align__(8) unsigned long long bar;
+    float2 *srho = reinterpret_cast<float2 *>(smem);
+    float2 *sv = srho + 12 * NT;
+    unsigned char *sU = reinterpret_cast<unsigned char *>(sv + 12 * NT);
+    unsigned char *sA = sU + (size_t)NT * RasSmem<P, false>::link_bytes;
+    float *sAn = reinterpret_cast<float *>(sA + (size_t)NT * RasSmem<P, false>::clover_data);
+    unsigned char *raw = smem;  // staged input vectors, inside the rho/v area
+    const LinkView lU{sU};
+    const CloverView lA = SC ? CloverView{sA, sAn} : a.A;
+    const int l = threadIdx.x;
+    LocSite s;
+    loc_site(a.g, a.dg, dom, l, s);
+
+    if (l == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (l == 0) {
+        int k[4], r = dom;
+        for (int mu = 0; mu < 4; mu++) {
+            k[mu] = r % a.dg.nb[mu];
+            r /= a.dg.nb[mu];
+        }
+        const int x0 = k[0] * a.dg.b[0], y0 = k[1] * a.dg.b[1], z0 = k[2] * a.dg.b[2], t0 = k[3] * a.dg.b[3];
+        mbar_arrive_expect_tx(&bar, tm.bytes);
+        tma_load_5d(sU, &tm.links, &bar, x0 * LW, y0, z0, t0, 0);
+        if constexpr (SC) {
+            tma_load_5d(sA, &tm.clover, &bar, x0 * 4, y0, z0, t0, 0);
+            tma_load_5d(sAn, &tm.clover_n, &bar, x0, y0, z0, t0, 0);
+        }
+        for (int j = 0; j < tm.nin; j++) {
+            unsigned char *dst = raw + (size_t)j * RAW * NT;
+            tma_load_5d(dst, &tm.in[j], &bar, x0 * 4, y0, z0, t0, rr * INP);
+            if constexpr (P == P16) tma_load_5d(dst + 48 * NT, &tm.in_n[j], &bar, x0, y0, z0, t0, rr);
+        }
+    }
+    // bounded wait, with a CTA-uniform outcome
+    const bool ok = mbar_wait_bounded(&bar, 0);
+    if (__syncthreads_or(!ok)) {
+        if (l == 0) {
+            if (a.sc) const_cast<Scalars *>(a.sc)[rr].status = S_TIMEOUT;
+            else if (a.err) atomicOr(a.err, 1u);
+        }
+        mbar_wait_bounded(&bar, 0);  // give the copies in flight a last chance to land
+        return;
+    }
+
+    // the projected input: every site of a block without overlap is bulk
+    C<float> r[12];
+    {
+        auto raw_view = [&](int j) {
+            unsigned char *b = raw + (size_t)j * RAW * NT;
+            return SpinorView{b, P == P16 ? reinterpret_cast<float *>(b + 48 * NT) : nullptr};
+        };
+        load_spinor<P>(raw_view(0), NT, l, r);
+        if (tm.nin > 1) {  // fused update: inputs r, v (and p), as in staged_input
+            C<float> t[12];
+            load_spinor<P>(raw_view(1), NT, l, t);
+#pragma unroll
+            for (int q = 0; q < 12; q++) r[q] = cfma(fc, t[q], r[q]);
+            if (tm.nin > 2) {
+                load_spinor<P>(raw_view(2), NT, l, t);
+#pragma unroll
+                for (int q = 0; q < 12; q++) r[q] = cfma(fb, t[q], r[q]);
+            }
+        }
+    }
+    __syncthreads();  // all raw inputs read before rho and v overwrite them
+    {
+        C<float> z[12];
+#pragma unroll
+        for (int q = 0; q < 12; q++) z[q] = {0.f, 0.f};
+        st_local(srho, NT, l, r);
+        st_local(sv, NT, l, z);
+        if (a.fuse != RAS_FUSE_NONE) store_spinor<P>(a.in, a.g.V, s.x, r);
+    }
+    ras_mr_domain<P, NT, SC, false>(a, s, srho, sv, sA, lU, lA, wpart);
 }
 
 constexpr int RAS_GMEM_NT = 256;
@@ -561,11 +690,119 @@ static cudaError_t launch_smem(const RasArgs &a, cudaStream_t st)
 // FP32 clover, 768 B per site); 256-site domains keep the links 12-real and,
 // for FP16 storage, the clover in FP16 (111.6 KB, two CTAs per SM); for FP32
 // storage the clover is read through L1 instead.
+// ---------------------------------------------------------------- TMA host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime (no
+// link-time dependency on the driver library); null if unavailable.
+static EncodeTiledFn tma_encoder()
+{
+    static std::atomic<int> state{0};  // 0 unknown, 1 found, 2 unavailable
+    static EncodeTiledFn fn = nullptr;
+    int s = state.load();
+    if (s == 0) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess && f) {
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+            state.store(1);
+        } else {
+            cudaGetLastError();
+            state.store(2);
+        }
+        s = state.load();
+    }
+    return s == 1 ? fn : nullptr;
+}
+
+// Map of a planar field with w 32-bit words per site and `planes` planes of V
+// sites, boxed by the block (b) and `box_planes` planes.
+static bool encode_field(EncodeTiledFn enc, CUtensorMap *m, const void *base, int w, const Geom &g, long long planes,
+                         const int b[4], int box_planes, unsigned *bytes)
+{
+    if (!base || (reinterpret_cast<size_t>(base) & 15)) return false;
+    const cuuint64_t row = (cuuint64_t)w * 4 * g.L[0];
+    const cuuint64_t dims[5] = {(cuuint64_t)w * g.L[0], (cuuint64_t)g.L[1], (cuuint64_t)g.L[2], (cuuint64_t)g.L[3],
+                                (cuuint64_t)planes};
+    const cuuint64_t strides[4] = {row, row * g.L[1], row * g.L[1] * g.L[2], (cuuint64_t)w * 4 * g.V};
+    const cuuint32_t box[5] = {(cuuint32_t)(w * b[0]), (cuuint32_t)b[1], (cuuint32_t)b[2], (cuuint32_t)b[3],
+                               (cuuint32_t)box_planes};
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    for (int i = 0; i < 4; i++)
+        if (strides[i] % 16 || strides[i] >= (1ull << 40)) return false;
+    for (int i = 0; i < 5; i++)
+        if (box[i] < 1 || box[i] > 256 || box[i] > dims[i]) return false;
+    if ((box[0] * 4) % 16) return false;
+    if (enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 5, const_cast<void *>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return false;
+    *bytes += box[0] * box[1] * box[2] * box[3] * box[4] * 4u;
+    return true;
+}
+
+// Builds the maps of ras_tma_kernel for this sweep; false when the sweep does
+// not qualify (overlap, domain size, extents not multiples of 4 along x,
+// misaligned fields, a fused p update in FP32, no encoder).
+template <int P>
+static bool tma_maps(const RasArgs &a, int nt, RasTma *tm)
+{
+    if (a.variant != 0 || a.dg.nloc != nt) return false;
+    for (int mu = 0; mu < 4; mu++)
+        if (a.dg.e[mu] != a.dg.b[mu]) return false;
+    if (a.dg.b[0] % 4 || a.g.L[0] % 4) return false;
+    if (P == P32 && a.fuse == RAS_FUSE_P) return false;
+    EncodeTiledFn enc = tma_encoder();
+    if (!enc) return false;
+    memset(tm, 0, sizeof(*tm));
+    const int lw = P == P16 ? 2 : 4, inp = P == P16 ? 3 : 6;
+    if (!encode_field(enc, &tm->links, a.U.d, lw, a.g, 12, a.dg.b, 12, &tm->bytes)) return false;
+    if (P == P16) {
+        if (!encode_field(enc, &tm->clover, a.A.d, 4, a.g, 9, a.dg.b, 9, &tm->bytes)) return false;
+        if (!encode_field(enc, &tm->clover_n, a.A.n, 1, a.g, 1, a.dg.b, 1, &tm->bytes)) return false;
+    }
+    const SpinorView ins[3] = {a.fuse == RAS_FUSE_NONE ? a.in : a.fr, a.fz, a.in};
+    tm->nin = a.fuse == RAS_FUSE_NONE ? 1 : a.fuse == RAS_FUSE_S ? 2 : 3;
+    for (int j = 0; j < tm->nin; j++) {
+        if (!encode_field(enc, &tm->in[j], ins[j].d, 4, a.g, (long long)inp * a.nrhs, a.dg.b, inp, &tm->bytes))
+            return false;
+        if (P == P16 && !encode_field(enc, &tm->in_n[j], ins[j].n, 1, a.g, a.nrhs, a.dg.b, 1, &tm->bytes))
+            return false;
+    }
+    return true;
+}
+
+template <int P, int NT>
+static cudaError_t launch_tma(const RasArgs &a, const RasTma &tm, cudaStream_t st)
+{
+    const size_t smem = RasSmem<P, false>::bytes(NT, P == P16) + 128;
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !((done.load() >> dev) & 1ull)) {
+        cudaError_t e =
+            cudaFuncSetAttribute(ras_tma_kernel<P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) done.fetch_or(1ull << dev);
+    }
+    ras_tma_kernel<P, NT><<<a.dg.ndom * a.nrhs, NT, smem, st>>>(a, tm);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <int P>
 static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
 {
     const int n = a.dg.nloc;
     if constexpr (P == P16 || P == P32) {
+        if (n == 256) {
+            RasTma tm;
+            if (tma_maps<P>(a, 256, &tm)) return launch_tma<P, 256>(a, tm, st);
+        }
         if (a.variant == 1) {  // compact staging at every size
             if (n <= 32) return launch_smem<P, 32, P == P16>(a, st);
             if (n <= 64) return launch_smem<P, 64, P == P16>(a, st);

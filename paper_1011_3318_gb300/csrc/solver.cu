@@ -185,6 +185,7 @@ qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params 
     ra.slots = ras_default_slots();
     ra.nrhs = lat->nrhs;
     ra.variant = p->ras_kernel;
+    ra.err = lat->ras_err;
     for (int j = 0; j < p->n_ras; j++) {
         const bool last = j == p->n_ras - 1;
         ra.in = j == 0 ? in : rho;
@@ -533,6 +534,9 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                 if (h.status == S_NONFINITE) {
                     m.done[r] = 1;
                     m.result[r] = QDD_ERR_NONFINITE;
+                } else if (h.status == S_TIMEOUT) {
+                    m.done[r] = 1;
+                    m.result[r] = QDD_ERR_TIMEOUT;
                 }
             }
             cudaError_t e;
@@ -590,6 +594,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
     if (result == QDD_ERR_NOT_CONVERGED) set_error("solve did not reach the tolerance");
     else if (result == QDD_ERR_BREAKDOWN) set_error("BiCGStab broke down");
     else if (result == QDD_ERR_NONFINITE) set_error("non-finite residual");
+    else if (result == QDD_ERR_TIMEOUT) set_error("a RAS sweep gave up waiting for its staged data");
     return result;
 }
 
