@@ -179,4 +179,10 @@ qdd_status qdd_measure_fma_peak(int fp64, double *tflops)
     return fp64 ? fma_probe<double>(tflops) : fma_probe<float>(tflops);
 }
 
+qdd_status qdd_test_ras_wait(unsigned extra_bytes, long max_polls)
+{
+    ras_set_wait_test(extra_bytes, max_polls);
+    return QDD_OK;
+}
+
 }  // extern "C"

@@ -147,6 +147,8 @@ cudaError_t launch_ras_block(int prec, const RasArgs &a, cudaStream_t st);
 // scratch and slot count given in a (FP32 and FP16 only).
 cudaError_t launch_ras_block_gmem(int prec, const RasArgs &a, cudaStream_t st);
 size_t ras_scratch_bytes(const DomainGeom &dg, int slots, int nrhs);
+// Test support for the TMA sweep's bounded wait (qdd_test_ras_wait).
+void ras_set_wait_test(unsigned extra_bytes, long max_polls);
 int ras_default_slots();
 
 bool domain_geom(const Geom &g, const int block[4], int s, DomainGeom *dg, std::string *why);

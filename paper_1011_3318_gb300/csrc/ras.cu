@@ -485,6 +485,10 @@ struct RasTma {
     CUtensorMap in[3], in_n[3];
     unsigned bytes;  // bytes delivered per domain by all the copies
     int nin;         // input vectors: 1, or r, v (and p) of a fused update
+    // bounded-wait parameters: polls before giving up, and bytes announced on
+    // top of `bytes` (non-zero only when a test makes the wait run out)
+    long max_polls;
+    unsigned extra_tx;
 };
 
 // The sweep of ras_smem_kernel (compact staging) for blocks without overlap
@@ -533,7 +537,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_tma_kernel(RasArgs 
             r /= a.dg.nb[mu];
         }
         const int x0 = k[0] * a.dg.b[0], y0 = k[1] * a.dg.b[1], z0 = k[2] * a.dg.b[2], t0 = k[3] * a.dg.b[3];
-        mbar_arrive_expect_tx(&bar, tm.bytes);
+        mbar_arrive_expect_tx(&bar, tm.bytes + tm.extra_tx);
         tma_load_5d(sU, &tm.links, &bar, x0 * LW, y0, z0, t0, 0);
         if constexpr (SC) {
             tma_load_5d(sA, &tm.clover, &bar, x0 * 4, y0, z0, t0, 0);
@@ -546,13 +550,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_tma_kernel(RasArgs 
         }
     }
     // bounded wait, with a CTA-uniform outcome
-    const bool ok = mbar_wait_bounded(&bar, 0);
+    const bool ok = mbar_wait_bounded(&bar, 0, tm.max_polls);
     if (__syncthreads_or(!ok)) {
         if (l == 0) {
             if (a.sc) const_cast<Scalars *>(a.sc)[rr].status = S_TIMEOUT;
             else if (a.err) atomicOr(a.err, 1u);
         }
-        mbar_wait_bounded(&bar, 0);  // give the copies in flight a last chance to land
+        mbar_wait_bounded(&bar, 0, tm.max_polls);  // give the copies in flight a last chance to land
         return;
     }
 
@@ -745,6 +749,16 @@ static bool encode_field(EncodeTiledFn enc, CUtensorMap *m, const void *base, in
     return true;
 }
 
+// Bounded-wait settings of the TMA sweep (see qdd_test_ras_wait).
+static std::atomic<long> g_tma_polls{TMA_WAIT_TRIES};
+static std::atomic<unsigned> g_tma_extra_tx{0};
+
+void ras_set_wait_test(unsigned extra_bytes, long max_polls)
+{
+    g_tma_extra_tx.store(extra_bytes);
+    g_tma_polls.store(max_polls > 0 ? max_polls : TMA_WAIT_TRIES);
+}
+
 // Builds the maps of ras_tma_kernel for this sweep; false when the sweep does
 // not qualify (overlap, domain size, extents not multiples of 4 along x,
 // misaligned fields, a fused p update in FP32, no encoder).
@@ -759,6 +773,8 @@ static bool tma_maps(const RasArgs &a, int nt, RasTma *tm)
     EncodeTiledFn enc = tma_encoder();
     if (!enc) return false;
     memset(tm, 0, sizeof(*tm));
+    tm->max_polls = g_tma_polls.load();
+    tm->extra_tx = g_tma_extra_tx.load();
     const int lw = P == P16 ? 2 : 4, inp = P == P16 ? 3 : 6;
     if (!encode_field(enc, &tm->links, a.U.d, lw, a.g, 12, a.dg.b, 12, &tm->bytes)) return false;
     if (P == P16) {

@@ -5,8 +5,8 @@
 // count 1), makes the initialisation visible to the async proxy, and after a
 // CTA barrier arrives on it announcing the total number of bytes the copies
 // will deliver, then issues the copies; every thread waits for phase 0.  The
-// wait is bounded: after TMA_WAIT_TRIES polls it gives up and reports it, so
-// that a copy that never lands cannot hang the GPU.
+// wait is bounded: after TMA_WAIT_TRIES polls (by default) it gives up and
+// reports it, so that a copy that never lands cannot hang the GPU.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap
@@ -42,11 +42,11 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     return ok != 0;
 }
 
-// Polls phase `parity` of the barrier at most TMA_WAIT_TRIES times; returns
-// whether it completed.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity)
+// Polls phase `parity` of the barrier at most `tries` times; returns whether
+// it completed.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, unsigned parity, long tries)
 {
-    for (long i = 0; i < TMA_WAIT_TRIES; i++)
+    for (long i = 0; i < tries; i++)
         if (mbar_try_wait(bar, parity)) return true;
     return false;
 }

@@ -41,7 +41,8 @@ PREC = {"f64": QDD_F64, "f32": QDD_F32, "f16": QDD_F16, QDD_F64: QDD_F64, QDD_F3
 ABI = ("qdd_version", "qdd_last_error", "qdd_default_params", "qdd_create_lattice", "qdd_destroy_lattice",
        "qdd_load_gauge", "qdd_dslash", "qdd_ras_apply", "qdd_solve", "qdd_field_create", "qdd_field_destroy",
        "qdd_field_import", "qdd_field_export", "qdd_dslash_field", "qdd_kernel_launches", "qdd_set_profiling",
-       "qdd_profile_read", "qdd_measure_fma_peak", "qdd_ras_field_noalloc", "qdd_autotune", "qdd_solve_batch")
+       "qdd_profile_read", "qdd_measure_fma_peak", "qdd_ras_field_noalloc", "qdd_autotune", "qdd_solve_batch",
+       "qdd_test_ras_wait")
 
 # Kernel classes of the per-class GPU timers (qdd_profile).
 KCLASS = ("dslash", "dslash_f64", "ras", "blas", "convert", "clover")
@@ -97,6 +98,7 @@ def _load():
     lib.qdd_set_profiling.argtypes = [P, ctypes.c_int]
     lib.qdd_profile_read.argtypes = [P, ctypes.POINTER(Profile), ctypes.c_int]
     lib.qdd_measure_fma_peak.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
+    lib.qdd_test_ras_wait.argtypes = [ctypes.c_uint, ctypes.c_long]
     lib.qdd_solve_batch.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                                     ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo)]
@@ -340,6 +342,12 @@ def profile_read(lat: Lattice, reset: bool = True) -> dict:
     p = Profile()
     _check(_lib.qdd_profile_read(lat.handle, ctypes.byref(p), int(bool(reset))), "qdd_profile_read")
     return {k: (p.ms[i], p.launches[i]) for i, k in enumerate(KCLASS)}
+
+
+def test_ras_wait(extra_bytes: int = 0, max_polls: int = 0) -> None:
+    """Test support: bound the TMA-staged RAS sweep's wait to max_polls polls
+    and make it expect extra_bytes that never arrive (0, 0: defaults)."""
+    _check(_lib.qdd_test_ras_wait(int(extra_bytes), int(max_polls)), "qdd_test_ras_wait")
 
 
 def measure_fma_peak(fp64: bool) -> float:
