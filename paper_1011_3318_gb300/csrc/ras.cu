@@ -513,7 +513,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_tma_kernel(RasArgs 
     C<float> fb, fc;
     fuse_coefs(a, rr, fb, fc);
     extern __shared__ __align__(128) unsigned char smem_dyn[];
-    unsigned char *smem = reinterpret_cast<unsigned char *>((reinterpret_cast<size_t>(smem_dyn) + 127) & ~(size_t)127);
+    // 128-byte alignment for the copies, as an offset into the shared array
+    // (an integer round trip would hide the address space from the compiler
+    // and turn every shared-memory access into a generic one)
+    unsigned char *smem = smem_dyn + ((128u - (smem_addr(smem_dyn) & 127u)) & 127u);
     __shared__ float wpart[3][NT / 32];
     __shared__ __align__(8) unsigned long long bar;
     float2 *srho = reinterpret_cast<float2 *>(smem);
