@@ -98,9 +98,11 @@ typedef struct {
     int use_ras;        /* 1: right-precondition the inner solve with K_RAS (default 1) */
     int outer_mode;     /* 0: FP64 defect correction (the only mode so far) */
     int autotune;       /* reserved, 0 */
-    int ras_kernel;     /* RAS sweep staging: 0 auto, 1 compact (links and clover in the field's
-                           storage format), 2 expanded (FP32 18-real links and FP32 clover,
-                           domains of at most 256 sites) */
+    int ras_kernel;     /* RAS sweep staging: 0 auto (TMA bulk tensor copies for overlap-free
+                           256-site blocks with x extents divisible by 4, else per-thread
+                           loads), 1 compact per-thread staging (links and clover in the
+                           field's storage format), 2 expanded (FP32 18-real links and FP32
+                           clover, domains of at most 256 sites) */
 } qdd_solver_params;
 
 typedef struct {
@@ -162,7 +164,8 @@ qdd_status qdd_dslash(qdd_lattice *lat, double *out, const double *in, double ka
  * r -= D v.  Uses params->block, overlap, n_dominv, n_ras and inner_prec
  * (QDD_F32 or QDD_F16).  in/out canonical FP64 spinors, host or device.
  * Errors: QDD_ERR_ARG if a block does not divide the lattice or
- * block + 2*overlap exceeds it. */
+ * block + 2*overlap exceeds it; QDD_ERR_TIMEOUT if a sweep gave up waiting
+ * for its staged data (out is then undefined). */
 qdd_status qdd_ras_apply(qdd_lattice *lat, double *out, const double *in, double kappa, double c_sw,
                          const qdd_solver_params *params);
 
@@ -173,8 +176,9 @@ qdd_status qdd_ras_apply(qdd_lattice *lat, double *out, const double *in, double
  * defaults.  phi is overwritten (no initial guess).  info may be NULL, else
  * it receives n_rhs entries.  The inner iterations run as a CUDA graph when
  * the lattice has a non-default stream and profiling is off.  Returns QDD_OK,
- * QDD_ERR_NOT_CONVERGED (phi = best iterate), QDD_ERR_BREAKDOWN or
- * QDD_ERR_NONFINITE (the first failure over the right-hand sides). */
+ * QDD_ERR_NOT_CONVERGED (phi = best iterate), QDD_ERR_BREAKDOWN,
+ * QDD_ERR_NONFINITE or QDD_ERR_TIMEOUT (the first failure over the
+ * right-hand sides). */
 qdd_status qdd_solve(qdd_lattice *lat, double *phi, const double *eta, double kappa, double c_sw,
                      double tol, const qdd_solver_params *params, qdd_solve_info *info);
 
@@ -196,8 +200,7 @@ qdd_status qdd_solve_batch(qdd_lattice *const *lats, double *const *phi, const d
  * coordinate search over (n_dominv, n_ras), block shapes of 16 to 256 sites,
  * overlap 1, the sweep kernel's staging variant, the inner precision and
  * tighter inner tolerances (3e-4 with FP16 storage, 1e-4 and 1e-5 with
- * FP32 storage); at most
- * max_trials solves.  params is the starting point
+ * FP32 storage); at most max_trials solves.  params is the starting point
  * (inner_prec QDD_F32 or QDD_F16, use_ras = 1) and receives the best
  * parameters; best_ms (may be NULL) receives the best solve time.  eta is a
  * canonical FP64 spinor, host or device.  Runs synchronously. */
