@@ -279,9 +279,9 @@ qdd_status qdd_measure_fma_peak(int fp64, double *tflops);
 
 /* Test support, with no counterpart in the paper.  The TMA-staged RAS sweep
  * waits for its bulk copies on an mbarrier for at most max_polls polls
- * (<= 0: the default, 2^22) and then gives up: the call that ran it returns
- * QDD_ERR_TIMEOUT and its results are undefined, while the CUDA context
- * stays usable.  extra_bytes > 0 makes every such sweep announce that many
+ * (<= 0: the default, 2000 polls that each suspend the thread for at most
+ * 0.5 ms) and then gives up: the call that ran it returns QDD_ERR_TIMEOUT
+ * and its results are undefined, while the CUDA context stays usable.  extra_bytes > 0 makes every such sweep announce that many
  * bytes more than its copies deliver, so that its wait runs out; this is
  * how the tests exercise the timeout path.  Process-wide; (0, 0) restores
  * the defaults.  Never fails. */

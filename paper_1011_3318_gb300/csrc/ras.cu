@@ -499,7 +499,7 @@ struct RasTma {
 // Input vectors land in the rho/v area as raw FP16 (or FP32) planes and are
 // combined (fused update) and widened there.
 template <int P, int NT>
-__global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_tma_kernel(RasArgs a, const __grid_constant__ RasTma tm)
+__global__ void __launch_bounds__(NT, 512 / NT) ras_tma_kernel(RasArgs a, const __grid_constant__ RasTma tm)
 {
     constexpr bool SC = P == P16;
     constexpr int RAW = P == P16 ? 52 : 96;      // bytes per site of one staged input vector
@@ -818,9 +818,9 @@ static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
 {
     const int n = a.dg.nloc;
     if constexpr (P == P16 || P == P32) {
-        if (n == 256) {
+        if (n == 256 || n == 128) {
             RasTma tm;
-            if (tma_maps<P>(a, 256, &tm)) return launch_tma<P, 256>(a, tm, st);
+            if (tma_maps<P>(a, n, &tm)) return n == 256 ? launch_tma<P, 256>(a, tm, st) : launch_tma<P, 128>(a, tm, st);
         }
         if (a.variant == 1) {  // compact staging at every size
             if (n <= 32) return launch_smem<P, 32, P == P16>(a, st);

@@ -5,15 +5,20 @@
 // count 1), makes the initialisation visible to the async proxy, and after a
 // CTA barrier arrives on it announcing the total number of bytes the copies
 // will deliver, then issues the copies; every thread waits for phase 0.  The
-// wait is bounded: after TMA_WAIT_TRIES polls (by default) it gives up and
-// reports it, so that a copy that never lands cannot hang the GPU.
+// wait is bounded: after TMA_WAIT_TRIES polls (by default; about one second)
+// it gives up and reports it, so that a copy that never lands cannot hang
+// the GPU.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap
 
 namespace qdd {
 
-constexpr long TMA_WAIT_TRIES = 1L << 22;
+// Each poll may suspend the thread until the phase completes, for at most
+// TMA_SUSPEND_NS (so waiting warps take no issue slots from the other CTA of
+// the SM); TMA_WAIT_TRIES polls bound a wait to about one second.
+constexpr unsigned TMA_SUSPEND_NS = 500000;
+constexpr long TMA_WAIT_TRIES = 2000;
 
 __device__ __forceinline__ unsigned smem_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
 
@@ -34,10 +39,10 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned 
     unsigned ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(TMA_SUSPEND_NS)
         : "memory");
     return ok != 0;
 }

@@ -24,7 +24,8 @@ def _ras(qdd, lat, eta, p):
 
 
 @pytest.mark.parametrize("dims,block", [((8, 8, 8, 8), (4, 4, 4, 4)), ((8, 8, 8, 16), (8, 4, 4, 2)),
-                                        ((12, 8, 4, 8), (4, 4, 4, 4))])
+                                        ((12, 8, 4, 8), (4, 4, 4, 4)), ((8, 8, 8, 8), (4, 4, 4, 2)),
+                                        ((8, 4, 8, 8), (4, 2, 4, 4))])
 @pytest.mark.parametrize("prec", ["f32", "f16"])
 def test_tma_staging_matches_per_thread_staging(qdd, oracle_mod, dims, block, prec):
     bc = (1, 1, 1, -1)
@@ -71,7 +72,7 @@ def test_tma_wait_times_out_and_context_survives(qdd, oracle_mod):
     d_eta = torch.from_numpy(eta).cuda()
     out = torch.empty_like(d_eta)
     try:
-        qdd.test_ras_wait(extra_bytes=16, max_polls=2000)
+        qdd.test_ras_wait(extra_bytes=16, max_polls=4)
         with pytest.raises(qdd.QddError) as e:
             qdd.ras_apply(lat, out, d_eta, 0.125, 1.0, p)
         assert e.value.status == qdd.QDD_ERR_TIMEOUT
