@@ -148,7 +148,9 @@ qdd_status qdd_destroy_lattice(qdd_lattice *lat);
  * conjugated cross product of the first two) copies; invalidates the clover
  * cache.  The links enter D through the hopping term of Eq. 1 and the clover
  * leaves.  Rejects with QDD_ERR_ARG a field with any max|U^dag U - 1| or
- * |det U - 1| above 1e-10 (the compression needs SU(3)). */
+ * |det U - 1| above 1e-10 (the compression needs SU(3)).  A host U goes
+ * through a device staging buffer (576 B per site) allocated by the first
+ * such call and kept until the lattice is destroyed.  Synchronous. */
 qdd_status qdd_load_gauge(qdd_lattice *lat, const double *U);
 
 /* out = D in (Eq. 1), computed in precision prec (QDD_F64: FP64 throughout;

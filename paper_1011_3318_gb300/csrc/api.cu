@@ -261,7 +261,7 @@ qdd_status qdd_destroy_lattice(qdd_lattice *lat)
     cudaStreamSynchronize(lat->stream);
     void *ptrs[] = {lat->U64, lat->Udf, lat->U32, lat->U16, lat->A64, lat->A32, lat->A16, lat->A16n, lat->rs.partials,
                     lat->rs.counter, lat->sc, lat->maxdev, lat->ras_err, lat->stage_a, lat->stage_b,
-                    lat->ras_scratch};
+                    lat->ras_scratch, lat->gauge_stage};
     for (void *p : ptrs) cudaFree(p);
     if (lat->sc_host) cudaFreeHost(lat->sc_host);
     work_free(lat->work);
@@ -281,17 +281,19 @@ qdd_status qdd_load_gauge(qdd_lattice *lat, const double *U)
     }
     const size_t bytes = (size_t)lat->g.V * 72 * sizeof(double);
     const double *src = U;
-    double *tmp = nullptr;
     cudaError_t e;
     if (!is_device_ptr(U)) {
-        e = cudaMalloc((void **)&tmp, bytes);
-        if (e != cudaSuccess) return cuda_fail(e, "gauge staging");
-        e = cudaMemcpyAsync(tmp, U, bytes, cudaMemcpyHostToDevice, lat->stream);
-        if (e != cudaSuccess) {
-            cudaFree(tmp);
-            return cuda_fail(e, "gauge copy");
+        // host links go through a device staging buffer kept for later loads
+        if (!lat->gauge_stage) {
+            e = cudaMalloc((void **)&lat->gauge_stage, bytes);
+            if (e != cudaSuccess) {
+                lat->gauge_stage = nullptr;
+                return cuda_fail(e, "gauge staging");
+            }
         }
-        src = tmp;
+        e = cudaMemcpyAsync(lat->gauge_stage, U, bytes, cudaMemcpyHostToDevice, lat->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "gauge copy");
+        src = lat->gauge_stage;
     }
     e = cudaMemsetAsync(lat->maxdev, 0, sizeof(unsigned long long), lat->stream);
     if (e == cudaSuccess) {
@@ -301,7 +303,6 @@ qdd_status qdd_load_gauge(qdd_lattice *lat, const double *U)
     unsigned long long bits = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&bits, lat->maxdev, sizeof(bits), cudaMemcpyDeviceToHost, lat->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
-    cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(e, "gauge conversion");
     double dev;
     memcpy(&dev, &bits, sizeof(dev));

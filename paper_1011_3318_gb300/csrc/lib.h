@@ -185,8 +185,9 @@ struct qdd_lattice {
     qdd::Scalars *sc_host;  // pinned mirror
     unsigned long long *maxdev;
     unsigned *ras_err;  // device word: a RAS sweep's bounded wait gave up
-    // canonical staging buffers for host pointers
+    // canonical staging buffers for host pointers (spinors, and the links)
     double *stage_a, *stage_b;
+    double *gauge_stage;
     // RAS scratch
     float2 *ras_scratch;
     size_t ras_scratch_bytes;
