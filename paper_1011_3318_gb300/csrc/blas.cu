@@ -8,6 +8,7 @@
 // iteration return at once when the status is no longer "running", which
 // lets the host enqueue several iterations ahead of the convergence check.
 #include "device.cuh"
+#include "df64.cuh"
 #include "lib.h"
 
 namespace qdd {
@@ -239,14 +240,32 @@ __global__ void __launch_bounds__(BLAS_NT) convert_scaled_kernel(long long V, Sp
     const unsigned bid = blockIdx.x / nrhs, nblk = gridDim.x / nrhs;
     dst = rhs_view<PD>(dst, V, r);
     src64 = rhs_view<P64>(src64, V, r);
-    const double n2 = sc[r].aux[slot];
-    const double inv = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
+    // 1/|r| once per block (an FP64 division and square root are long
+    // sequences on this GPU's FP64 pipe)
+    __shared__ double s_inv;
+    if (threadIdx.x == 0) {
+        const double n2 = sc[r].aux[slot];
+        s_inv = n2 > 0 ? 1.0 / sqrt(n2) : 0.0;
+    }
+    __syncthreads();
+    const double inv = s_inv;
+    const float invf = (float)inv;
+    // values in the normal float range are converted in integer arithmetic
+    // and scaled in FP32 (|value * inv| <= 1); others are scaled in FP64 first
+    auto cvt = [&](double v) -> T {
+        if constexpr (PD == P64) return (T)(v * inv);
+        else {
+            const int e = dexp(v);
+            return (e >= 897 && e <= 1150 && invf > 0.f && invf < 3.0e38f) ? d2f_rn(v) * invf
+                                                                             : __double2float_rn(v * inv);
+        }
+    };
     for (long long x = (long long)bid * BLAS_NT + threadIdx.x; x < V; x += (long long)nblk * BLAS_NT) {
         C<double> s[12];
         load_spinor<P64>(src64, V, x, s);
         C<T> d[12];
 #pragma unroll
-        for (int k = 0; k < 12; k++) d[k] = {(T)(s[k].r * inv), (T)(s[k].i * inv)};
+        for (int k = 0; k < 12; k++) d[k] = {cvt(s[k].r), cvt(s[k].i)};
         store_spinor<PD>(dst, V, x, d);
     }
 }
@@ -260,7 +279,10 @@ __global__ void __launch_bounds__(BLAS_NT) accum_scaled_kernel(long long V, Spin
     const unsigned bid = blockIdx.x / nrhs, nblk = gridDim.x / nrhs;
     phi64 = rhs_view<P64>(phi64, V, r);
     xs = rhs_view<PS>(xs, V, r);
-    const double sc_ = sqrt(sc[r].aux[slot]);
+    __shared__ double s_sc;
+    if (threadIdx.x == 0) s_sc = sqrt(sc[r].aux[slot]);  // once per block
+    __syncthreads();
+    const double sc_ = s_sc;
     for (long long x = (long long)bid * BLAS_NT + threadIdx.x; x < V; x += (long long)nblk * BLAS_NT) {
         C<double> p[12];
         C<T> e[12];
@@ -268,8 +290,13 @@ __global__ void __launch_bounds__(BLAS_NT) accum_scaled_kernel(long long V, Spin
         load_spinor<PS>(xs, V, x, e);
 #pragma unroll
         for (int k = 0; k < 12; k++) {
-            p[k].r += sc_ * (double)e[k].r;
-            p[k].i += sc_ * (double)e[k].i;
+            if constexpr (PS == P64) {
+                p[k].r += sc_ * (double)e[k].r;
+                p[k].i += sc_ * (double)e[k].i;
+            } else {  // exact widening in integer arithmetic
+                p[k].r = fma(sc_, f2d(e[k].r), p[k].r);
+                p[k].i = fma(sc_, f2d(e[k].i), p[k].i);
+            }
         }
         store_spinor<P64>(phi64, V, x, p);
     }

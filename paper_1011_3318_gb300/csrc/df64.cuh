@@ -27,6 +27,44 @@ __device__ __forceinline__ DF df_from_double(double d)
     return DF{h, l};
 }
 
+// Conversions between double and float in integer arithmetic: on this GPU
+// the conversion instructions run on the FP64 pipe, at a small fraction of
+// the integer rate, and they dominate kernels that convert many values.
+// Biased double exponent of d.
+__device__ __forceinline__ int dexp(double d) { return (__double2hiint(d) >> 20) & 0x7ff; }
+
+// float(d) rounded to nearest even, exact for results in the normal float
+// range (the 29 dropped mantissa bits decide the rounding; a carry out of the
+// mantissa moves into the exponent, as IEEE 754 encodings allow); other
+// inputs use the hardware conversion.
+__device__ __forceinline__ float d2f_rn(double d)
+{
+    const int e = dexp(d);
+    if (e < 897 || e > 1150) return __double2float_rn(d);
+    const unsigned hi = (unsigned)__double2hiint(d), lo = (unsigned)__double2loint(d);
+    unsigned f = (hi & 0x80000000u) | ((unsigned)(e - 896) << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29);
+    const unsigned rem = lo & 0x1fffffffu, half = 1u << 28;
+    f += (rem > half || (rem == half && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(f);
+}
+
+// double(f), exact; zeros, subnormals, infinities and NaNs use the hardware.
+__device__ __forceinline__ double f2d(float f)
+{
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 255u) return (double)f;
+    return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)),
+                            (int)(b << 29));
+}
+
+// df_from_double with one FP64 operation (the exact subtraction d - hi).
+__device__ __forceinline__ DF df_from_double_i(double d)
+{
+    const float h = d2f_rn(d);
+    return DF{h, d2f_rn(d - f2d(h))};
+}
+
 __device__ __forceinline__ double df_to_double(DF a) { return (double)a.h + (double)a.l; }
 
 // s + e = a + b exactly (Knuth)

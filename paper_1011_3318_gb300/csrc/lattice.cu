@@ -81,7 +81,7 @@ __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, floa
                                      unsigned long long *maxdev)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double dev = 0.0;
+    float dev = 0.f;
     if (t < g.V * 4) {
         const long long x = t >> 2;
         const int mu = (int)(t & 3);
@@ -92,7 +92,7 @@ __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, floa
         for (int k = 0; k < 9; k++) {
             double2 v = u2[k];
             m[k] = {v.x, v.y};
-            d[k] = CDF{df_from_double(v.x), df_from_double(v.y)};
+            d[k] = CDF{df_from_double_i(v.x), df_from_double_i(v.y)};
         }
         // SU(3) check in double-float: max |(U^dag U - 1)_{ab}| and |det U - 1|.
         // The deviations are formed in double-float; their high words carry
@@ -123,7 +123,7 @@ __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, floa
             const DF dr = df_add(det.r, DF{-1.f, 0.f});
             devf = dev_max(devf, sqrtf(dr.h * dr.h + det.i.h * det.i.h));
         }
-        dev = isfinite(devf) ? (double)devf : 1e300;
+        dev = isfinite(devf) ? devf : 3.0e38f;
 
         const long long V = g.V;
 #pragma unroll
@@ -133,18 +133,20 @@ __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, floa
         }
 #pragma unroll
         for (int q = 0; q < 3; q++) {
+            // float(u) is the double-float high word
             U32[((long long)mu * 3 + q) * V + x] =
-                make_float4((float)m[2 * q].r, (float)m[2 * q].i, (float)m[2 * q + 1].r, (float)m[2 * q + 1].i);
-            __half2 h0 = __floats2half2_rn((float)m[2 * q].r, (float)m[2 * q].i);
-            __half2 h1 = __floats2half2_rn((float)m[2 * q + 1].r, (float)m[2 * q + 1].i);
+                make_float4(d[2 * q].r.h, d[2 * q].i.h, d[2 * q + 1].r.h, d[2 * q + 1].i.h);
+            __half2 h0 = __floats2half2_rn(d[2 * q].r.h, d[2 * q].i.h);
+            __half2 h1 = __floats2half2_rn(d[2 * q + 1].r.h, d[2 * q + 1].i.h);
             U16[((long long)mu * 3 + q) * V + x] =
                 make_uint2(*reinterpret_cast<unsigned *>(&h0), *reinterpret_cast<unsigned *>(&h1));
         }
     }
-    // block max, then one atomic per block on the bit pattern (non-negative
-    // doubles order like their bit patterns)
-    for (int o = 16; o > 0; o >>= 1) dev = fmax(dev, __shfl_xor_sync(0xffffffffu, dev, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(maxdev, (unsigned long long)__double_as_longlong(dev));
+    // warp max in FP32, then one atomic per warp on the bit pattern of the
+    // double (non-negative doubles order like their bit patterns)
+    for (int o = 16; o > 0; o >>= 1) dev = fmaxf(dev, __shfl_xor_sync(0xffffffffu, dev, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(maxdev, (unsigned long long)__double_as_longlong(dev >= 3.0e38f ? 1e300 : (double)dev));
 }
 
 cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void *U32, void *U16, void *Udf,
