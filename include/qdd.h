@@ -177,7 +177,7 @@ qdd_status qdd_ras_apply(qdd_lattice *lat, double *out, const double *in, double
  * plain FP64 BiCGStab when params->inner_prec == QDD_F64.  params NULL:
  * defaults.  phi is overwritten (no initial guess).  info may be NULL, else
  * it receives n_rhs entries.  The inner iterations run as a CUDA graph when
- * the lattice has a non-default stream and profiling is off.  Returns QDD_OK,
+ * the lattice has a non-default stream.  Returns QDD_OK,
  * QDD_ERR_NOT_CONVERGED (phi = best iterate), QDD_ERR_BREAKDOWN,
  * QDD_ERR_NONFINITE or QDD_ERR_TIMEOUT (the first failure over the
  * right-hand sides). */
@@ -266,8 +266,8 @@ typedef struct {
 unsigned long long qdd_kernel_launches(void);
 
 /* Turns per-class GPU timing on or off for this lattice: while on, every
- * launch is bracketed by CUDA events on the lattice's stream (about a
- * microsecond of overhead each). */
+ * launch is bracketed by CUDA events on the lattice's stream (inside a
+ * solve's captured graph, as event-record nodes read after each replay). */
 qdd_status qdd_set_profiling(qdd_lattice *lat, int on);
 
 /* Synchronises the lattice's stream and returns the per-class totals since

@@ -21,7 +21,21 @@ Profiler::~Profiler()
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
     }
+    for (auto &p : graph_pairs) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+void Profiler::release_graph()
+{
+    for (auto &p : graph_pairs) {
+        pool.push_back(p.a);
+        pool.push_back(p.b);
+    }
+    graph_pairs.clear();
+    graph_replays = 0;
 }
 
 cudaEvent_t Profiler::get()
@@ -41,6 +55,20 @@ cudaEvent_t Profiler::get()
 
 void Profiler::drain()
 {
+    // each replay of a captured graph re-records its pairs; one replay runs
+    // between two reads, so the pairs hold the last replay's times
+    if (graph_replays > 0) {
+        for (auto &p : graph_pairs) {
+            float ms_ = 0.f;
+            if (cudaEventElapsedTime(&ms_, p.a, p.b) == cudaSuccess) {
+                ms[p.cls] += ms_ * graph_replays;
+                n[p.cls] += graph_replays;
+            } else {
+                cudaGetLastError();
+            }
+        }
+        graph_replays = 0;
+    }
     for (auto &p : pending) {
         float ms_ = 0.f;
         if (cudaEventElapsedTime(&ms_, p.a, p.b) == cudaSuccess) {
@@ -59,7 +87,9 @@ ProfScope::ProfScope(qdd_lattice *lat, int cls) : prof(lat->prof), cls(cls), st(
 {
     if (!prof || !prof->on) return;
     a = prof->get();
-    if (a) cudaEventRecord(a, st);
+    // inside a stream capture only an "external" record becomes an event
+    // node that records a time stamp when the graph runs
+    if (a) cudaEventRecordWithFlags(a, st, prof->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
 }
 
 ProfScope::~ProfScope()
@@ -70,7 +100,11 @@ ProfScope::~ProfScope()
         prof->pool.push_back(a);
         return;
     }
-    cudaEventRecord(b, st);
+    cudaEventRecordWithFlags(b, st, prof->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
+    if (prof->capturing) {  // the records are nodes of the graph being captured
+        prof->graph_pairs.push_back(Profiler::Pair{cls, a, b});
+        return;
+    }
     prof->pending.push_back(Profiler::Pair{cls, a, b});
     // bound the number of outstanding pairs: drain (which waits) when many
     if (prof->pending.size() >= 4096) {

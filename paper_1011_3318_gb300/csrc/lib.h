@@ -26,11 +26,17 @@ struct Profiler {
     bool on = false;
     std::vector<cudaEvent_t> pool;
     std::vector<Pair> pending;
+    // pairs recorded while a CUDA graph is captured: event-record nodes of
+    // the graph, read after each replay and kept until the graph is released
+    bool capturing = false;
+    std::vector<Pair> graph_pairs;
+    int graph_replays = 0;  // replays since the graph pairs were last read
     double ms[QDD_NKCLASS] = {};
     long long n[QDD_NKCLASS] = {};
     ~Profiler();
     cudaEvent_t get();
-    void drain();  // after the stream has passed every pending event
+    void drain();          // after the stream has passed every pending event and replay
+    void release_graph();  // the graph holding graph_pairs is destroyed
 };
 
 // Dslash epilogues.

@@ -11,8 +11,9 @@
 // The inner iterations of all lattices are captured once into a CUDA graph
 // (forked across the lattices' streams) and replayed; kernels of a right-hand
 // side that has converged return at once, so the host can run several
-// iterations between status reads.  With per-kernel profiling on, or when a
-// lattice uses the legacy default stream, the same work is launched eagerly.
+// iterations between status reads.  Per-kernel profiling records its event
+// pairs as nodes of the graph.  When a lattice uses the legacy default
+// stream, the same work is launched eagerly.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -259,7 +260,6 @@ bool graph_capable(const std::vector<Member> &ms)
 {
     for (size_t i = 0; i < ms.size(); i++) {
         if (!ms[i].lat->stream) return false;
-        if (ms[i].lat->prof && ms[i].lat->prof->on) return false;
         for (size_t j = 0; j < i; j++)
             if (ms[j].lat->stream == ms[i].lat->stream) return false;
     }
@@ -273,9 +273,12 @@ struct IterGraph {
     std::vector<cudaEvent_t> events;  // fork/join inside the capture
     std::vector<cudaEvent_t> pre;     // member streams -> launch stream, before each launch
     cudaEvent_t post = nullptr;       // launch stream -> member streams, after each launch
+    std::vector<qdd_lattice *> lats;  // whose profilers hold event pairs recorded in the graph
     ~IterGraph()
     {
         if (exec) cudaGraphExecDestroy(exec);
+        for (qdd_lattice *lat : lats)
+            if (lat->prof) lat->prof->release_graph();
         for (cudaEvent_t e : events) cudaEventDestroy(e);
         for (cudaEvent_t e : pre) cudaEventDestroy(e);
         if (post) cudaEventDestroy(post);
@@ -295,9 +298,12 @@ qdd_status build_graph(std::vector<Member> &ms, int prec, const qdd_solver_param
             return cuda_fail(cudaGetLastError(), "event");
     if (cudaEventCreateWithFlags(&g.post, cudaEventDisableTiming) != cudaSuccess)
         return cuda_fail(cudaGetLastError(), "event");
+    for (Member &m : ms) g.lats.push_back(m.lat);
     const unsigned long long c0 = launch_count();
     cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    for (Member &m : ms)
+        if (m.lat->prof && m.lat->prof->on) m.lat->prof->capturing = true;
     qdd_status st = QDD_OK;
     cudaEventRecord(g.events[0], s0);
     for (size_t i = 1; i < ms.size(); i++) cudaStreamWaitEvent(ms[i].lat->stream, g.events[0], 0);
@@ -310,6 +316,8 @@ qdd_status build_graph(std::vector<Member> &ms, int prec, const qdd_solver_param
     }
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(s0, &graph);
+    for (Member &m : ms)
+        if (m.lat->prof) m.lat->prof->capturing = false;
     g.launches = launch_count() - c0;
     note_launch_adjust(-(long long)g.launches);  // counted again on every replay
     if (st != QDD_OK) {
@@ -477,6 +485,8 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                     cudaError_t e = cudaGraphLaunch(graph.exec, s0);
                     if (e != cudaSuccess) return cuda_fail(e, "graph launch");
                     note_launch_adjust((long long)graph.launches);
+                    for (Member &m : ms)
+                        if (m.lat->prof && !m.lat->prof->graph_pairs.empty()) m.lat->prof->graph_replays++;
                     cudaEventRecord(graph.post, s0);
                     for (size_t i = 1; i < ms.size(); i++) cudaStreamWaitEvent(ms[i].lat->stream, graph.post, 0);
                 }
