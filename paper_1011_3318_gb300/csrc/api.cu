@@ -247,6 +247,8 @@ qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc
     if (e == cudaSuccess) e = cudaMemset(lat->sc, 0, sizeof(Scalars) * n_rhs);
     if (e == cudaSuccess) e = cudaMemset(lat->ras_err, 0, 64);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&lat->sc_host, sizeof(Scalars) * n_rhs);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&lat->copy_stream, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; k++) e = cudaEventCreateWithFlags(&lat->copy_ev[k], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         qdd_destroy_lattice(lat);
         return cuda_fail(e, "lattice initialisation");
@@ -264,6 +266,12 @@ qdd_status qdd_destroy_lattice(qdd_lattice *lat)
                     lat->ras_scratch, lat->gauge_stage};
     for (void *p : ptrs) cudaFree(p);
     if (lat->sc_host) cudaFreeHost(lat->sc_host);
+    if (lat->copy_stream) {
+        cudaStreamSynchronize(lat->copy_stream);
+        cudaStreamDestroy(lat->copy_stream);
+    }
+    for (int k = 0; k < 2; k++)
+        if (lat->copy_ev[k]) cudaEventDestroy(lat->copy_ev[k]);
     work_free(lat->work);
     for (int p = 0; p < 3; p++)
         for (int k = 0; k < 2; k++) field_free(lat->io_d[p][k], lat->io_n[p][k]);
@@ -282,8 +290,11 @@ qdd_status qdd_load_gauge(qdd_lattice *lat, const double *U)
     const size_t bytes = (size_t)lat->g.V * 72 * sizeof(double);
     const double *src = U;
     cudaError_t e;
-    if (!is_device_ptr(U)) {
-        // host links go through a device staging buffer kept for later loads
+    e = cudaMemsetAsync(lat->maxdev, 0, sizeof(unsigned long long), lat->stream);
+    if (e == cudaSuccess && !is_device_ptr(U)) {
+        // host links go through a device staging buffer kept for later loads,
+        // in chunks of sites: the copy of chunk c + 1 (copy stream) overlaps
+        // the conversion of chunk c (lattice stream)
         if (!lat->gauge_stage) {
             e = cudaMalloc((void **)&lat->gauge_stage, bytes);
             if (e != cudaSuccess) {
@@ -291,12 +302,25 @@ qdd_status qdd_load_gauge(qdd_lattice *lat, const double *U)
                 return cuda_fail(e, "gauge staging");
             }
         }
-        e = cudaMemcpyAsync(lat->gauge_stage, U, bytes, cudaMemcpyHostToDevice, lat->stream);
-        if (e != cudaSuccess) return cuda_fail(e, "gauge copy");
-        src = lat->gauge_stage;
-    }
-    e = cudaMemsetAsync(lat->maxdev, 0, sizeof(unsigned long long), lat->stream);
-    if (e == cudaSuccess) {
+        const long long V = lat->g.V, per_site = 72;
+        const int chunks = V >= 65536 ? 8 : 1;
+        // the staging buffer is free once the lattice stream's earlier work is done
+        e = cudaEventRecord(lat->copy_ev[0], lat->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(lat->copy_stream, lat->copy_ev[0], 0);
+        for (int c = 0; c < chunks && e == cudaSuccess; c++) {
+            const long long s0 = V * c / chunks, s1 = V * (c + 1) / chunks;
+            e = cudaMemcpyAsync(lat->gauge_stage + s0 * per_site, U + s0 * per_site,
+                                (size_t)(s1 - s0) * per_site * sizeof(double), cudaMemcpyHostToDevice,
+                                lat->copy_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(lat->copy_ev[1], lat->copy_stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(lat->stream, lat->copy_ev[1], 0);
+            if (e == cudaSuccess) {
+                ProfScope ps(lat, QDD_K_CLOVER);
+                e = launch_gauge_convert(lat->g, lat->gauge_stage, lat->U64, lat->U32, lat->U16, lat->Udf,
+                                         lat->maxdev, lat->stream, s0, s1);
+            }
+        }
+    } else if (e == cudaSuccess) {
         ProfScope ps(lat, QDD_K_CLOVER);
         e = launch_gauge_convert(lat->g, src, lat->U64, lat->U32, lat->U16, lat->Udf, lat->maxdev, lat->stream);
     }
@@ -427,7 +451,23 @@ qdd_status qdd_solve(qdd_lattice *lat, double *phi, const double *eta, double ka
     }
     qdd_status st;
     const double *deta;
-    if ((st = stage_in(lat, eta, &lat->stage_a, &deta)) != QDD_OK) return st;
+    if (!is_device_ptr(eta)) {
+        // the host source is copied on the copy stream while the clover term
+        // is built on the lattice stream
+        if ((st = ensure_stage(lat, &lat->stage_a)) != QDD_OK) return st;
+        cudaError_t e = cudaEventRecord(lat->copy_ev[0], lat->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(lat->copy_stream, lat->copy_ev[0], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(lat->stage_a, eta, canon_bytes(lat), cudaMemcpyHostToDevice, lat->copy_stream);
+        if (e == cudaSuccess) e = cudaEventRecord(lat->copy_ev[1], lat->copy_stream);
+        if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+        if ((st = ensure_clover(lat, kappa, c_sw)) != QDD_OK) return st;
+        e = cudaStreamWaitEvent(lat->stream, lat->copy_ev[1], 0);
+        if (e != cudaSuccess) return cuda_fail(e, "host-to-device copy");
+        deta = lat->stage_a;
+    } else if ((st = stage_in(lat, eta, &lat->stage_a, &deta)) != QDD_OK) {
+        return st;
+    }
     double *dphi;
     bool host;
     if ((st = stage_out(lat, phi, &lat->stage_b, &dphi, &host)) != QDD_OK) return st;

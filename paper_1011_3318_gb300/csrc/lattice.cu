@@ -78,11 +78,11 @@ cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorVie
 __device__ __forceinline__ float dev_max(float a, float b) { return (b <= 3.0e38f) ? fmaxf(a, b) : 3.0e38f; }
 
 __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, float4 *U32, uint2 *U16, float4 *Udf,
-                                     unsigned long long *maxdev)
+                                     unsigned long long *maxdev, long long t0, long long t1)
 {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long t = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
     float dev = 0.f;
-    if (t < g.V * 4) {
+    if (t < t1) {
         const long long x = t >> 2;
         const int mu = (int)(t & 3);
         const double2 *u2 = reinterpret_cast<const double2 *>(U) + t * 9;
@@ -150,12 +150,14 @@ __global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, floa
 }
 
 cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void *U32, void *U16, void *Udf,
-                                 unsigned long long *maxdev, cudaStream_t st)
+                                 unsigned long long *maxdev, cudaStream_t st, long long site0, long long site1)
 {
-    const long long n = g.V * 4;
+    if (site1 < 0) site1 = g.V;
+    const long long n = (site1 - site0) * 4;
+    if (n <= 0) return cudaSuccess;
     const unsigned nb = (unsigned)((n + 255) / 256);
     gauge_convert_kernel<<<nb, 256, 0, st>>>(g, U, (double2 *)U64, (float4 *)U32, (uint2 *)U16, (float4 *)Udf,
-                                             maxdev);
+                                             maxdev, site0 * 4, site1 * 4);
     note_launch();
     return cudaGetLastError();
 }

@@ -72,10 +72,12 @@ cudaError_t launch_import_spinor(const Geom &g, int prec, SpinorView dst, const 
                                  cudaStream_t st);
 cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorView src, int nrhs, cudaStream_t st);
 
-// Gauge conversion; writes max(|U^dag U - 1|, |det U - 1|) as the bit
-// pattern of a non-negative double into *maxdev (device, zeroed first).
+// Gauge conversion of the links of sites [site0, site1) (site1 < 0: up to
+// V); writes max(|U^dag U - 1|, |det U - 1|) as the bit pattern of a
+// non-negative double into *maxdev (device, zeroed first; a running max).
 cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void *U32, void *U16, void *Udf,
-                                 unsigned long long *maxdev, cudaStream_t st);
+                                 unsigned long long *maxdev, cudaStream_t st, long long site0 = 0,
+                                 long long site1 = -1);
 
 // Clover term from the double-float links, stored in all three precisions.
 cudaError_t launch_clover_build(const Geom &g, const void *Udf, double kappa, double csw, void *A64, void *A32,
@@ -194,6 +196,9 @@ struct qdd_lattice {
     // canonical staging buffers for host pointers (spinors, and the links)
     double *stage_a, *stage_b;
     double *gauge_stage;
+    // host-to-device copies that overlap the lattice stream's work
+    cudaStream_t copy_stream;
+    cudaEvent_t copy_ev[2];
     // RAS scratch
     float2 *ras_scratch;
     size_t ras_scratch_bytes;
