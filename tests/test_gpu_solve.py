@@ -117,3 +117,24 @@ def test_point_source_far_field_fp16(qdd, oracle_mod):
     for prec in ("f16", "f32"):
         info = qdd.solve(lat, phi, eta, 0.124, 1.0, 1e-10, qdd.default_params(inner_prec=prec))
         assert info["status"] == 0 and op.true_residual(eta, phi) <= 1e-10
+
+
+@pytest.mark.parametrize("stream", [False, True])
+def test_back_to_back_host_solves(qdd, oracle_mod, stream):
+    """Host sources are copied on the lattice's copy stream while the clover
+    term is built: consecutive solves with different sources, kappas and a
+    reloaded gauge field (host links, chunked copy and conversion at 16^4)
+    must each see their own inputs."""
+    dims = (16, 16, 16, 16)
+    s = torch.cuda.Stream() if stream else None
+    lat = qdd.create_lattice(dims, BC, stream=s)
+    p = qdd.default_params(inner_prec="f16")
+    for k, (gseed, sseed, kappa) in enumerate([(5, 6, 0.12), (5, 7, 0.121), (8, 9, 0.12)]):
+        U = synth.gauge_field(dims, 0.3, gseed)
+        eta = synth.gaussian_source(dims, sseed)
+        if k != 1:
+            qdd.load_gauge(lat, U)
+        phi = np.empty_like(eta)
+        info = qdd.solve(lat, phi, eta, kappa, 1.0, 1e-10, p)
+        op = oracle_mod.Op(dims, BC, U, kappa, 1.0, store_clover=True)
+        assert info["status"] == 0 and op.true_residual(eta, phi) <= 1e-10
