@@ -77,15 +77,35 @@ cudaError_t launch_export_spinor(const Geom &g, int prec, double *dst, SpinorVie
 // max(a, b) where a NaN b counts as the largest deviation (fmaxf would drop it)
 __device__ __forceinline__ float dev_max(float a, float b) { return (b <= 3.0e38f) ? fmaxf(a, b) : 3.0e38f; }
 
-__global__ void gauge_convert_kernel(Geom g, const double *U, double2 *U64, float4 *U32, uint2 *U16, float4 *Udf,
-                                     unsigned long long *maxdev, long long t0, long long t1)
+// One block converts the 4 links of GC_SITES consecutive sites.  The
+// canonical links of those sites are one contiguous range of 144-byte
+// records: the block reads it with coalesced 16-byte loads into shared
+// memory, and thread (mu, site) takes its record from there, so that a warp
+// then writes 32 consecutive sites of one plane of each internal copy.
+constexpr int GC_SITES = 64;
+constexpr int GC_THREADS = 4 * GC_SITES;
+
+__global__ void __launch_bounds__(GC_THREADS) gauge_convert_kernel(Geom g, const double *U, double2 *U64, float4 *U32,
+                                                                  uint2 *U16, float4 *Udf, unsigned long long *maxdev,
+                                                                  long long site0, long long site1)
 {
-    const long long t = t0 + (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    // a site's 36 complex numbers at a stride of 37 (16-byte units), so that
+    // the 32 sites a warp reads fall into different shared-memory banks
+    constexpr int SREC = 37;
+    __shared__ double2 srec[GC_SITES * SREC];
+    const long long xb = site0 + (long long)blockIdx.x * GC_SITES;  // first site of the block
+    const long long nsite = min((long long)GC_SITES, site1 - xb);
+    {
+        const double2 *src = reinterpret_cast<const double2 *>(U) + xb * 36;
+        const int n = (int)nsite * 36;
+        for (int i = threadIdx.x; i < n; i += GC_THREADS) srec[(i / 36) * SREC + i % 36] = src[i];
+    }
+    __syncthreads();
+    const int mu = threadIdx.x / GC_SITES, ls = threadIdx.x % GC_SITES;
+    const long long x = xb + ls;
     float dev = 0.f;
-    if (t < t1) {
-        const long long x = t >> 2;
-        const int mu = (int)(t & 3);
-        const double2 *u2 = reinterpret_cast<const double2 *>(U) + t * 9;
+    if (ls < nsite) {
+        const double2 *u2 = srec + ls * SREC + mu * 9;
         C<double> m[9];
         CDF d[9];
 #pragma unroll
@@ -153,11 +173,11 @@ cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void
                                  unsigned long long *maxdev, cudaStream_t st, long long site0, long long site1)
 {
     if (site1 < 0) site1 = g.V;
-    const long long n = (site1 - site0) * 4;
+    const long long n = site1 - site0;
     if (n <= 0) return cudaSuccess;
-    const unsigned nb = (unsigned)((n + 255) / 256);
-    gauge_convert_kernel<<<nb, 256, 0, st>>>(g, U, (double2 *)U64, (float4 *)U32, (uint2 *)U16, (float4 *)Udf,
-                                             maxdev, site0 * 4, site1 * 4);
+    const unsigned nb = (unsigned)((n + GC_SITES - 1) / GC_SITES);
+    gauge_convert_kernel<<<nb, GC_THREADS, 0, st>>>(g, U, (double2 *)U64, (float4 *)U32, (uint2 *)U16, (float4 *)Udf,
+                                                    maxdev, site0, site1);
     note_launch();
     return cudaGetLastError();
 }
