@@ -60,6 +60,11 @@ struct DomainGeom {
     int nb[4];   // blocks per direction
     int ndom;
     int nloc;    // sites in an extended domain
+    // division by nb[mu] and e[mu] of numerators below 2^31 as a multiply-high
+    // and a shift (Granlund and Montgomery): n / d = umulhi(n, m) >> sh for
+    // d >= 2, with m = ceil(2^p / d), p = 31 + ceil(log2 d), sh = p - 32
+    unsigned nb_m[4], e_m[4];
+    int nb_sh[4], e_sh[4];
 };
 
 // Solver scalars kept on the device so that an iteration needs no host

@@ -42,6 +42,12 @@ struct DomSite {
     float cf[4], cb[4];
 };
 
+// n / d for 0 <= n < 2^31 with the divisor's precomputed multiplier
+__device__ __forceinline__ int fast_div(int n, int d, unsigned m, int sh)
+{
+    return d >= 2 ? (int)(__umulhi((unsigned)n, m) >> sh) : n;
+}
+
 __device__ __forceinline__ void dom_site(const Geom &g, const DomainGeom &dg, int dom, int l, float kappa,
                                          DomSite &s)
 {
@@ -51,17 +57,26 @@ __device__ __forceinline__ void dom_site(const Geom &g, const DomainGeom &dg, in
     {
         int r = dom;
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) { k[mu] = r % dg.nb[mu]; r /= dg.nb[mu]; }
+        for (int mu = 0; mu < 4; mu++) {
+            const int q = fast_div(r, dg.nb[mu], dg.nb_m[mu], dg.nb_sh[mu]);
+            k[mu] = r - q * dg.nb[mu];
+            r = q;
+        }
         r = ll;
 #pragma unroll
-        for (int mu = 0; mu < 4; mu++) { lc[mu] = r % dg.e[mu]; r /= dg.e[mu]; }
+        for (int mu = 0; mu < 4; mu++) {
+            const int q = fast_div(r, dg.e[mu], dg.e_m[mu], dg.e_sh[mu]);
+            lc[mu] = r - q * dg.e[mu];
+            r = q;
+        }
     }
     s.x = 0;
     s.bulk = s.act;
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
-        int v = (k[mu] * dg.b[mu] - dg.sh[mu] + lc[mu]) % g.L[mu];
+        int v = k[mu] * dg.b[mu] - dg.sh[mu] + lc[mu];  // in (-L, 2L)
         if (v < 0) v += g.L[mu];
+        else if (v >= g.L[mu]) v -= g.L[mu];
         gc[mu] = v;
         s.x += (long long)v * g.stride[mu];
         if (lc[mu] < dg.sh[mu] || lc[mu] >= dg.sh[mu] + dg.b[mu]) s.bulk = false;
@@ -213,19 +228,29 @@ __device__ __forceinline__ void loc_site(const Geom &g, const DomainGeom &dg, in
     int k[4], lc[4];
     int r = dom;
 #pragma unroll
-    for (int mu = 0; mu < 4; mu++) { k[mu] = r % dg.nb[mu]; r /= dg.nb[mu]; }
+    for (int mu = 0; mu < 4; mu++) {
+        const int q = fast_div(r, dg.nb[mu], dg.nb_m[mu], dg.nb_sh[mu]);
+        k[mu] = r - q * dg.nb[mu];
+        r = q;
+    }
     const bool act = l < dg.nloc;
     r = act ? l : 0;
 #pragma unroll
-    for (int mu = 0; mu < 4; mu++) { lc[mu] = r % dg.e[mu]; r /= dg.e[mu]; }
+    for (int mu = 0; mu < 4; mu++) {
+        const int q = fast_div(r, dg.e[mu], dg.e_m[mu], dg.e_sh[mu]);
+        lc[mu] = r - q * dg.e[mu];
+        r = q;
+    }
     unsigned m = act ? (unsigned)M_ACT : 0u;
     bool bulk = act;
     long long x = 0;
     int ls = 1;
 #pragma unroll
     for (int mu = 0; mu < 4; mu++) {
-        int gc = (k[mu] * dg.b[mu] - dg.sh[mu] + lc[mu]) % g.L[mu];
+        // k b - sh + lc lies in (-L, 2L): one conditional wrap
+        int gc = k[mu] * dg.b[mu] - dg.sh[mu] + lc[mu];
         if (gc < 0) gc += g.L[mu];
+        else if (gc >= g.L[mu]) gc -= g.L[mu];
         x += (long long)gc * g.stride[mu];
         if (lc[mu] < dg.sh[mu] || lc[mu] >= dg.sh[mu] + dg.b[mu]) bulk = false;
         const int e = dg.e[mu];
@@ -924,6 +949,17 @@ bool domain_geom(const Geom &g, const int block[4], int s, DomainGeom *dg, std::
         return false;
     }
     dg->nloc = (int)nloc;
+    auto magic = [](int d, unsigned *m, int *sh) {
+        int l = 0;
+        while ((1LL << l) < d) l++;
+        const int p = 31 + l;
+        *m = d >= 2 ? (unsigned)(((1ULL << p) + (unsigned long long)d - 1) / (unsigned long long)d) : 0u;
+        *sh = d >= 2 ? p - 32 : 0;
+    };
+    for (int mu = 0; mu < 4; mu++) {
+        magic(dg->nb[mu], &dg->nb_m[mu], &dg->nb_sh[mu]);
+        magic(dg->e[mu], &dg->e_m[mu], &dg->e_sh[mu]);
+    }
     return true;
 }
 
