@@ -76,8 +76,9 @@ template <typename T> __device__ __forceinline__ C<T> cconj(C<T> a) { return {a.
 
 // ---------------------------------------------------------------- geometry
 // Coordinates of site x.  Site indices fit in 32 bits (the lattice volume
-// is capped at 2^31), so the divisions are 32-bit: 64-bit integer division is
-// emulated by a long instruction sequence on the GPU.
+// is capped), so the divisions are 32-bit: 64-bit integer division is
+// emulated by a long instruction sequence on the GPU.  (Multiply-high
+// division here changed the register allocation of the FP32 D for the worse.)
 __device__ __forceinline__ void site_coords(const Geom &g, long long x, int c[4])
 {
     unsigned r = (unsigned)x;

@@ -188,8 +188,11 @@ typedef C<double> Z;
 __device__ __forceinline__ long long shifted(const Geom &g, const int c[4], int mu, int dm, int nu, int dn)
 {
     int d[4] = {c[0], c[1], c[2], c[3]};
-    d[mu] = (d[mu] + dm + g.L[mu]) % g.L[mu];
-    d[nu] = (d[nu] + dn + g.L[nu]) % g.L[nu];
+    // dm, dn in {-1, 0, 1}: one conditional wrap each
+    d[mu] += dm;
+    d[mu] += d[mu] < 0 ? g.L[mu] : (d[mu] >= g.L[mu] ? -g.L[mu] : 0);
+    d[nu] += dn;
+    d[nu] += d[nu] < 0 ? g.L[nu] : (d[nu] >= g.L[nu] ? -g.L[nu] : 0);
     return d[0] + g.stride[1] * d[1] + g.stride[2] * d[2] + g.stride[3] * d[3];
 }
 

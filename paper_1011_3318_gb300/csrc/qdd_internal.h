@@ -37,6 +37,17 @@ struct Geom {
     long long V;
 };
 
+// Multiplier and shift of the division by d (1 <= d <= 2^30) for numerators
+// below 2^31: m = ceil(2^p / d), p = 31 + ceil(log2 d), shift p - 32.
+inline void division_magic(int d, unsigned *m, int *sh)
+{
+    int l = 0;
+    while ((1LL << l) < d) l++;
+    const int p = 31 + l;
+    *m = d >= 2 ? (unsigned)(((1ULL << p) + (unsigned long long)d - 1) / (unsigned long long)d) : 0u;
+    *sh = d >= 2 ? p - 32 : 0;
+}
+
 // A spinor field in the internal layout of its precision.
 struct SpinorView {
     void *d;

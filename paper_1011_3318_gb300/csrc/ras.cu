@@ -949,16 +949,9 @@ bool domain_geom(const Geom &g, const int block[4], int s, DomainGeom *dg, std::
         return false;
     }
     dg->nloc = (int)nloc;
-    auto magic = [](int d, unsigned *m, int *sh) {
-        int l = 0;
-        while ((1LL << l) < d) l++;
-        const int p = 31 + l;
-        *m = d >= 2 ? (unsigned)(((1ULL << p) + (unsigned long long)d - 1) / (unsigned long long)d) : 0u;
-        *sh = d >= 2 ? p - 32 : 0;
-    };
     for (int mu = 0; mu < 4; mu++) {
-        magic(dg->nb[mu], &dg->nb_m[mu], &dg->nb_sh[mu]);
-        magic(dg->e[mu], &dg->e_m[mu], &dg->e_sh[mu]);
+        division_magic(dg->nb[mu], &dg->nb_m[mu], &dg->nb_sh[mu]);
+        division_magic(dg->e[mu], &dg->e_m[mu], &dg->e_sh[mu]);
     }
     return true;
 }
