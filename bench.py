@@ -206,6 +206,10 @@ def host_cpu():
     except OSError:
         pass
     import platform
+    arm_parts = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1",
+                 "0xd49": "Arm Neoverse N2"}
+    if model in arm_parts:
+        model = f"{arm_parts[model]} (CPU part {model})"
     return {"model": model or platform.processor() or platform.machine(), "machine": platform.machine(),
             "nproc": os.cpu_count()}
 
