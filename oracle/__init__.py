@@ -12,7 +12,8 @@ the paper it follows (Osaki & Ishikawa, Lattice 2010):
 * ``dslash``       Eq. 1, the Wilson-clover operator D (Sec. 1, Sec. 5);
 * ``clover``       the O(a) improvement term of Sec. 5 (c_SW);
 * ``domain_*``     the Dirichlet-restricted operator and domain solve of Alg. 1;
-* ``ras``          Alg. 1, phi = K_RAS eta;
+* ``ras``          Alg. 1, phi = K_RAS eta (and the AS / SAP members of the
+                   Schwarz family, Sec. 1 and Sec. 2);
 * ``bicgstab``     the right-preconditioned Krylov solve of Eq. 3;
 * ``solve``        the nested solver of Sec. 3 (FP64 defect correction).
 
@@ -56,7 +57,14 @@ class OraOp(ctypes.Structure):
 
 class OraPrec(ctypes.Structure):
     _fields_ = [("use_ras", ctypes.c_int), ("block", ctypes.c_int * 4), ("s", ctypes.c_int),
-                ("n_ras", ctypes.c_int), ("n_dominv", ctypes.c_int), ("dom_solver", ctypes.c_int)]
+                ("n_ras", ctypes.c_int), ("n_dominv", ctypes.c_int), ("dom_solver", ctypes.c_int),
+                ("schwarz", ctypes.c_int)]
+
+
+# Members of the Schwarz family (ora_prec.schwarz): RAS is Alg. 1; SAP is the
+# multiplicative alternating procedure over a red/black block ordering; AS is
+# the additive iteration without the restriction (overlaps summed).
+SCHWARZ = {"ras": 0, "sap": 1, "as": 2}
 
 
 class OraInfo(ctypes.Structure):
@@ -209,10 +217,14 @@ class Op:
         return out
 
     # -- Alg. 1, Eq. 3, Sec. 3 ------------------------------------------
-    def ras(self, eta, block, s: int = 0, n_ras: int = 3, n_dominv: int = 4, exact: bool = False):
+    def ras(self, eta, block, s: int = 0, n_ras: int = 3, n_dominv: int = 4, exact: bool = False,
+            schwarz: str = "ras"):
+        """NRAS cycles of the Schwarz iteration from phi = 0 (Alg. 1 for
+        schwarz="ras"; "sap" and "as" are the multiplicative and the plain
+        additive members of the family, Sec. 1 and Sec. 2)."""
         eta, pe = _c(eta)
         out = np.empty(self.shape(), dtype=np.complex128)
-        p = prec(True, block, s, n_ras, n_dominv, exact)
+        p = prec(True, block, s, n_ras, n_dominv, exact, schwarz)
         if lib().ora_ras(ctypes.byref(self._s), ctypes.byref(p), pe, out.ctypes.data):
             raise ValueError("invalid blocking")
         return out
@@ -250,5 +262,6 @@ class Op:
 
 
 def prec(use_ras: bool, block=(4, 4, 4, 4), s: int = 0, n_ras: int = 3, n_dominv: int = 4,
-         exact: bool = False) -> OraPrec:
-    return OraPrec(int(bool(use_ras)), _i4(block), int(s), int(n_ras), int(n_dominv), int(bool(exact)))
+         exact: bool = False, schwarz: str = "ras") -> OraPrec:
+    return OraPrec(int(bool(use_ras)), _i4(block), int(s), int(n_ras), int(n_dominv), int(bool(exact)),
+                   SCHWARZ[schwarz])

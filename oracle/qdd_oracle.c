@@ -17,6 +17,11 @@
  *   - Sec. 2, Eq. 2: K_RAS = S sum_j (1 - D S)^j, S = sum_i R_i D_i'^-1 P_i.
  *   - Sec. 2, Eq. 3: right preconditioning D K chi = eta, phi = K chi.
  *   - Sec. 2 (parameters d, N_dominv, NRAS) and Sec. 4 (extension s, d = 2s).
+ *   - Sec. 1 and Sec. 2 (the Schwarz family): plain additive Schwarz (AS,
+ *     the domain solutions summed over every extended site) and the
+ *     multiplicative Schwarz alternating procedure (SAP, domains of one colour
+ *     of a red/black block ordering at a time, the residual updated between
+ *     the colours), as comparisons to RAS.
  *   - Sec. 3: mixed-precision nested BiCGStab (inner solve preconditions the
  *     outer); here every level is FP64.
  *   - Sec. 5: O(a)-improved Wilson quark, kappa, c_SW, stopping rule
@@ -80,7 +85,11 @@ typedef struct {
     int n_ras;         /* NRAS */
     int n_dominv;      /* N_dominv */
     int dom_solver;    /* 0: MR with n_dominv iterations; 1: exact */
+    int schwarz;       /* 0: RAS (Alg. 1); 1: SAP (multiplicative, red/black);
+                          2: AS (additive, no restriction) */
 } ora_prec;
+
+enum { ORA_RAS = 0, ORA_SAP = 1, ORA_AS = 2 };
 
 typedef struct {
     int outer_iters;
@@ -692,40 +701,77 @@ int ora_domain_solve(const ora_op *op, const ora_prec *p, int dom, const cplx *r
 /* RAS iteration (Alg. 1): phi = K_RAS eta                                    */
 /* ------------------------------------------------------------------------ */
 
+/* Colour of a domain in the red/black block ordering: the parity of the sum
+ * of its block coordinates. */
+static int dd_color(const ora_dd *d, int dom)
+{
+    int sum = 0, r = dom;
+    for (int mu = 0; mu < 4; mu++) {
+        sum += r % d->nb[mu];
+        r /= d->nb[mu];
+    }
+    return sum & 1;
+}
+
+/* v = sum over the domains i of colour `color` (every domain when color < 0)
+ * of the solution of D_i' v_i' = P_i' r (Alg. 1 lines 3-8), restricted to the
+ * bulk sites (restrict_bulk = 1: R_i, RAS) or prolonged onto every site of the
+ * extended domain with the overlaps summed (restrict_bulk = 0: AS). */
+static void dd_sweep(const ora_op *op, const ora_dd *d, const ora_prec *p, int color, int restrict_bulk,
+                     const cplx *r, cplx *v)
+{
+    memset(v, 0, volume(op->L) * 12 * sizeof(cplx));
+#pragma omp parallel for schedule(dynamic)
+    for (int i = 0; i < d->ndom; i++) {                 /* line 3 */
+        if (color >= 0 && dd_color(d, i) != color) continue;
+        long *g = malloc(d->nloc * sizeof(long));
+        int *bulk = malloc(d->nloc * sizeof(int));
+        cplx *rl = malloc(d->nloc * 12 * sizeof(cplx)), *vl = malloc(d->nloc * 12 * sizeof(cplx));
+        for (long l = 0; l < d->nloc; l++) g[l] = dd_global(d, i, l, &bulk[l]);
+        /* line 4: projection r_i' = P_i' r */
+        for (long l = 0; l < d->nloc; l++) memcpy(rl + l * 12, r + g[l] * 12, 12 * sizeof(cplx));
+        /* line 5: solve D_i' v_i' = r_i' with the Dirichlet boundary */
+        dd_solve(op, d, g, p, rl, vl);
+        /* lines 6 and 8: v_i = R_i v_i', v = sum_i v_i (bulk sites are disjoint);
+         * without the restriction the extended domains overlap */
+        if (restrict_bulk) {
+            for (long l = 0; l < d->nloc; l++)
+                if (bulk[l])
+                    for (int k = 0; k < 12; k++) v[g[l] * 12 + k] += vl[l * 12 + k];
+        } else {
+#pragma omp critical(ora_as_sum)
+            for (long l = 0; l < d->nloc; l++)
+                for (int k = 0; k < 12; k++) v[g[l] * 12 + k] += vl[l * 12 + k];
+        }
+        free(g); free(bulk); free(rl); free(vl);
+    }
+}
+
+/* NRAS Schwarz cycles from phi = 0.  RAS (Alg. 1) and AS do one sweep over
+ * all domains per cycle; SAP does the red domains, updates the residual, then
+ * the black domains.  Every sweep ends with line 9: phi += v, r -= D v. */
 int ora_ras(const ora_op *op, const ora_prec *p, const cplx *eta, cplx *phi)
 {
     ora_dd d;
     if (dd_init(&d, op->L, op->bc, p->block, p->s)) return -1;
+    if (p->schwarz < ORA_RAS || p->schwarz > ORA_AS) return -1;
     long V = volume(op->L), n = V * 12;
     cplx *r = malloc(n * sizeof(cplx)), *v = malloc(n * sizeof(cplx)), *dv = malloc(n * sizeof(cplx));
+    const int ncolor = p->schwarz == ORA_SAP ? 2 : 1;
 
     /* line 1: phi = 0, r = eta */
     memset(phi, 0, n * sizeof(cplx));
     memcpy(r, eta, n * sizeof(cplx));
 
     for (int j = 0; j < p->n_ras; j++) {               /* line 2 */
-        memset(v, 0, n * sizeof(cplx));
-#pragma omp parallel for schedule(dynamic)
-        for (int i = 0; i < d.ndom; i++) {              /* line 3 */
-            long *g = malloc(d.nloc * sizeof(long));
-            int *bulk = malloc(d.nloc * sizeof(int));
-            cplx *rl = malloc(d.nloc * 12 * sizeof(cplx)), *vl = malloc(d.nloc * 12 * sizeof(cplx));
-            for (long l = 0; l < d.nloc; l++) g[l] = dd_global(&d, i, l, &bulk[l]);
-            /* line 4: projection r_i' = P_i' r */
-            for (long l = 0; l < d.nloc; l++) memcpy(rl + l * 12, r + g[l] * 12, 12 * sizeof(cplx));
-            /* line 5: solve D_i' v_i' = r_i' with the Dirichlet boundary */
-            dd_solve(op, &d, g, p, rl, vl);
-            /* lines 6 and 8: v_i = R_i v_i', v = sum_i v_i (bulk sites are disjoint) */
-            for (long l = 0; l < d.nloc; l++)
-                if (bulk[l])
-                    for (int k = 0; k < 12; k++) v[g[l] * 12 + k] += vl[l * 12 + k];
-            free(g); free(bulk); free(rl); free(vl);
-        }
-        /* line 9: phi = phi + v, r = r - D v */
-        ora_dslash(op, v, dv);
-        for (long k = 0; k < n; k++) {
-            phi[k] += v[k];
-            r[k] -= dv[k];
+        for (int c = 0; c < ncolor; c++) {
+            dd_sweep(op, &d, p, p->schwarz == ORA_SAP ? c : -1, p->schwarz != ORA_AS, r, v);
+            /* line 9: phi = phi + v, r = r - D v */
+            ora_dslash(op, v, dv);
+            for (long k = 0; k < n; k++) {
+                phi[k] += v[k];
+                r[k] -= dv[k];
+            }
         }
     }
     free(r); free(v); free(dv);
@@ -762,8 +808,9 @@ int ora_bicgstab(const ora_op *op, const ora_prec *p, const cplx *b, cplx *x,
     int dv = 0, it = 0;
     int st = bicgstab(n, dslash_cb, &c, p && p->use_ras ? ras_cb : NULL, &c, b, x, tol, maxit, &it, &dv);
     if (iters) *iters = it;
-    /* D applications inside K_RAS: NRAS per preconditioner call (line 9), two calls per iteration */
-    if (ndv) *ndv = dv + (p && p->use_ras ? it * 2 * p->n_ras : 0);
+    /* D applications inside the preconditioner: one per sweep (line 9), NRAS
+     * sweeps per call (2 NRAS for SAP), two calls per iteration */
+    if (ndv) *ndv = dv + (p && p->use_ras ? it * 2 * p->n_ras * (p->schwarz == ORA_SAP ? 2 : 1) : 0);
     return st;
 }
 

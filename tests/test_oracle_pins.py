@@ -367,6 +367,140 @@ def test_ras_sweeps_converge_to_inverse(small_system):
     assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-3
 
 
+# ---------------------------------------------------------------- Schwarz variants
+def block_color(dims, block, dom):
+    """Red/black colour of a domain: parity of the sum of its block coordinates."""
+    nb = [L // b for L, b in zip(dims, block)]
+    k, r = [], dom
+    for mu in range(4):
+        k.append(r % nb[mu])
+        r //= nb[mu]
+    return sum(k) % 2
+
+
+def dense_domain_sweep(op, block, s, restrict, color=None):
+    """S = sum_i Q_i D_i'^{-1} P_i' over the domains of one colour (all when
+    colour is None): Q_i = R_i (bulk sites) for RAS and SAP, Q_i = P_i'^T (every
+    extended site, overlaps summed) for AS; D_i' assembled column by column
+    from the Dirichlet operator and inverted by LAPACK."""
+    n = op.V * 12
+    S = np.zeros((n, n), complex)
+    for dom in range(op.ndomains(block, s)):
+        if color is not None and block_color(op.dims, block, dom) != color:
+            continue
+        sites, bulk = op.domain_sites(block, s, dom)
+        idx = (sites[:, None] * 12 + np.arange(12)[None]).reshape(-1)
+        Dd = dense(lambda v: op.domain_apply(block, s, dom, v.reshape(-1, 4, 3)), idx.size)
+        inv = np.linalg.inv(Dd)
+        keep = np.repeat(bulk, 12) if restrict else np.ones(idx.size, bool)
+        np.add.at(S, (idx[keep][:, None], idx[None, :]), inv[keep])
+    return S
+
+
+def stationary(Dm, sweeps, eta, ncycles):
+    """x_0 = 0; each cycle applies x += S_c (eta - D x) for every S_c in turn."""
+    x = np.zeros_like(eta)
+    for _ in range(ncycles):
+        for S in sweeps:
+            x = x + S @ (eta - Dm @ x)
+    return x
+
+
+@pytest.fixture(scope="module")
+def schwarz_system(oracle_mod):
+    dims = (8, 4, 2, 2)
+    op = oracle_mod.Op(dims, BC_AP, synth.gauge_field(dims, 0.3, 301), 0.12, 1.0)
+    Dm = dense(lambda v: op.dslash(v.reshape(op.V, 4, 3)), op.V * 12)
+    eta = synth.gaussian_source(dims, 302)
+    return op, Dm, eta
+
+
+def test_sap_without_overlap_is_block_gauss_seidel(schwarz_system):
+    """Multiplicative Schwarz with exact domain solves and no overlap is block
+    Gauss-Seidel over the red/black ordering: one cycle gives x = M^{-1} eta with
+    M the block lower-triangular part [[D_RR, 0], [D_BR, D_BB]] of D (red
+    blocks first), built here from the dense matrix by masking, not from the
+    domains."""
+    op, Dm, eta = schwarz_system
+    block = (2, 2, 2, 2)
+    c = coords(op.dims)
+    red_site = ((c[:, 0] // 2 + c[:, 1] // 2) % 2) == 0
+    red = np.repeat(red_site, 12)
+    M = Dm.copy()
+    M[np.ix_(red, ~red)] = 0.0
+    e = eta.reshape(-1)
+    x = np.zeros_like(e)
+    for ncyc in (1, 2, 3):
+        x = x + np.linalg.solve(M, e - Dm @ x)
+        phi = op.ras(eta, block, s=0, n_ras=ncyc, exact=True, schwarz="sap")
+        assert rel(phi.reshape(-1), x) < 1e-11
+    # block Jacobi (the additive sweep) is a different operator
+    assert rel(op.ras(eta, block, s=0, n_ras=1, exact=True).reshape(-1),
+               np.linalg.solve(M, e)) > 1e-3
+
+
+@pytest.mark.parametrize("s", [0, 1])
+def test_sap_and_as_match_dense_schwarz_operators(schwarz_system, s):
+    """SAP: x += S_red (eta - D x), then x += S_black (eta - D x) per cycle with
+    the restricted colour sums; AS: x += S_AS (eta - D x) with the unrestricted
+    sum over extended domains (Sec. 2)."""
+    op, Dm, eta = schwarz_system
+    block = (4, 2, 2, 2)
+    e = eta.reshape(-1)
+    S_red = dense_domain_sweep(op, block, s, True, 0)
+    S_black = dense_domain_sweep(op, block, s, True, 1)
+    S_as = dense_domain_sweep(op, block, s, False)
+    for ncyc in (1, 2):
+        sap = op.ras(eta, block, s=s, n_ras=ncyc, exact=True, schwarz="sap")
+        assert rel(sap.reshape(-1), stationary(Dm, [S_red, S_black], e, ncyc)) < 1e-11
+        add = op.ras(eta, block, s=s, n_ras=ncyc, exact=True, schwarz="as")
+        assert rel(add.reshape(-1), stationary(Dm, [S_as], e, ncyc)) < 1e-11
+
+
+def test_as_without_overlap_is_ras(schwarz_system):
+    """With d = 0 the extended domains are the bulk blocks: AS and RAS coincide
+    (the restriction removes nothing)."""
+    op, _, eta = schwarz_system
+    for block in [(2, 2, 2, 2), (4, 2, 2, 2)]:
+        a = op.ras(eta, block, s=0, n_ras=2, n_dominv=3, schwarz="as")
+        r = op.ras(eta, block, s=0, n_ras=2, n_dominv=3)
+        assert np.array_equal(a, r)
+
+
+def test_sap_whole_lattice_block_is_exact_inverse(small_system):
+    """One domain (red) covering the lattice with an exact solve: the black
+    half-sweep has nothing to do and K_SAP = D^{-1}."""
+    op, Dm, eta, x = small_system
+    phi = op.ras(eta, op.dims, s=0, n_ras=1, exact=True, schwarz="sap")
+    assert rel(phi, x) < 1e-11
+
+
+@pytest.mark.parametrize("schwarz", ["sap", "as"])
+def test_schwarz_kappa_zero_is_exact(oracle_mod, schwarz):
+    """With the hopping off D = A is site-local and every member of the family
+    inverts it in one cycle (AS sums overlapping copies: only without overlap)."""
+    dims = (8, 4, 4, 4)
+    U = synth.gauge_field(dims, 0.3, 303)
+    A = oracle_mod.clover(dims, U, 0.12, 1.0)
+    op = oracle_mod.Op(dims, BC_AP, U, 0.0, 1.0, A=A)
+    eta = synth.gaussian_source(dims, 304)
+    expect = np.linalg.solve(A, eta.reshape(op.V, 12)[..., None])[..., 0]
+    for block, s in [((2, 2, 2, 2), 0), ((4, 2, 2, 2), 1 if schwarz == "sap" else 0)]:
+        phi = op.ras(eta, block, s=s, n_ras=1, exact=True, schwarz=schwarz)
+        assert rel(phi.reshape(op.V, 12), expect) < 1e-12
+
+
+def test_sap_converges_faster_than_ras_per_cycle(small_system):
+    """The multiplicative sweep uses the red update before the black solve;
+    on this system its cycles contract faster than the additive ones."""
+    op, Dm, eta, x = small_system
+    block = (2, 2, 2, 2)
+    for k in (2, 4):
+        sap = rel(op.ras(eta, block, s=0, n_ras=k, exact=True, schwarz="sap"), x)
+        ras = rel(op.ras(eta, block, s=0, n_ras=k, exact=True), x)
+        assert sap < ras
+
+
 # ---------------------------------------------------------------- the config-1 contract
 def test_config1_plain_fp64_solve(oracle_mod):
     """8^4, eps = 0.3 (seed 1), kappa = 0.12, c_sw = 1, Gaussian source (seed 2),
