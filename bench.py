@@ -544,6 +544,11 @@ def run_workload(args):
                4 x 32^3, d = 0, 2, 4, NRAS 3, N_dominv 5, FP32 inner, kappa
                0.126, tolerance 1e-14, and no preconditioner; Dv counts and
                times beside the paper's (context only);
+      schwarz -- the 32^4 workload solved with each member of the Schwarz
+               family as K (RAS, red/black SAP, plain AS; Sec. 1, Sec. 2), 4^4
+               blocks, N_dominv 4, FP16 inner, 1..3 cycles, d in {0, 2} (AS:
+               one cycle, d in {2, 4}, as AS with d = 0 is RAS), each solve
+               timed once after an untimed one;
       survey -- the paper's parameter survey (Sec. 5) on the 32^4 workload:
                NRAS 1..10 x N_dominv 1..20 x d = 2s in {0, 2, 4}, 4^4 blocks,
                FP16 inner, each solve timed once after one untimed solve of the
@@ -635,6 +640,42 @@ def run_workload(args):
                if paper else None,
                "converged": len(done), "points": len(grid), "skipped_over_budget": skipped,
                "budget_s": budget_s, "grid": grid}
+    elif args.workload == "schwarz":
+        U = synth.gauge_field(DIMS, EPS, GSEED)
+        eta = synth.gaussian_source(DIMS, SSEED)
+        st = torch.cuda.Stream()
+        lat = qdd.create_lattice(DIMS, BC, stream=st)
+        qdd.load_gauge(lat, torch.from_numpy(U).cuda())
+        d_eta = torch.from_numpy(eta).cuda()
+        d_phi = torch.empty_like(d_eta)
+        op = oracle.Op(DIMS, BC, U, KAPPA, CSW, store_clover=False)
+        grid = []
+        for sch, ds in (("ras", (0, 2)), ("sap", (0, 2)), ("as", (2, 4))):
+            for d in ds:
+                # AS: one cycle only; with overlap its Richardson iteration
+                # amplifies the residual, so further cycles only hurt
+                for cyc in ((1,) if sch == "as" else (1, 2, 3)):
+                    p = qdd.default_params(inner_prec="f16", block=(4, 4, 4, 4), overlap=d // 2, n_ras=cyc,
+                                           n_dominv=4, schwarz=sch, max_inner=400, max_outer=12)
+                    qdd.solve(lat, d_phi, d_eta, KAPPA, CSW, TOL, p, raise_on_failure=False)  # untimed
+                    ms, infos = time_steps(torch, st, lambda: qdd.solve(lat, d_phi, d_eta, KAPPA, CSW, TOL, p,
+                                                                        raise_on_failure=False), 1)
+                    i = infos[0]
+                    res = op.true_residual(eta, d_phi.cpu().numpy())
+                    ok = i["status"] == 0 and res <= TOL
+                    grid.append({"schwarz": sch, "d": d, "cycles": cyc, "ms": round(ms, 2) if ok else None,
+                                 "inner_iters": i["inner_iters"], "outer_iters": i["outer_iters"],
+                                 "dv_count": i["dv_count"], "domain_solves_per_site": i["ras_sweeps"]
+                                 // (2 if sch == "sap" else 1), "oracle_true_rel_residual": res})
+        done = [g for g in grid if g["ms"] is not None]
+        best = {sch: min((g for g in done if g["schwarz"] == sch), key=lambda g: g["ms"], default=None)
+                for sch in ("ras", "sap", "as")}
+        rec = {"workload": "schwarz",
+               "metric": "32^4 solve time to 1e-10 with RAS, SAP (red/black multiplicative) or AS as K",
+               "unit": "ms", "ras": {"block": [4, 4, 4, 4], "n_dominv": 4, "inner_prec": "f16"},
+               "equal_cost": "a cycle solves every domain once in each variant (SAP: red then black); "
+                             "domain_solves_per_site counts them over the whole solve",
+               "best": best, "grid": grid}
     elif args.workload == "mrhs":
         dims, kappa, eps = (24, 24, 24, 48), 0.124, 0.25
         U = synth.gauge_field(dims, eps, 1)
@@ -781,9 +822,10 @@ def main():
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
                     help="use --block/--overlap/--n-dominv/--n-ras as given instead of tuning them")
     ap.add_argument("--tune-trials", dest="tune_trials", type=int, default=42)
-    ap.add_argument("--workload", choices=("solve", "mrhs", "batch", "survey", "table1"), default="solve",
+    ap.add_argument("--workload", choices=("solve", "mrhs", "batch", "survey", "table1", "schwarz"), default="solve",
                     help="solve: the 32^4 headline; mrhs / batch: the batched workloads; survey: the Sec. 5 "
-                         "parameter survey; table1: the paper's slab-domain experiment emulated")
+                         "parameter survey; table1: the paper's slab-domain experiment emulated; schwarz: RAS, "
+                         "SAP and AS compared as the preconditioner")
     ap.add_argument("--kernels", default=None,
                     help="profiler workload: dslash:f16|f32|f64, ras:f16|f32 or clover, three launches at 32^4")
     args = ap.parse_args()

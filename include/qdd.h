@@ -103,13 +103,32 @@ typedef struct {
                            loads), 1 compact per-thread staging (links and clover in the
                            field's storage format), 2 expanded (FP32 18-real links and FP32
                            clover, domains of at most 256 sites) */
+    int schwarz;        /* member of the Schwarz family used as K (Sec. 1, Sec. 2), a
+                           qdd_schwarz: QDD_SCHWARZ_RAS (default, Alg. 1), QDD_SCHWARZ_SAP or
+                           QDD_SCHWARZ_AS; n_ras counts cycles for each */
 } qdd_solver_params;
+
+/* The Schwarz iteration run by K.  Every variant starts from phi = 0, r = eta
+ * and ends each sweep with phi += v, r -= D v (Alg. 1 line 9); they differ in
+ * which domains a sweep solves and where their solutions go:
+ *   RAS  one sweep per cycle over every domain, solution restricted to the
+ *        bulk block (R_i), Alg. 1;
+ *   SAP  the multiplicative Schwarz alternating procedure: two sweeps per
+ *        cycle, first the domains whose block coordinates have an even sum
+ *        (red), then the odd ones (black), each restricted to its bulk block,
+ *        with the residual updated in between;
+ *   AS   plain additive Schwarz: one sweep per cycle over every domain, the
+ *        solution prolonged onto the whole extended domain and the
+ *        overlapping copies summed (identical to RAS when overlap = 0; with
+ *        overlap the sum is formed with FP32 atomic additions, so its
+ *        rounding depends on their order). */
+typedef enum { QDD_SCHWARZ_RAS = 0, QDD_SCHWARZ_SAP = 1, QDD_SCHWARZ_AS = 2 } qdd_schwarz;
 
 typedef struct {
     int outer_iters;            /* defect-correction steps */
     int inner_iters;            /* inner BiCGStab iterations, summed */
     int dv_count;               /* global D applications (the paper's "Dv count", Table 1) */
-    int ras_sweeps;             /* RAS block-solve sweeps */
+    int ras_sweeps;             /* block-solve sweeps of K (SAP: two per cycle, one per colour) */
     int status;                 /* qdd_status of the solve */
     double true_rel_residual;   /* |eta - D phi| / |eta| with the FP64 D */
     double t_total_ms;          /* wall time of the call */
@@ -163,8 +182,9 @@ qdd_status qdd_dslash(qdd_lattice *lat, double *out, const double *in, double ka
 /* out = K_RAS in (Alg. 1): NRAS sweeps of projection onto every extended
  * domain Omega'_i, n_dominv MR iterations of the Dirichlet-restricted D on
  * it, restriction to the bulk block and summation, then phi += v,
- * r -= D v.  Uses params->block, overlap, n_dominv, n_ras and inner_prec
- * (QDD_F32 or QDD_F16).  in/out canonical FP64 spinors, host or device.
+ * r -= D v.  Uses params->block, overlap, n_dominv, n_ras, inner_prec
+ * (QDD_F32 or QDD_F16) and schwarz (SAP and AS in place of RAS, see
+ * qdd_schwarz).  in/out canonical FP64 spinors, host or device.
  * Errors: QDD_ERR_ARG if a block does not divide the lattice or
  * block + 2*overlap exceeds it; QDD_ERR_TIMEOUT if a sweep gave up waiting
  * for its staged data (out is then undefined). */
@@ -228,9 +248,11 @@ qdd_status qdd_dslash_field(qdd_lattice *lat, qdd_field *out, const qdd_field *i
  * cannot let the library call cudaMalloc when the preconditioner runs --
  * code inside a CUDA stream capture, programs that own all device memory
  * through their own pool, and loops where an allocation would stall the GPU.
- * out = K_RAS in with params->block, overlap, n_dominv, n_ras; out, in, rho
- * and v are four different fields of this lattice in one precision (QDD_F32
- * or QDD_F16); rho and v are work vectors whose contents are overwritten.
+ * out = K_RAS in with params->block, overlap, n_dominv, n_ras and schwarz
+ * (RAS or SAP; AS with overlap > 0 needs a summation buffer and is rejected
+ * with QDD_ERR_ARG); out, in, rho and v are four different fields of this
+ * lattice in one precision (QDD_F32 or QDD_F16); rho and v are work vectors
+ * whose contents are overwritten.
  * Every sweep runs the general domain kernel, whose scratch is a fixed
  * 16 MiB device array inside the library (present on every GPU that loads
  * it, until the process exits): an extended domain may have at most 58254

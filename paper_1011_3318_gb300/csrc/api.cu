@@ -182,6 +182,7 @@ void qdd_default_params(qdd_solver_params *p)
     p->outer_mode = 0;
     p->autotune = 0;
     p->ras_kernel = 0;
+    p->schwarz = QDD_SCHWARZ_RAS;
 }
 
 qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc[4], int n_rhs, void *cuda_stream)
@@ -263,7 +264,7 @@ qdd_status qdd_destroy_lattice(qdd_lattice *lat)
     cudaStreamSynchronize(lat->stream);
     void *ptrs[] = {lat->U64, lat->Udf, lat->U32, lat->U16, lat->A64, lat->A32, lat->A16, lat->A16n, lat->rs.partials,
                     lat->rs.counter, lat->sc, lat->maxdev, lat->ras_err, lat->stage_a, lat->stage_b,
-                    lat->ras_scratch, lat->gauge_stage};
+                    lat->ras_scratch, lat->gauge_stage, lat->as_sum};
     for (void *p : ptrs) cudaFree(p);
     if (lat->sc_host) cudaFreeHost(lat->sc_host);
     if (lat->copy_stream) {
@@ -389,8 +390,8 @@ qdd_status qdd_ras_apply(qdd_lattice *lat, double *out, const double *in, double
         set_error("qdd_ras_apply needs inner_prec QDD_F32 or QDD_F16");
         return QDD_ERR_ARG;
     }
-    if (params->n_ras < 1 || params->n_dominv < 0) {
-        set_error("n_ras must be >= 1 and n_dominv >= 0");
+    if (params->n_ras < 1 || params->n_dominv < 0 || !valid_schwarz(params->schwarz)) {
+        set_error("n_ras must be >= 1, n_dominv >= 0 and schwarz a qdd_schwarz");
         return QDD_ERR_ARG;
     }
     DomainGeom dg;
@@ -445,7 +446,7 @@ qdd_status qdd_solve(qdd_lattice *lat, double *phi, const double *eta, double ka
     if (params) p = *params;
     else qdd_default_params(&p);
     if (!valid_prec(p.inner_prec) || p.max_inner < 1 || p.max_outer < 1 || p.n_ras < 1 || p.n_dominv < 0 ||
-        (p.inner_prec != QDD_F64 && !(p.inner_tol > 0 && p.inner_tol < 1))) {
+        !valid_schwarz(p.schwarz) || (p.inner_prec != QDD_F64 && !(p.inner_tol > 0 && p.inner_tol < 1))) {
         set_error("invalid solver parameters");
         return QDD_ERR_ARG;
     }
@@ -494,7 +495,7 @@ qdd_status qdd_solve_batch(qdd_lattice *const *lats, double *const *phi, const d
     if (params) p = *params;
     else qdd_default_params(&p);
     if (!valid_prec(p.inner_prec) || p.max_inner < 1 || p.max_outer < 1 || p.n_ras < 1 || p.n_dominv < 0 ||
-        (p.inner_prec != QDD_F64 && !(p.inner_tol > 0 && p.inner_tol < 1))) {
+        !valid_schwarz(p.schwarz) || (p.inner_prec != QDD_F64 && !(p.inner_tol > 0 && p.inner_tol < 1))) {
         set_error("invalid solver parameters");
         return QDD_ERR_ARG;
     }

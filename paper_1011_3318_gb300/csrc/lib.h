@@ -143,6 +143,15 @@ struct RasArgs {
     int fuse;
     SpinorView fr, fz;
     unsigned *err;  // may be null: set to 1 when a bounded wait for staged data gives up
+    // Schwarz variants (qdd_schwarz).  color = 0: every domain; color = 1 + c:
+    // only the domains whose block coordinates sum to parity c are solved,
+    // the others write zero to vout and (accumulate = 0) acc on their bulk
+    // sites.  asum non-null
+    // (additive Schwarz with overlap): instead of writing outputs, every
+    // domain adds its solution on all its extended sites to asum, FP32
+    // float4[nrhs][6][V], and launch_as_finish writes vout and acc from it.
+    int color;
+    float4 *asum;
 };
 
 enum { RAS_FUSE_NONE = 0, RAS_FUSE_P = 1, RAS_FUSE_S = 2 };
@@ -151,6 +160,17 @@ enum { RAS_FUSE_NONE = 0, RAS_FUSE_P = 1, RAS_FUSE_S = 2 };
 constexpr int RAS_SMEM_MAX_SITES = 512;
 
 cudaError_t launch_ras_block(int prec, const RasArgs &a, cudaStream_t st);
+// vout = asum, acc = asum or acc += asum (the additive-Schwarz sum of a sweep)
+cudaError_t launch_as_finish(int prec, const RasArgs &a, cudaStream_t st);
+// Which sweeps K runs: the effective variant (AS without overlap is RAS),
+// sweeps per cycle, and whether the additive sum needs asum.
+struct SchwarzPlan {
+    int variant;  // qdd_schwarz
+    int colors;   // 2 for SAP, else 1
+    bool sum;     // additive Schwarz over overlapping domains
+};
+SchwarzPlan schwarz_plan(int schwarz, const DomainGeom &dg);
+inline bool valid_schwarz(int s) { return s == QDD_SCHWARZ_RAS || s == QDD_SCHWARZ_SAP || s == QDD_SCHWARZ_AS; }
 // The general (global-scratch) sweep kernel for any domain size, with the
 // scratch and slot count given in a (FP32 and FP16 only).
 cudaError_t launch_ras_block_gmem(int prec, const RasArgs &a, cudaStream_t st);
@@ -199,9 +219,10 @@ struct qdd_lattice {
     // host-to-device copies that overlap the lattice stream's work
     cudaStream_t copy_stream;
     cudaEvent_t copy_ev[2];
-    // RAS scratch
+    // RAS scratch, and the additive-Schwarz sum (FP32 float4[nrhs][6][V])
     float2 *ras_scratch;
     size_t ras_scratch_bytes;
+    float4 *as_sum;
     // in/out fields of the canonical-layout entry points, per precision
     void *io_d[3][2];
     float *io_n[3][2];
@@ -238,8 +259,8 @@ qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params 
 // Whether the first sweep of ras_apply_fields can form the BiCGStab update
 // `fuse` while staging (shared-memory kernel; the in-place p update also
 // needs domains without overlap, whose halo would read p after another
-// domain has written it).
-bool ras_can_fuse(int prec, const DomainGeom &dg, int fuse);
+// domain has written it; RAS only: a SAP sweep skips half of the domains).
+bool ras_can_fuse(int prec, const DomainGeom &dg, int fuse, int schwarz = QDD_SCHWARZ_RAS);
 qdd_status solve_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, double kappa, double csw, double tol,
                       const qdd_solver_params *p, qdd_solve_info *info);
 qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, const double *const *eta_dev, int n,

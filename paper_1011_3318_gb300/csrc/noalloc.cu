@@ -88,14 +88,19 @@ extern "C" qdd_status qdd_ras_field_noalloc(qdd_lattice *lat, qdd_field *out, co
         set_error("the no-allocation K_RAS needs QDD_F32 or QDD_F16 fields");
         return QDD_ERR_ARG;
     }
-    if (params->n_ras < 1 || params->n_dominv < 0) {
-        set_error("n_ras must be >= 1 and n_dominv >= 0");
+    if (params->n_ras < 1 || params->n_dominv < 0 || !valid_schwarz(params->schwarz)) {
+        set_error("n_ras must be >= 1, n_dominv >= 0 and schwarz a qdd_schwarz");
         return QDD_ERR_ARG;
     }
     DomainGeom dg;
     std::string why;
     if (!domain_geom(lat->g, params->block, params->overlap, &dg, &why)) {
         set_error("invalid RAS blocking: " + why);
+        return QDD_ERR_ARG;
+    }
+    const SchwarzPlan sp = schwarz_plan(params->schwarz, dg);
+    if (sp.sum) {
+        set_error("additive Schwarz with overlap needs a summation buffer: use qdd_ras_apply");
         return QDD_ERR_ARG;
     }
     const size_t per_slot = (size_t)36 * (size_t)dg.nloc * sizeof(float2);
@@ -136,12 +141,14 @@ extern "C" qdd_status qdd_ras_field_noalloc(qdd_lattice *lat, qdd_field *out, co
     da.sc = lat->sc;
     da.nrhs = lat->nrhs;
 
-    for (int j = 0; j < params->n_ras; j++) {
-        const bool last = j == params->n_ras - 1;
+    const int nsweep = params->n_ras * sp.colors;
+    for (int j = 0; j < nsweep; j++) {
+        const bool last = j == nsweep - 1;
         ra.in = j == 0 ? in->view() : rho->view();
         ra.vout = last ? SpinorView{nullptr, nullptr} : v->view();
         ra.acc = out->view();
         ra.accumulate = j > 0;
+        ra.color = sp.colors == 2 ? 1 + j % 2 : 0;
         cudaError_t e = launch_ras_block_gmem(prec, ra, lat->stream);
         if (e != cudaSuccess) return cuda_fail(e, "RAS block kernel");
         if (!last) {

@@ -25,6 +25,13 @@
 //  * ras_gmem_kernel: any domain size.  A persistent grid of `slots` CTAs
 //    loops over the domains; rho, q and v of the current domain live in a
 //    per-CTA slot of global scratch (L2-resident for moderate domains).
+//
+// The same kernels run the other members of the Schwarz family: a sweep of
+// the multiplicative SAP solves only the domains of one colour of the
+// red/black block ordering (the others write zero), and a sweep of plain
+// additive Schwarz adds each domain's solution on all its extended sites into
+// an FP32 sum (atomic additions: the extended domains overlap), which
+// as_finish_kernel then writes out.
 #include <atomic>
 #include <cstring>
 
@@ -156,20 +163,67 @@ __device__ __forceinline__ void dom_apply(const RasArgs &a, const DomSite &ds, c
 }
 
 template <int P>
-__device__ __forceinline__ void write_outputs(const RasArgs &a, long long x, const C<float> (&v)[12])
+__device__ __forceinline__ void write_outputs_to(SpinorView vout, SpinorView acc, int accumulate, long long V,
+                                                 long long x, const C<float> (&v)[12])
 {
     typedef typename RealOf<P>::T T;
-    const long long V = a.g.V;
-    if (a.vout.d) store_spinor<P>(a.vout, V, x, v);
-    if (a.accumulate) {
+    if (vout.d) store_spinor<P>(vout, V, x, v);
+    if (accumulate) {
         C<T> o[12];
-        load_spinor<P>(a.acc, V, x, o);
+        load_spinor<P>(acc, V, x, o);
 #pragma unroll
         for (int k = 0; k < 12; k++) o[k] = cadd(o[k], C<T>{(T)v[k].r, (T)v[k].i});
-        store_spinor<P>(a.acc, V, x, o);
+        store_spinor<P>(acc, V, x, o);
     } else {
-        store_spinor<P>(a.acc, V, x, v);
+        store_spinor<P>(acc, V, x, v);
     }
+}
+
+template <int P>
+__device__ __forceinline__ void write_outputs(const RasArgs &a, long long x, const C<float> (&v)[12])
+{
+    write_outputs_to<P>(a.vout, a.acc, a.accumulate, a.g.V, x, v);
+}
+
+// Bulk site of a domain that this SAP sweep does not solve: v = 0 there.
+template <int P>
+__device__ __forceinline__ void zero_outputs(const RasArgs &a, long long x)
+{
+    C<float> z[12];
+#pragma unroll
+    for (int k = 0; k < 12; k++) z[k] = {0.f, 0.f};
+    if (a.vout.d) store_spinor<P>(a.vout, a.g.V, x, z);
+    if (!a.accumulate) store_spinor<P>(a.acc, a.g.V, x, z);
+}
+
+// Additive Schwarz: the domain's solution at one of its extended sites,
+// added to the sum of all domains covering that site (asum already offset to
+// this right-hand side; complex pair k of the site in float4 plane k).
+__device__ __forceinline__ void as_add(const RasArgs &a, long long x, const C<float> (&v)[12])
+{
+#pragma unroll
+    for (int k = 0; k < 6; k++)
+        atomicAdd(&a.asum[(long long)k * a.g.V + x],
+                  make_float4(v[2 * k].r, v[2 * k].i, v[2 * k + 1].r, v[2 * k + 1].i));
+}
+
+// Colour of a domain in the red/black block ordering: parity of the sum of
+// its block coordinates.
+__device__ __forceinline__ int dom_color(const DomainGeom &dg, int dom)
+{
+    int sum = 0, r = dom;
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        const int q = fast_div(r, dg.nb[mu], dg.nb_m[mu], dg.nb_sh[mu]);
+        sum += r - q * dg.nb[mu];
+        r = q;
+    }
+    return sum & 1;
+}
+
+__device__ __forceinline__ bool skip_domain(const RasArgs &a, int dom)
+{
+    return a.color != 0 && dom_color(a.dg, dom) != a.color - 1;
 }
 
 // The sweep's input at site x: `in`, or with a fused BiCGStab update
@@ -414,7 +468,13 @@ __device__ __forceinline__ void ras_mr_domain(const RasArgs &a, const LocSite &s
             st_local(srho, NT, l, own);
         }
     }
-    if (s.m & M_BULK) {  // restriction R_{Omega}
+    if (a.asum) {  // additive Schwarz: no restriction, overlaps summed
+        if (act) {
+            C<float> vv[12];
+            ld_local(sv, NT, l, vv);
+            as_add(a, s.x, vv);
+        }
+    } else if (s.m & M_BULK) {  // restriction R_{Omega}
         C<float> vv[12];
         ld_local(sv, NT, l, vv);
         write_outputs<P>(a, s.x, vv);
@@ -431,6 +491,7 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(RasArgs
     a.acc = rhs_view<P>(a.acc, a.g.V, rr);
     a.fr = rhs_view<P>(a.fr, a.g.V, rr);
     a.fz = rhs_view<P>(a.fz, a.g.V, rr);
+    if (a.asum) a.asum += (long long)rr * 6 * a.g.V;
     C<float> fb, fc;
     fuse_coefs(a, rr, fb, fc);
     extern __shared__ __align__(16) unsigned char smem[];
@@ -447,6 +508,10 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(RasArgs
     LocSite s;
     loc_site(a.g, a.dg, dom, l, s);
     const bool act = s.m & M_ACT;
+    if (skip_domain(a, dom)) {  // uniform over the CTA, before any barrier
+        if (s.m & M_BULK) zero_outputs<P>(a, s.x);
+        return;
+    }
 
     // stage the projection P_{Omega'} r, and the domain's links and clover
     {
@@ -535,6 +600,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) ras_tma_kernel(RasArgs a, const 
     a.in = rhs_view<P>(a.in, a.g.V, rr);
     a.vout = rhs_view<P>(a.vout, a.g.V, rr);
     a.acc = rhs_view<P>(a.acc, a.g.V, rr);
+    if (a.asum) a.asum += (long long)rr * 6 * a.g.V;
     C<float> fb, fc;
     fuse_coefs(a, rr, fb, fc);
     extern __shared__ __align__(128) unsigned char smem_dyn[];
@@ -555,6 +621,10 @@ __global__ void __launch_bounds__(NT, 512 / NT) ras_tma_kernel(RasArgs a, const 
     const int l = threadIdx.x;
     LocSite s;
     loc_site(a.g, a.dg, dom, l, s);
+    if (skip_domain(a, dom)) {  // uniform over the CTA, before the barrier exists
+        if (s.m & M_BULK) zero_outputs<P>(a, s.x);
+        return;
+    }
 
     if (l == 0) mbar_init(&bar, 1);
     __syncthreads();
@@ -638,6 +708,15 @@ __global__ void __launch_bounds__(RAS_GMEM_NT) ras_gmem_kernel(const RasArgs a0)
         a.in = rhs_view<P>(a0.in, a0.g.V, rr);
         a.vout = rhs_view<P>(a0.vout, a0.g.V, rr);
         a.acc = rhs_view<P>(a0.acc, a0.g.V, rr);
+        if (a.asum) a.asum += (long long)rr * 6 * a.g.V;
+        if (skip_domain(a, dom)) {  // uniform over the CTA
+            for (int l = threadIdx.x; l < n; l += RAS_GMEM_NT) {
+                DomSite ds;
+                dom_site(a.g, a.dg, dom, l, a.kappa, ds);
+                if (ds.bulk) zero_outputs<P>(a, ds.x);
+            }
+            continue;
+        }
         for (int l = threadIdx.x; l < n; l += RAS_GMEM_NT) {
             DomSite ds;
             dom_site(a.g, a.dg, dom, l, a.kappa, ds);
@@ -688,7 +767,11 @@ __global__ void __launch_bounds__(RAS_GMEM_NT) ras_gmem_kernel(const RasArgs a0)
         for (int l = threadIdx.x; l < n; l += RAS_GMEM_NT) {
             DomSite ds;
             dom_site(a.g, a.dg, dom, l, a.kappa, ds);
-            if (ds.bulk) {
+            if (a.asum) {
+                C<float> v[12];
+                ld_local(vv, n, l, v);
+                as_add(a, ds.x, v);
+            } else if (ds.bulk) {
                 C<float> v[12];
                 ld_local(vv, n, l, v);
                 write_outputs<P>(a, ds.x, v);
@@ -838,12 +921,48 @@ static cudaError_t launch_tma(const RasArgs &a, const RasTma &tm, cudaStream_t s
     return cudaGetLastError();
 }
 
+// vout = asum, acc = asum (or acc += asum) on every site: the additive
+// Schwarz sum of one sweep, in the fields' precision.  grid.y = right-hand side.
+template <int P>
+__global__ void __launch_bounds__(256) as_finish_kernel(const RasArgs a)
+{
+    const int rr = blockIdx.y;
+    if (a.sc && a.sc[rr].status != S_RUN) return;
+    const long long V = a.g.V;
+    const long long x = (long long)blockIdx.x * 256 + threadIdx.x;
+    if (x >= V) return;
+    const float4 *sum = a.asum + (long long)rr * 6 * V;
+    C<float> v[12];
+#pragma unroll
+    for (int k = 0; k < 6; k++) {
+        const float4 f = sum[(long long)k * V + x];
+        v[2 * k] = {f.x, f.y};
+        v[2 * k + 1] = {f.z, f.w};
+    }
+    write_outputs_to<P>(rhs_view<P>(a.vout, V, rr), rhs_view<P>(a.acc, V, rr), a.accumulate, V, x, v);
+}
+
+cudaError_t launch_as_finish(int prec, const RasArgs &a, cudaStream_t st)
+{
+    if (!a.asum || a.nrhs < 1 || a.nrhs > 65535) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((a.g.V + 255) / 256), (unsigned)a.nrhs);
+    switch (prec) {
+    case P32: as_finish_kernel<P32><<<grid, 256, 0, st>>>(a); break;
+    case P16: as_finish_kernel<P16><<<grid, 256, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <int P>
 static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
 {
     const int n = a.dg.nloc;
     if constexpr (P == P16 || P == P32) {
-        if (n == 256 || n == 128) {
+        // (the TMA kernel serves blocks without overlap, where the additive
+        // sum is never used)
+        if ((n == 256 || n == 128) && !a.asum) {
             RasTma tm;
             if (tma_maps<P>(a, n, &tm)) return n == 256 ? launch_tma<P, 256>(a, tm, st) : launch_tma<P, 128>(a, tm, st);
         }

@@ -155,24 +155,52 @@ static qdd_status ensure_ras_scratch(qdd_lattice *lat, const DomainGeom &dg)
     return QDD_OK;
 }
 
-// out = K_RAS in (Alg. 1): sweep j projects, solves and restricts on every
-// domain (one launch), accumulates phi += v, and updates rho = rho - D v
-// except after the last sweep, where phi no longer depends on rho.
-bool ras_can_fuse(int prec, const DomainGeom &dg, int fuse)
+SchwarzPlan schwarz_plan(int schwarz, const DomainGeom &dg)
+{
+    bool overlap = false;
+    for (int mu = 0; mu < 4; mu++) overlap |= dg.e[mu] != dg.b[mu];
+    SchwarzPlan sp;
+    sp.variant = schwarz == QDD_SCHWARZ_AS && !overlap ? QDD_SCHWARZ_RAS : schwarz;
+    sp.colors = sp.variant == QDD_SCHWARZ_SAP ? 2 : 1;
+    sp.sum = sp.variant == QDD_SCHWARZ_AS;
+    return sp;
+}
+
+bool ras_can_fuse(int prec, const DomainGeom &dg, int fuse, int schwarz)
 {
     if (prec == P64 || dg.nloc > RAS_SMEM_MAX_SITES) return false;
+    if (schwarz_plan(schwarz, dg).variant != QDD_SCHWARZ_RAS) return false;
     if (fuse == RAS_FUSE_P)
         for (int mu = 0; mu < 4; mu++)
             if (dg.e[mu] != dg.b[mu]) return false;
     return true;
 }
 
+static qdd_status ensure_as_sum(qdd_lattice *lat)
+{
+    if (lat->as_sum) return QDD_OK;
+    cudaError_t e = cudaMalloc(&lat->as_sum, (size_t)lat->nrhs * 6 * (size_t)lat->g.V * sizeof(float4));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        lat->as_sum = nullptr;
+        set_error("cudaMalloc of the additive-Schwarz sum failed");
+        return QDD_ERR_NOMEM;
+    }
+    return QDD_OK;
+}
+
+// out = K in for the Schwarz variant of p (Alg. 1 for RAS): sweep q projects,
+// solves and restricts on its domains (one launch; SAP alternates the two
+// colours), accumulates phi += v, and updates rho = rho - D v except after
+// the last sweep, where phi no longer depends on rho.
 qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params *p, const DomainGeom &dg,
                             SpinorView out, SpinorView in, SpinorView rho, SpinorView v, double kappa, int *dv,
                             const Scalars *sc, int fuse, SpinorView fr, SpinorView fz)
 {
     qdd_status st = ensure_ras_scratch(lat, dg);
     if (st != QDD_OK) return st;
+    const SchwarzPlan sp = schwarz_plan(p->schwarz, dg);
+    if (sp.sum && (st = ensure_as_sum(lat)) != QDD_OK) return st;
     RasArgs ra;
     memset(&ra, 0, sizeof(ra));
     ra.g = lat->g;
@@ -187,20 +215,28 @@ qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params 
     ra.nrhs = lat->nrhs;
     ra.variant = p->ras_kernel;
     ra.err = lat->ras_err;
-    for (int j = 0; j < p->n_ras; j++) {
-        const bool last = j == p->n_ras - 1;
-        ra.in = j == 0 ? in : rho;
+    ra.asum = sp.sum ? lat->as_sum : nullptr;
+    const int nsweep = p->n_ras * sp.colors;
+    for (int q = 0; q < nsweep; q++) {
+        const bool last = q == nsweep - 1;
+        ra.in = q == 0 ? in : rho;
         ra.vout = last ? SpinorView{nullptr, nullptr} : v;
         ra.acc = out;
-        ra.accumulate = j > 0;
+        ra.accumulate = q > 0;
+        ra.color = sp.colors == 2 ? 1 + q % 2 : 0;
         // the first sweep may form its input (written to `in`) from fr, in, fz
-        ra.fuse = j == 0 ? fuse : RAS_FUSE_NONE;
+        ra.fuse = q == 0 ? fuse : RAS_FUSE_NONE;
         ra.fr = fr;
         ra.fz = fz;
         cudaError_t e;
         {
             ProfScope ps(lat, QDD_K_RAS);
-            e = launch_ras_block(prec, ra, lat->stream);
+            e = cudaSuccess;
+            if (sp.sum)
+                e = cudaMemsetAsync(ra.asum, 0, (size_t)lat->nrhs * 6 * (size_t)lat->g.V * sizeof(float4),
+                                    lat->stream);
+            if (e == cudaSuccess) e = launch_ras_block(prec, ra, lat->stream);
+            if (e == cudaSuccess && sp.sum) e = launch_as_finish(prec, ra, lat->stream);
         }
         if (e != cudaSuccess) return cuda_fail(e, "RAS block kernel");
         if (!last) {
@@ -240,8 +276,8 @@ qdd_status enqueue_iteration(Member &m, int prec, const qdd_solver_params *p)
     // with RAS, the updates p = r + beta (p - omega v) and s = r - alpha v are
     // formed by the sweeps that precondition them, while they stage their
     // input, instead of by separate passes over memory
-    const bool fuse_p = m.use_ras && ras_can_fuse(prec, m.dg, RAS_FUSE_P);
-    const bool fuse_s = m.use_ras && ras_can_fuse(prec, m.dg, RAS_FUSE_S);
+    const bool fuse_p = m.use_ras && ras_can_fuse(prec, m.dg, RAS_FUSE_P, p->schwarz);
+    const bool fuse_s = m.use_ras && ras_can_fuse(prec, m.dg, RAS_FUSE_S, p->schwarz);
     qdd_status st;
     if (!fuse_p && (st = blas(lat, prec, B_P, {F(W_P), F(W_R), F(W_V)})) != QDD_OK) return st;
     if (m.use_ras && (st = ras_apply_fields(lat, prec, p, m.dg, phat, F(W_P), F(W_RHO), F(W_VR), m.kappa, nullptr,
@@ -537,8 +573,9 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                 const Scalars &h = lat->sc_host[r];
                 if (m.info) {
                     m.info[r].inner_iters += h.iter;
-                    m.info[r].dv_count += 2 * h.iter + (m.use_ras ? 2 * h.iter * (p->n_ras - 1) : 0);
-                    m.info[r].ras_sweeps += m.use_ras ? 2 * h.iter * p->n_ras : 0;
+                    const int nsweep = p->n_ras * schwarz_plan(p->schwarz, m.dg).colors;
+                    m.info[r].dv_count += 2 * h.iter + (m.use_ras ? 2 * h.iter * (nsweep - 1) : 0);
+                    m.info[r].ras_sweeps += m.use_ras ? 2 * h.iter * nsweep : 0;
                     m.info[r].outer_iters++;
                 }
                 if (h.status == S_NONFINITE) {

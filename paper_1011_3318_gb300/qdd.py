@@ -36,6 +36,9 @@ STATUS_NAMES = {0: "QDD_OK", 1: "QDD_ERR_ARG", 2: "QDD_ERR_CUDA", 3: "QDD_ERR_NO
 
 QDD_F64, QDD_F32, QDD_F16 = 0, 1, 2
 PREC = {"f64": QDD_F64, "f32": QDD_F32, "f16": QDD_F16, QDD_F64: QDD_F64, QDD_F32: QDD_F32, QDD_F16: QDD_F16}
+# qdd_schwarz: the member of the Schwarz family used as the preconditioner
+QDD_SCHWARZ_RAS, QDD_SCHWARZ_SAP, QDD_SCHWARZ_AS = 0, 1, 2
+SCHWARZ = {"ras": QDD_SCHWARZ_RAS, "sap": QDD_SCHWARZ_SAP, "as": QDD_SCHWARZ_AS}
 
 # Every function the header declares (checked by the tests against the library's exports).
 ABI = ("qdd_version", "qdd_last_error", "qdd_default_params", "qdd_create_lattice", "qdd_destroy_lattice",
@@ -58,7 +61,8 @@ class SolverParams(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int * 4), ("overlap", ctypes.c_int), ("n_dominv", ctypes.c_int),
                 ("n_ras", ctypes.c_int), ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("max_inner", ctypes.c_int), ("max_outer", ctypes.c_int), ("use_ras", ctypes.c_int),
-                ("outer_mode", ctypes.c_int), ("autotune", ctypes.c_int), ("ras_kernel", ctypes.c_int)]
+                ("outer_mode", ctypes.c_int), ("autotune", ctypes.c_int), ("ras_kernel", ctypes.c_int),
+                ("schwarz", ctypes.c_int)]
 
 
 class Profile(ctypes.Structure):
@@ -186,6 +190,8 @@ def default_params(**overrides) -> SolverParams:
             p.block = (ctypes.c_int * 4)(*[int(b) for b in v])
         elif k == "inner_prec":
             p.inner_prec = PREC[v]
+        elif k == "schwarz" and isinstance(v, str):
+            p.schwarz = SCHWARZ[v]
         else:
             setattr(p, k, v)
     return p
