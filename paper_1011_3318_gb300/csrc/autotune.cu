@@ -52,7 +52,8 @@ qdd_status autotune_impl(qdd_lattice *lat, double *phi_dev, const double *eta_de
             if (same_ras(t.p, q)) return;
         DomainGeom dg;
         if (!domain_geom(lat->g, q.block, q.overlap, &dg, nullptr)) return;
-        if (dg.nloc > RAS_SMEM_MAX_SITES) return;  // the general kernel is never the fastest
+        // the general kernel is never the fastest
+        if (dg.nloc > RAS_SMEM_MAX_SITES && !ras_cluster_shape(dg)) return;
         std::vector<qdd_solve_info> info(lat->nrhs);
         const auto t0 = clk::now();
         qdd_status s = solve_impl(lat, phi_dev, eta_dev, kappa, csw, tol, &q, info.data());

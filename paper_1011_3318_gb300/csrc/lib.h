@@ -158,6 +158,9 @@ enum { RAS_FUSE_NONE = 0, RAS_FUSE_P = 1, RAS_FUSE_S = 2 };
 
 // Sites of an extended domain up to which the shared-memory kernel is used.
 constexpr int RAS_SMEM_MAX_SITES = 512;
+// Whether larger extended domains fit the cluster kernel (one CTA per
+// t-slice of at most 512 sites, at most 8 slices).
+bool ras_cluster_shape(const DomainGeom &dg);
 
 cudaError_t launch_ras_block(int prec, const RasArgs &a, cudaStream_t st);
 // vout = asum, acc = asum or acc += asum (the additive-Schwarz sum of a sweep)

@@ -690,6 +690,314 @@ __global__ void __launch_bounds__(NT, 512 / NT) ras_tma_kernel(RasArgs a, const 
     ras_mr_domain<P, NT, SC, false>(a, s, srho, sv, sA, lU, lA, wpart);
 }
 
+// ---------------------------------------------------------------- clusters
+// Extended domains too large for one CTA (overlap d > 0 on 4^4 blocks: 6^4 or
+// 8^4 sites) are solved by one thread-block cluster each: one CTA per t-slice
+// of the extended domain (cluster size e_t <= 8), one thread per site of the
+// slice (e_x e_y e_z <= 512 sites).  Every CTA keeps its slice's residual,
+// solution, links and (FP16) clover in shared memory as ras_smem_kernel does;
+// the hops in t read the neighbouring slice's residual, and backwards its
+// forward t link, from the neighbour CTA's shared memory (distributed shared
+// memory), and the MR dot products are summed over the cluster from one
+// partial per CTA.  Per MR iteration two cluster barriers order the accesses:
+// one before the hops (every slice's residual is updated) and one before the
+// partials are read (every hop has read the residual it needs, so it may be
+// updated in place).
+
+constexpr int RAS_CLUSTER_MAX_SLICE = 512;
+constexpr int RAS_CLUSTER_MAX_CTAS = 8;
+
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// All threads of all CTAs of the cluster; orders shared-memory accesses
+// across the cluster (release / acquire).  The split form lets a thread do
+// work that needs no other CTA between its arrival and its wait.
+__device__ __forceinline__ void cluster_arrive()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_wait()
+{
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    cluster_arrive();
+    cluster_wait();
+}
+
+// Shared-memory address of p (in this CTA) mapped to CTA `rank` of the cluster.
+__device__ __forceinline__ unsigned cluster_map(const void *p, unsigned rank)
+{
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr(p)), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ float4 ld_cluster_f4(unsigned addr)
+{
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ uint2 ld_cluster_u2(unsigned addr)
+{
+    uint2 v;
+    asm volatile("ld.shared::cluster.v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(addr));
+    return v;
+}
+
+// ld_local of site l from the residual of CTA `rank`.
+__device__ __forceinline__ void ld_remote(const float2 *base, int stride, int l, unsigned rank, C<float> (&s)[12])
+{
+    const unsigned b = cluster_map(base, rank) + (unsigned)l * 16u;
+#pragma unroll
+    for (int q = 0; q < 6; q++) {
+        const float4 v = ld_cluster_f4(b + (unsigned)(q * stride) * 16u);
+        s[2 * q] = {v.x, v.y};
+        s[2 * q + 1] = {v.z, v.w};
+    }
+}
+
+// The staged forward link in direction mu of site l of CTA `rank` (the
+// compact FP16 or FP32 format of the shared-memory kernel), row 2 rebuilt.
+template <int P>
+__device__ __forceinline__ void ld_remote_link(LinkView sU, int stride, int mu, int l, unsigned rank, C<float> (&U)[9])
+{
+    if constexpr (P == P32) {
+        const unsigned b = cluster_map(sU.d, rank) + (unsigned)(mu * 3 * stride + l) * 16u;
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const float4 a = ld_cluster_f4(b + (unsigned)(q * stride) * 16u);
+            U[2 * q] = {a.x, a.y};
+            U[2 * q + 1] = {a.z, a.w};
+        }
+    } else {
+        const unsigned b = cluster_map(sU.d, rank) + (unsigned)(mu * 3 * stride + l) * 8u;
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            const uint2 a = ld_cluster_u2(b + (unsigned)(q * stride) * 8u);
+            unsigned w[2] = {a.x, a.y};
+#pragma unroll
+            for (int j = 0; j < 2; j++) {
+                const float2 f2 = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
+                U[2 * q + j] = {f2.x, f2.y};
+            }
+        }
+    }
+    rebuild_row2(U);
+}
+
+// The two t hops of a site whose t neighbours live in the neighbouring CTAs
+// (forward: rank + 1, wrapping to 0 in a whole-lattice direction; backward:
+// rank - 1, wrapping to ncta - 1).
+template <int P>
+__device__ __forceinline__ void cluster_hops_t(const LocSite &s, int l, const float2 *srho, LinkView sU, float kappa,
+                                               C<float> (&q)[12], int NT, unsigned rank, unsigned ncta)
+{
+    if (s.m & (1u << 3)) {
+        const unsigned nr = (s.m & (1u << 19)) ? 0u : rank + 1;
+        C<float> n[12], U[9];
+        ld_remote(srho, NT, l, nr, n);
+        load_link<P>(sU, NT, 3, l, U);
+        hop<3, true>(q, n, U, (s.m & (1u << 11)) ? kappa : -kappa);
+    }
+    if (s.m & (1u << 7)) {
+        const unsigned nr = (s.m & (1u << 23)) ? ncta - 1 : rank - 1;
+        C<float> n[12], U[9];
+        ld_remote(srho, NT, l, nr, n);
+        ld_remote_link<P>(sU, NT, 3, l, nr, U);
+        hop<3, false>(q, n, U, (s.m & (1u << 15)) ? kappa : -kappa);
+    }
+}
+
+// One cluster (dg.e[3] CTAs of blockDim.x >= e_x e_y e_z threads) per
+// (domain, right-hand side); launched with the cluster dimension dg.e[3].
+template <int P>
+__global__ void __launch_bounds__(RAS_CLUSTER_MAX_SLICE, 1) ras_cluster_kernel(RasArgs a)
+{
+    constexpr bool SC = P == P16;
+    const int NT = blockDim.x;
+    const int S = a.dg.e[0] * a.dg.e[1] * a.dg.e[2];
+    const unsigned ncta = (unsigned)a.dg.e[3];
+    const unsigned rank = cluster_rank();
+    const int item = blockIdx.x / ncta;
+    const int rr = item % a.nrhs, dom = item / a.nrhs;
+    // every decision below that returns is uniform over the cluster
+    if (a.sc && a.sc[rr].status != S_RUN) return;
+    a.in = rhs_view<P>(a.in, a.g.V, rr);
+    a.vout = rhs_view<P>(a.vout, a.g.V, rr);
+    a.acc = rhs_view<P>(a.acc, a.g.V, rr);
+    a.fr = rhs_view<P>(a.fr, a.g.V, rr);
+    a.fz = rhs_view<P>(a.fz, a.g.V, rr);
+    if (a.asum) a.asum += (long long)rr * 6 * a.g.V;
+    C<float> fb, fc;
+    fuse_coefs(a, rr, fb, fc);
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ float wpart[3][RAS_CLUSTER_MAX_SLICE / 32];
+    __shared__ float4 cpart;
+    float2 *srho = reinterpret_cast<float2 *>(smem);
+    float2 *sv = srho + 12 * NT;
+    unsigned char *sU = reinterpret_cast<unsigned char *>(sv + 12 * NT);
+    unsigned char *sA = sU + (size_t)NT * RasSmem<P, false>::link_bytes;
+    float *sAn = reinterpret_cast<float *>(sA + (size_t)NT * RasSmem<P, false>::clover_data);
+    const LinkView lU{sU};
+    const CloverView lA = SC ? CloverView{sA, sAn} : a.A;
+    const long long V = a.g.V;
+    const int l = threadIdx.x;
+    LocSite s;
+    loc_site(a.g, a.dg, dom, l < S ? (int)rank * S + l : a.dg.nloc, s);
+    const bool act = s.m & M_ACT;
+    if (skip_domain(a, dom)) {
+        if (s.m & M_BULK) zero_outputs<P>(a, s.x);
+        return;
+    }
+
+    // stage this slice: P_{Omega'} r (or the fused update), links, clover
+    {
+        C<float> r[12], z[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) { r[k] = {0.f, 0.f}; z[k] = {0.f, 0.f}; }
+        if (act) {
+            staged_input<P>(a, V, s.x, fb, fc, r);
+            if (a.fuse != RAS_FUSE_NONE && (s.m & M_BULK)) store_spinor<P>(a.in, V, s.x, r);
+        }
+        st_local(srho, NT, l, r);
+        st_local(sv, NT, l, z);
+        if (act) {
+            if constexpr (P == P16) {
+                const uint2 *g = (const uint2 *)a.U.d;
+#pragma unroll
+                for (int k = 0; k < 12; k++) ((uint2 *)sU)[k * NT + l] = g[(long long)k * V + s.x];
+                const uint4 *ga = (const uint4 *)a.A.d;
+#pragma unroll
+                for (int k = 0; k < 9; k++) ((uint4 *)sA)[k * NT + l] = ga[(long long)k * V + s.x];
+                sAn[l] = a.A.n[s.x];
+            } else {
+                const float4 *g = (const float4 *)a.U.d;
+#pragma unroll
+                for (int k = 0; k < 12; k++) ((float4 *)sU)[k * NT + l] = g[(long long)k * V + s.x];
+            }
+        }
+    }
+
+    const int nw = NT / 32;
+    // The residual of this slice is staged (or, in the loop, updated): arrive
+    // on the cluster barrier, make it visible to this CTA, and apply the
+    // site-local and in-slice parts of D before waiting for the other slices.
+    cluster_arrive();
+    __syncthreads();
+    for (int it = 0; it < a.n_iter; it++) {
+        C<float> q[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) q[k] = {0.f, 0.f};
+        if (act) {
+            {
+                C<float> own[12];
+                float av[72];
+                ld_local(srho, NT, l, own);
+                const float na = load_clover_u<P>(lA, SC ? (long long)NT : V, SC ? l : s.x, av);
+                clover_apply(av, own, q);
+                if constexpr (P == P16) {
+#pragma unroll
+                    for (int k = 0; k < 12; k++) q[k] = cscale(q[k], na);
+                }
+            }
+            smem_hops<P, false, 0>(s, l, srho, lU, a.kappa, q, NT);
+            smem_hops<P, false, 1>(s, l, srho, lU, a.kappa, q, NT);
+            smem_hops<P, false, 2>(s, l, srho, lU, a.kappa, q, NT);
+        }
+        cluster_wait();  // every slice staged / updated
+        if (act) cluster_hops_t<P>(s, l, srho, lU, a.kappa, q, NT, rank, ncta);
+        // <q, rho> and |q|^2: warps, then the CTA (thread 0), then the cluster
+        float red[3];
+        {
+            C<float> own[12];
+            ld_local(srho, NT, l, own);
+            float qr = 0.f, qi = 0.f, qq = 0.f;
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                cdot_acc(q[k], own[k], qr, qi);
+                cnorm_acc(q[k], qq);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                qr += __shfl_xor_sync(0xffffffffu, qr, o);
+                qi += __shfl_xor_sync(0xffffffffu, qi, o);
+                qq += __shfl_xor_sync(0xffffffffu, qq, o);
+            }
+            if ((l & 31) == 0) {
+                wpart[0][l >> 5] = qr;
+                wpart[1][l >> 5] = qi;
+                wpart[2][l >> 5] = qq;
+            }
+            __syncthreads();
+            if (l == 0) {
+                float4 t = {0.f, 0.f, 0.f, 0.f};
+                for (int w = 0; w < nw; w++) {
+                    t.x += wpart[0][w];
+                    t.y += wpart[1][w];
+                    t.z += wpart[2][w];
+                }
+                cpart = t;
+            }
+            cluster_sync();  // every partial written; every hop has read its residual
+            const int lane = l & 31;
+            float4 t = {0.f, 0.f, 0.f, 0.f};
+            if (lane < (int)ncta) t = ld_cluster_f4(cluster_map(&cpart, (unsigned)lane));
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                t.x += __shfl_xor_sync(0xffffffffu, t.x, o);
+                t.y += __shfl_xor_sync(0xffffffffu, t.y, o);
+                t.z += __shfl_xor_sync(0xffffffffu, t.z, o);
+            }
+            // lane 0's sum, identical in every warp of every CTA
+            red[0] = __shfl_sync(0xffffffffu, t.x, 0);
+            red[1] = __shfl_sync(0xffffffffu, t.y, 0);
+            red[2] = __shfl_sync(0xffffffffu, t.z, 0);
+        }
+        if (red[2] > 0.f) {
+            const float inv = 1.0f / red[2];
+            const C<float> al = {red[0] * inv, red[1] * inv};
+            C<float> own[12], vv[12];
+            ld_local(srho, NT, l, own);
+            ld_local(sv, NT, l, vv);
+#pragma unroll
+            for (int k = 0; k < 12; k++) {
+                vv[k] = cfma(al, own[k], vv[k]);
+                own[k] = cfma(cneg(al), q[k], own[k]);
+            }
+            st_local(sv, NT, l, vv);
+            st_local(srho, NT, l, own);
+        }
+        cluster_arrive();
+        __syncthreads();
+    }
+    // no CTA leaves while another may still read its partial or residual
+    cluster_wait();
+    if (a.asum) {
+        if (act) {
+            C<float> vv[12];
+            ld_local(sv, NT, l, vv);
+            as_add(a, s.x, vv);
+        }
+    } else if (s.m & M_BULK) {
+        C<float> vv[12];
+        ld_local(sv, NT, l, vv);
+        write_outputs<P>(a, s.x, vv);
+    }
+}
+
 constexpr int RAS_GMEM_NT = 256;
 
 template <int P>
@@ -955,6 +1263,69 @@ cudaError_t launch_as_finish(int prec, const RasArgs &a, cudaStream_t st)
     return cudaGetLastError();
 }
 
+bool ras_cluster_shape(const DomainGeom &dg)
+{
+    const int slice = dg.e[0] * dg.e[1] * dg.e[2];
+    return dg.nloc > RAS_SMEM_MAX_SITES && dg.e[3] >= 2 && dg.e[3] <= RAS_CLUSTER_MAX_CTAS &&
+           slice <= RAS_CLUSTER_MAX_SLICE;
+}
+
+// Launches ras_cluster_kernel when the device can hold one of its clusters
+// (*launched = true); otherwise launches nothing and the caller falls back to
+// the general kernel.  The shared-memory opt-in and the residency query are
+// made once per device and cluster shape (before any capture: the first
+// launch of a solve is never captured).
+template <int P>
+static cudaError_t launch_cluster(const RasArgs &a, cudaStream_t st, bool *launched)
+{
+    *launched = false;
+    const int slice = a.dg.e[0] * a.dg.e[1] * a.dg.e[2];
+    const int ncta = a.dg.e[3];
+    const int nt = (slice + 31) / 32 * 32;
+    const size_t smem = RasSmem<P, false>::bytes(nt, P == P16);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    // per device: bit 0 opt-in done; per (cluster size, warps) a residency
+    // state 0 unknown, 1 resident, 2 not resident
+    static std::atomic<unsigned> optin[64];
+    static std::atomic<unsigned char> state[64][RAS_CLUSTER_MAX_CTAS + 1][RAS_CLUSTER_MAX_SLICE / 32 + 1];
+    if (dev < 0 || dev >= 64) return cudaSuccess;
+    if (!(optin[dev].load() & 1u)) {
+        cudaError_t e = cudaFuncSetAttribute(ras_cluster_kernel<P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)RasSmem<P, false>::bytes(RAS_CLUSTER_MAX_SLICE, P == P16));
+        if (e != cudaSuccess) return e;
+        optin[dev].fetch_or(1u);
+    }
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)((long long)ncta * a.dg.ndom * a.nrhs), 1, 1);
+    cfg.blockDim = dim3((unsigned)nt, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)ncta;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    std::atomic<unsigned char> &known = state[dev][ncta][nt / 32];
+    if (known.load() == 0) {
+        int clusters = 0;
+        cudaError_t e = cudaOccupancyMaxActiveClusters(&clusters, ras_cluster_kernel<P>, &cfg);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            clusters = 0;
+        }
+        known.store(clusters > 0 ? 1 : 2);
+    }
+    if (known.load() != 1) return cudaSuccess;
+    cudaError_t e = cudaLaunchKernelEx(&cfg, ras_cluster_kernel<P>, a);
+    note_launch();
+    *launched = true;
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 template <int P>
 static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
 {
@@ -977,6 +1348,13 @@ static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
         if (n <= 128) return launch_smem<P, 128, true, true>(a, st);
         if (n <= 256) return launch_smem<P, 256, P == P16>(a, st);
         if (n <= RAS_SMEM_MAX_SITES) return launch_smem<P, 512, P == P16>(a, st);
+    }
+    if constexpr (P == P16 || P == P32) {
+        if (a.variant != 3 && a.fuse == RAS_FUSE_NONE && ras_cluster_shape(a.dg)) {
+            bool ok = false;
+            const cudaError_t e = launch_cluster<P>(a, st, &ok);
+            if (ok || e != cudaSuccess) return e;
+        }
     }
     // the general kernel has no fused update (the caller checks ras_can_fuse)
     if (a.fuse != RAS_FUSE_NONE || !a.scratch || a.slots < 1) return cudaErrorInvalidValue;
