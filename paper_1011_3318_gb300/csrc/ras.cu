@@ -733,6 +733,18 @@ __device__ __forceinline__ void cluster_sync()
     cluster_wait();
 }
 
+// Arrival without ordering, for a thread whose prior writes are ordered by a
+// CTA barrier and one thread's cluster-scope release fence (cluster_fence).
+__device__ __forceinline__ void cluster_arrive_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void cluster_fence()
+{
+    asm volatile("fence.acq_rel.cluster;" ::: "memory");
+}
+
 // Shared-memory address of p (in this CTA) mapped to CTA `rank` of the cluster.
 __device__ __forceinline__ unsigned cluster_map(const void *p, unsigned rank)
 {
@@ -895,8 +907,9 @@ __global__ void __launch_bounds__(RAS_CLUSTER_MAX_SLICE, 1) ras_cluster_kernel(R
     // The residual of this slice is staged (or, in the loop, updated): arrive
     // on the cluster barrier, make it visible to this CTA, and apply the
     // site-local and in-slice parts of D before waiting for the other slices.
-    cluster_arrive();
     __syncthreads();
+    if (l == 0) cluster_fence();
+    cluster_arrive_relaxed();
     for (int it = 0; it < a.n_iter; it++) {
         C<float> q[12];
 #pragma unroll
@@ -950,8 +963,12 @@ __global__ void __launch_bounds__(RAS_CLUSTER_MAX_SLICE, 1) ras_cluster_kernel(R
                     t.z += wpart[2][w];
                 }
                 cpart = t;
+                cluster_fence();
             }
-            cluster_sync();  // every partial written; every hop has read its residual
+            // every partial written (thread 0's fence releases it); every hop
+            // has read its residual (the loaded values are consumed already)
+            cluster_arrive_relaxed();
+            cluster_wait();
             const int lane = l & 31;
             float4 t = {0.f, 0.f, 0.f, 0.f};
             if (lane < (int)ncta) t = ld_cluster_f4(cluster_map(&cpart, (unsigned)lane));
@@ -980,8 +997,11 @@ __global__ void __launch_bounds__(RAS_CLUSTER_MAX_SLICE, 1) ras_cluster_kernel(R
             st_local(sv, NT, l, vv);
             st_local(srho, NT, l, own);
         }
-        cluster_arrive();
+        // the updated residual: visible to this CTA after the CTA barrier, to
+        // the cluster after thread 0's release fence that follows it
         __syncthreads();
+        if (l == 0) cluster_fence();
+        cluster_arrive_relaxed();
     }
     // no CTA leaves while another may still read its partial or residual
     cluster_wait();
