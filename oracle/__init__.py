@@ -15,7 +15,8 @@ the paper it follows (Osaki & Ishikawa, Lattice 2010):
 * ``ras``          Alg. 1, phi = K_RAS eta (and the AS / SAP members of the
                    Schwarz family, Sec. 1 and Sec. 2);
 * ``bicgstab``     the right-preconditioned Krylov solve of Eq. 3;
-* ``solve``        the nested solver of Sec. 3 (FP64 defect correction).
+* ``solve``        the nested solver of Sec. 3 (FP64 defect correction);
+* ``solve_nested`` the same with the paper's FP64 outer BiCGStab (Sec. 3).
 
 Parity status of every function is pinned by ``tests/test_oracle_pins.py``.
 """
@@ -104,6 +105,8 @@ def lib():
                                     ctypes.c_int, ctypes.c_int, ctypes.c_double, P, P,
                                     ctypes.POINTER(OraInfo)]
             L.ora_solve.restype = ctypes.c_int
+            L.ora_solve_nested.argtypes = L.ora_solve.argtypes
+            L.ora_solve_nested.restype = ctypes.c_int
             L.ora_true_residual.argtypes = [ctypes.POINTER(OraOp), P, P]
             L.ora_true_residual.restype = ctypes.c_double
             _lib = L
@@ -252,6 +255,21 @@ class Op:
         info = OraInfo()
         lib().ora_solve(ctypes.byref(self._s), ctypes.byref(p), float(tol if inner_tol is None else inner_tol),
                         int(max_inner), int(max_outer), float(tol), pe, phi.ctypes.data, ctypes.byref(info))
+        return phi, {k: getattr(info, k) for k, _ in OraInfo._fields_}
+
+    def solve_nested(self, eta, tol: float, inner_tol: float = 1e-3, ras=None, max_inner: int = 100000,
+                     max_outer: int = 1000):
+        """The paper's nested solver (Sec. 3): FP64 outer BiCGStab with the
+        inner BiCGStab (right-preconditioned by K when ``ras`` is a dict of
+        prec() arguments) as a flexible preconditioner, restarted from the
+        true residual until it meets tol.  Returns (phi, info dict);
+        outer_iters counts outer BiCGStab iterations."""
+        eta, pe = _c(eta)
+        phi = np.zeros(self.shape(), dtype=np.complex128)
+        p = prec(False) if ras is None else prec(True, **ras)
+        info = OraInfo()
+        lib().ora_solve_nested(ctypes.byref(self._s), ctypes.byref(p), float(inner_tol), int(max_inner),
+                               int(max_outer), float(tol), pe, phi.ctypes.data, ctypes.byref(info))
         return phi, {k: getattr(info, k) for k, _ in OraInfo._fields_}
 
     def true_residual(self, eta, phi) -> float:

@@ -23,7 +23,9 @@
  *     of a red/black block ordering at a time, the residual updated between
  *     the colours), as comparisons to RAS.
  *   - Sec. 3: mixed-precision nested BiCGStab (inner solve preconditions the
- *     outer); here every level is FP64.
+ *     outer); here every level is FP64.  ora_solve takes the outer as FP64
+ *     defect correction, ora_solve_nested as the paper's outer BiCGStab with
+ *     the inner solve as a (variable) preconditioner.
  *   - Sec. 5: O(a)-improved Wilson quark, kappa, c_SW, stopping rule
  *     |eta - D phi| / |eta|.
  *
@@ -847,6 +849,97 @@ int ora_solve(const ora_op *op, const ora_prec *p, double inner_tol, int max_inn
     }
     if (info) *info = inf;
     free(r); free(rs); free(e); free(dphi);
+    return inf.status;
+}
+
+/* The paper's nested solver (Sec. 3): an FP64 BiCGStab whose preconditioner
+ * is the inner solve, M(y) = |y| inner(y / |y|), the inner BiCGStab
+ * (right-preconditioned by the Schwarz iteration when p->use_ras) run to
+ * inner_tol; M changes from call to call, which makes the outer BiCGStab a
+ * flexible one.  One pass solves D e = r from e = 0 until its recursive
+ * residual is below 0.5 tol |eta| (the margin covers the gap to the true
+ * residual); phi += e, r = eta - D phi, and a further pass starts from the
+ * true residual while |r| / |eta| > tol.  outer_iters counts outer BiCGStab
+ * iterations over all passes (capped by max_outer). */
+static void inner_apply(const ora_op *op, const ora_prec *p, double inner_tol, int max_inner, const cplx *y,
+                        cplx *out, cplx *tmp, ora_info *inf)
+{
+    long n = volume(op->L) * 12;
+    double yn = sqrt(vnorm2(n, y));
+    if (yn == 0) {
+        memset(out, 0, n * sizeof(cplx));
+        return;
+    }
+    for (long k = 0; k < n; k++) tmp[k] = y[k] / yn;
+    int it = 0, dv = 0;
+    ora_bicgstab(op, p, tmp, out, inner_tol, max_inner, &it, &dv);
+    for (long k = 0; k < n; k++) out[k] *= yn;
+    inf->inner_iters += it;
+    inf->dv_count += dv;
+}
+
+int ora_solve_nested(const ora_op *op, const ora_prec *p, double inner_tol, int max_inner, int max_outer,
+                     double tol, const cplx *eta, cplx *phi, ora_info *info)
+{
+    long n = volume(op->L) * 12;
+    size_t bytes = n * sizeof(cplx);
+    cplx *r = malloc(bytes), *e = malloc(bytes), *rr = malloc(bytes), *rh = malloc(bytes);
+    cplx *pp = malloc(bytes), *v = malloc(bytes), *s = malloc(bytes), *t = malloc(bytes);
+    cplx *ph = malloc(bytes), *sh = malloc(bytes), *tmp = malloc(bytes);
+    double enorm = sqrt(vnorm2(n, eta));
+    ora_info inf = {0, 0, 0, 1, 0.0};
+
+    memset(phi, 0, bytes);
+    memcpy(r, eta, bytes);
+    for (;;) {
+        double rn = sqrt(vnorm2(n, r));
+        inf.true_rel_residual = enorm > 0 ? rn / enorm : 0.0;
+        if (inf.true_rel_residual <= tol) { inf.status = 0; break; }
+        if (inf.outer_iters >= max_outer) { inf.status = 1; break; }
+        /* one flexible BiCGStab pass on D e = r */
+        double stop = 0.5 * tol * enorm;
+        memset(e, 0, bytes);
+        memcpy(rr, r, bytes);
+        memcpy(rh, r, bytes);
+        memset(pp, 0, bytes);
+        memset(v, 0, bytes);
+        cplx rho = 1, alpha = 1, omega = 1;
+        int broke = 0;
+        while (inf.outer_iters < max_outer) {
+            cplx rho1 = vdot(n, rh, rr);
+            if (rho1 == 0) { broke = 1; break; }
+            cplx beta = (rho1 / rho) * (alpha / omega);
+            for (long k = 0; k < n; k++) pp[k] = rr[k] + beta * (pp[k] - omega * v[k]);
+            inner_apply(op, p, inner_tol, max_inner, pp, ph, tmp, &inf);
+            ora_dslash(op, ph, v);
+            cplx rv = vdot(n, rh, v);
+            inf.outer_iters++;
+            if (rv == 0) { broke = 1; break; }
+            alpha = rho1 / rv;
+            for (long k = 0; k < n; k++) s[k] = rr[k] - alpha * v[k];
+            if (sqrt(vnorm2(n, s)) <= stop) {
+                for (long k = 0; k < n; k++) e[k] += alpha * ph[k];
+                break;
+            }
+            inner_apply(op, p, inner_tol, max_inner, s, sh, tmp, &inf);
+            ora_dslash(op, sh, t);
+            double tt = vnorm2(n, t);
+            if (tt == 0) { broke = 1; break; }
+            omega = vdot(n, t, s) / tt;
+            for (long k = 0; k < n; k++) {
+                e[k] += alpha * ph[k] + omega * sh[k];
+                rr[k] = s[k] - omega * t[k];
+            }
+            rho = rho1;
+            if (sqrt(vnorm2(n, rr)) <= stop) break;
+        }
+        for (long k = 0; k < n; k++) phi[k] += e[k];
+        ora_dslash(op, phi, t);
+        for (long k = 0; k < n; k++) r[k] = eta[k] - t[k];
+        if (broke && inf.outer_iters == 0) { inf.status = 2; break; }
+    }
+    if (info) *info = inf;
+    free(r); free(e); free(rr); free(rh); free(pp); free(v); free(s); free(t); free(ph); free(sh); free(tmp);
     return inf.status;
 }
 

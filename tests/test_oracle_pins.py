@@ -501,6 +501,46 @@ def test_sap_converges_faster_than_ras_per_cycle(small_system):
         assert sap < ras
 
 
+# ---------------------------------------------------------------- nested BiCGStab
+@pytest.mark.parametrize("inner_tol", [1e-1, 1e-3])
+@pytest.mark.parametrize("schwarz", [None, "ras", "sap"])
+def test_nested_bicgstab_matches_dense_solve(small_system, inner_tol, schwarz):
+    """The paper's outer BiCGStab around the inner solve reaches the dense
+    LAPACK solution to the requested tolerance whatever the inner accuracy
+    and preconditioner."""
+    op, Dm, eta, x = small_system
+    ras = None if schwarz is None else dict(block=(2, 2, 2, 2), s=0, n_ras=2, n_dominv=4, schwarz=schwarz)
+    phi, info = op.solve_nested(eta, 1e-11, inner_tol=inner_tol, ras=ras)
+    assert info["status"] == 0
+    assert np.linalg.norm(Dm @ phi.reshape(-1) - eta.reshape(-1)) / np.linalg.norm(eta) <= 1e-11
+    assert rel(phi, x) < 1e-9
+
+
+def test_nested_bicgstab_with_exact_inner_solve_takes_one_iteration(small_system):
+    """M = D^{-1} (inner solve to 1e-13): p = r, p_hat = D^{-1} r, v = r,
+    alpha = 1 and s = 0, so one outer iteration solves the system."""
+    op, Dm, eta, x = small_system
+    phi, info = op.solve_nested(eta, 1e-11, inner_tol=1e-13,
+                                ras=dict(block=(2, 2, 2, 2), s=0, n_ras=3, n_dominv=4))
+    assert info["status"] == 0 and info["outer_iters"] == 1
+    assert rel(phi, x) < 1e-11
+
+
+def test_nested_outer_krylov_beats_defect_correction(small_system):
+    """With a loose inner solve (1e-1, 0.5) defect correction gains at most
+    that factor per outer step (a Richardson iteration); the outer BiCGStab
+    builds a Krylov space from the same inner solves and needs fewer outer
+    iterations."""
+    op, Dm, eta, x = small_system
+    ras = dict(block=(2, 2, 2, 2), s=0, n_ras=1, n_dominv=2)
+    for inner_tol, min_dc in ((1e-1, 9), (0.5, 20)):
+        _, dc = op.solve(eta, 1e-11, inner_tol=inner_tol, ras=ras)
+        _, nb = op.solve_nested(eta, 1e-11, inner_tol=inner_tol, ras=ras)
+        assert dc["status"] == 0 and nb["status"] == 0
+        assert dc["outer_iters"] >= min_dc
+        assert nb["outer_iters"] < 0.7 * dc["outer_iters"]
+
+
 # ---------------------------------------------------------------- the config-1 contract
 def test_config1_plain_fp64_solve(oracle_mod):
     """8^4, eps = 0.3 (seed 1), kappa = 0.12, c_sw = 1, Gaussian source (seed 2),
