@@ -549,6 +549,10 @@ def run_workload(args):
                blocks, N_dominv 4, FP16 inner, 1..3 cycles, d in {0, 2} (AS:
                one cycle, d in {2, 4}, as AS with d = 0 is RAS), each solve
                timed once after an untimed one;
+      outer -- the 32^4 workload solved with FP64 defect correction and with
+               the paper's FP64 outer BiCGStab (Sec. 3) around the same inner
+               solve (4^4 blocks, NRAS 1, N_dominv 4), inner tolerance 1e-1,
+               1e-2, 1e-3, FP16 and FP32 inner;
       survey -- the paper's parameter survey (Sec. 5) on the 32^4 workload:
                NRAS 1..10 x N_dominv 1..20 x d = 2s in {0, 2, 4}, 4^4 blocks,
                FP16 inner, each solve timed once after one untimed solve of the
@@ -676,6 +680,38 @@ def run_workload(args):
                "equal_cost": "a cycle solves every domain once in each variant (SAP: red then black); "
                              "domain_solves_per_site counts them over the whole solve",
                "best": best, "grid": grid}
+    elif args.workload == "outer":
+        U = synth.gauge_field(DIMS, EPS, GSEED)
+        eta = synth.gaussian_source(DIMS, SSEED)
+        st = torch.cuda.Stream()
+        lat = qdd.create_lattice(DIMS, BC, stream=st)
+        qdd.load_gauge(lat, torch.from_numpy(U).cuda())
+        d_eta = torch.from_numpy(eta).cuda()
+        d_phi = torch.empty_like(d_eta)
+        op = oracle.Op(DIMS, BC, U, KAPPA, CSW, store_clover=False)
+        grid = []
+        for prec in ("f16", "f32"):
+            for itol in (1e-1, 1e-2, 1e-3):
+                for mode in (0, 1):
+                    p = qdd.default_params(inner_prec=prec, block=(4, 4, 4, 4), n_ras=1, n_dominv=4,
+                                           inner_tol=itol, outer_mode=mode)
+                    qdd.solve(lat, d_phi, d_eta, KAPPA, CSW, TOL, p, raise_on_failure=False)  # untimed
+                    ms, infos = time_steps(torch, st, lambda: qdd.solve(lat, d_phi, d_eta, KAPPA, CSW, TOL, p,
+                                                                        raise_on_failure=False), 1)
+                    i = infos[0]
+                    res = op.true_residual(eta, d_phi.cpu().numpy())
+                    ok = i["status"] == 0 and res <= TOL
+                    grid.append({"outer": "defect correction" if mode == 0 else "BiCGStab", "inner_prec": prec,
+                                 "inner_tol": itol, "ms": round(ms, 2) if ok else None,
+                                 "outer_iters": i["outer_iters"], "inner_iters": i["inner_iters"],
+                                 "oracle_true_rel_residual": res})
+        done = [g for g in grid if g["ms"] is not None]
+        rec = {"workload": "outer",
+               "metric": "32^4 solve time to 1e-10: FP64 defect correction vs the paper's FP64 outer BiCGStab",
+               "unit": "ms", "ras": {"block": [4, 4, 4, 4], "n_ras": 1, "n_dominv": 4},
+               "best": {o: min((g for g in done if g["outer"] == o), key=lambda g: g["ms"], default=None)
+                        for o in ("defect correction", "BiCGStab")},
+               "grid": grid}
     elif args.workload == "mrhs":
         dims, kappa, eps = (24, 24, 24, 48), 0.124, 0.25
         U = synth.gauge_field(dims, eps, 1)
@@ -822,10 +858,11 @@ def main():
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
                     help="use --block/--overlap/--n-dominv/--n-ras as given instead of tuning them")
     ap.add_argument("--tune-trials", dest="tune_trials", type=int, default=42)
-    ap.add_argument("--workload", choices=("solve", "mrhs", "batch", "survey", "table1", "schwarz"), default="solve",
+    ap.add_argument("--workload", choices=("solve", "mrhs", "batch", "survey", "table1", "schwarz", "outer"),
+                    default="solve",
                     help="solve: the 32^4 headline; mrhs / batch: the batched workloads; survey: the Sec. 5 "
                          "parameter survey; table1: the paper's slab-domain experiment emulated; schwarz: RAS, "
-                         "SAP and AS compared as the preconditioner")
+                         "SAP and AS compared as the preconditioner; outer: defect correction vs outer BiCGStab")
     ap.add_argument("--kernels", default=None,
                     help="profiler workload: dslash:f16|f32|f64, ras:f16|f32 or clover, three launches at 32^4")
     args = ap.parse_args()

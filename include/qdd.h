@@ -96,7 +96,11 @@ typedef struct {
     int max_inner;      /* inner BiCGStab iterations per outer step, default 2000 */
     int max_outer;      /* outer defect-correction steps, default 50 */
     int use_ras;        /* 1: right-precondition the inner solve with K_RAS (default 1) */
-    int outer_mode;     /* 0: FP64 defect correction (the only mode so far) */
+    int outer_mode;     /* outer level of the nested solver (Sec. 3): 0 FP64 defect
+                           correction, phi += |r| inner(r / |r|) (default); 1 the paper's
+                           FP64 outer BiCGStab with the inner solve (to inner_tol) as a
+                           flexible preconditioner, restarted from the true residual until
+                           tol is met; max_outer then bounds its iterations */
     int autotune;       /* reserved, 0 */
     int ras_kernel;     /* RAS sweep staging: 0 auto (TMA bulk tensor copies for overlap-free
                            256-site blocks with x extents divisible by 4, else per-thread
@@ -129,7 +133,8 @@ typedef struct {
 typedef enum { QDD_SCHWARZ_RAS = 0, QDD_SCHWARZ_SAP = 1, QDD_SCHWARZ_AS = 2 } qdd_schwarz;
 
 typedef struct {
-    int outer_iters;            /* defect-correction steps */
+    int outer_iters;            /* defect-correction steps (outer_mode 0) or outer BiCGStab
+                                   iterations (outer_mode 1) */
     int inner_iters;            /* inner BiCGStab iterations, summed */
     int dv_count;               /* global D applications (the paper's "Dv count", Table 1) */
     int ras_sweeps;             /* block-solve sweeps of K (SAP: two per cycle, one per colour) */

@@ -446,7 +446,8 @@ qdd_status qdd_solve(qdd_lattice *lat, double *phi, const double *eta, double ka
     if (params) p = *params;
     else qdd_default_params(&p);
     if (!valid_prec(p.inner_prec) || p.max_inner < 1 || p.max_outer < 1 || p.n_ras < 1 || p.n_dominv < 0 ||
-        !valid_schwarz(p.schwarz) || (p.inner_prec != QDD_F64 && !(p.inner_tol > 0 && p.inner_tol < 1))) {
+        !valid_schwarz(p.schwarz) || (p.outer_mode != 0 && p.outer_mode != 1) ||
+        (p.inner_prec != QDD_F64 && !(p.inner_tol > 0 && p.inner_tol < 1))) {
         set_error("invalid solver parameters");
         return QDD_ERR_ARG;
     }
@@ -495,7 +496,8 @@ qdd_status qdd_solve_batch(qdd_lattice *const *lats, double *const *phi, const d
     if (params) p = *params;
     else qdd_default_params(&p);
     if (!valid_prec(p.inner_prec) || p.max_inner < 1 || p.max_outer < 1 || p.n_ras < 1 || p.n_dominv < 0 ||
-        !valid_schwarz(p.schwarz) || (p.inner_prec != QDD_F64 && !(p.inner_tol > 0 && p.inner_tol < 1))) {
+        !valid_schwarz(p.schwarz) || (p.outer_mode != 0 && p.outer_mode != 1) ||
+        (p.inner_prec != QDD_F64 && !(p.inner_tol > 0 && p.inner_tol < 1))) {
         set_error("invalid solver parameters");
         return QDD_ERR_ARG;
     }

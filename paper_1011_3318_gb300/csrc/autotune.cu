@@ -33,7 +33,7 @@ bool same_ras(const qdd_solver_params &a, const qdd_solver_params &b)
 {
     return memcmp(a.block, b.block, sizeof(a.block)) == 0 && a.overlap == b.overlap && a.n_dominv == b.n_dominv &&
            a.n_ras == b.n_ras && a.ras_kernel == b.ras_kernel && a.inner_prec == b.inner_prec &&
-           a.inner_tol == b.inner_tol && a.schwarz == b.schwarz;
+           a.inner_tol == b.inner_tol && a.schwarz == b.schwarz && a.outer_mode == b.outer_mode;
 }
 
 }  // namespace

@@ -97,6 +97,13 @@ __global__ void __launch_bounds__(BLAS_NT) blas_kernel(BlasArgs a)
             C<T> z[12];
             zero12(z);
             store_spinor<P>(a.f[0], V, x, z);
+        } else if constexpr (OP == B_AXPY) {
+            C<T> f[12], g[12];
+            load_spinor<P>(a.f[0], V, x, f);
+            load_spinor<P>(a.f[1], V, x, g);
+#pragma unroll
+            for (int k = 0; k < 12; k++) f[k] = cadd(f[k], g[k]);
+            store_spinor<P>(a.f[0], V, x, f);
         } else if constexpr (OP == B_RESTART) {
             C<T> r[12], z[12];
             load_spinor<P>(a.f[1], V, x, r);
@@ -214,6 +221,7 @@ static cudaError_t launch_blas_p(int op, const BlasArgs &a, cudaStream_t st)
     case B_COPY: blas_kernel<P, B_COPY><<<nb, BLAS_NT, 0, st>>>(a); break;
     case B_ZERO: blas_kernel<P, B_ZERO><<<nb, BLAS_NT, 0, st>>>(a); break;
     case B_RESTART: blas_kernel<P, B_RESTART><<<nb, BLAS_NT, 0, st>>>(a); break;
+    case B_AXPY: blas_kernel<P, B_AXPY><<<nb, BLAS_NT, 0, st>>>(a); break;
     default: return cudaErrorInvalidValue;
     }
     note_launch();

@@ -104,6 +104,7 @@ enum BlasOp {
     B_COPY = 5,       // f0 = f1 (same precision)
     B_ZERO = 6,       // f0 = 0
     B_RESTART = 7,    // rhat(f0) = r(f1); p(f2) = v(f3) = 0; rho = <r, r>; alpha = omega = 1
+    B_AXPY = 8,       // f0 += f1 (same precision)
 };
 
 cudaError_t launch_blas(int prec, int op, const BlasArgs &a, cudaStream_t st);
@@ -252,8 +253,9 @@ qdd_status field_alloc(long long V, int prec, void **d, float **n);
 void field_free(void *d, float *n);
 LinkView links_of(const qdd_lattice *lat, int prec);
 CloverView clover_of(const qdd_lattice *lat, int prec);
+// sc: the scalars the epilogue reads and writes (null: the lattice's own)
 qdd_status run_dslash(qdd_lattice *lat, int prec, int epi, SpinorView out, SpinorView in, SpinorView y, double kappa,
-                      int aux_slot);
+                      int aux_slot, Scalars *sc = nullptr);
 qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params *p, const DomainGeom &dg,
                             SpinorView out, SpinorView in, SpinorView rho, SpinorView v, double kappa, int *dv,
                             const Scalars *sc,

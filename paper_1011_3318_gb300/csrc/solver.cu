@@ -1,6 +1,9 @@
-// solver.cu -- host orchestration of the nested solver (Sec. 3): FP64 outer
-// defect correction around an inner BiCGStab in FP32 or FP16 storage, right-
-// preconditioned by K_RAS (Eq. 3, Alg. 1); and the plain FP64 BiCGStab.
+// solver.cu -- host orchestration of the nested solver (Sec. 3): an FP64
+// outer level around an inner BiCGStab in FP32 or FP16 storage, right-
+// preconditioned by K_RAS (Eq. 3, Alg. 1); and the plain FP64 BiCGStab.  The
+// outer level is FP64 defect correction (outer_mode 0) or the paper's FP64
+// outer BiCGStab with the inner solve as a flexible preconditioner (outer_mode
+// 1), restarted from the true residual by the same defect-correction loop.
 //
 // A solve is a lockstep batch: one or more lattices, each with nrhs right-
 // hand sides, each lattice on its own stream with its own device scalars and
@@ -24,6 +27,11 @@
 struct qdd_work {
     // FP64 outer vectors: eta, phi, r (nrhs each)
     void *o_d[3] = {nullptr, nullptr, nullptr};
+    // FP64 vectors of the outer BiCGStab (outer_mode 1): e r rhat p v s t phat
+    // shat, and its scalars (device, and a pinned host mirror)
+    static constexpr int NNEST = 9;
+    void *n_d[NNEST] = {};
+    qdd::Scalars *osc = nullptr, *osc_host = nullptr;
     // inner vectors per precision: b x r rhat p v s t phat shat rho_ras v_ras
     static constexpr int NIN = 12;
     void *in_d[3][NIN] = {};
@@ -34,13 +42,18 @@ struct qdd_work {
 namespace qdd {
 
 enum { W_B, W_X, W_R, W_RHAT, W_P, W_V, W_S, W_T, W_PHAT, W_SHAT, W_RHO, W_VR };
+// vectors of the outer BiCGStab
+enum { N_E, N_R, N_RHAT, N_P, N_V, N_S, N_T, N_PHAT, N_SHAT };
 
-// aux slots of the device scalars
-enum { AUX_ETA2 = 0, AUX_R2 = 1, AUX_TOL2 = 7 };
+// aux slots of the device scalars (AUX_TOL2 is also read by B_INIT)
+enum { AUX_ETA2 = 0, AUX_R2 = 1, AUX_Y2 = 2, AUX_S2 = 3, AUX_TOL2 = 7 };
 
 void work_free(qdd_work *w)
 {
     if (!w) return;
+    for (int k = 0; k < qdd_work::NNEST; k++) cudaFree(w->n_d[k]);
+    cudaFree(w->osc);
+    if (w->osc_host) cudaFreeHost(w->osc_host);
     for (int k = 0; k < 3; k++) cudaFree(w->o_d[k]);
     for (int p = 0; p < 3; p++)
         for (int k = 0; k < qdd_work::NIN; k++) field_free(w->in_d[p][k], w->in_n[p][k]);
@@ -75,6 +88,39 @@ static qdd_status ensure_inner(qdd_lattice *lat, int prec)
     return QDD_OK;
 }
 
+static qdd_status ensure_nested(qdd_lattice *lat)
+{
+    qdd_work *w = lat->work;
+    for (int k = 0; k < qdd_work::NNEST; k++)
+        if (!w->n_d[k]) {
+            float *n = nullptr;
+            qdd_status st = field_alloc(nsites(lat), P64, &w->n_d[k], &n);
+            if (st != QDD_OK) return st;
+        }
+    if (!w->osc) {
+        if (cudaMalloc(&w->osc, sizeof(Scalars) * lat->nrhs) != cudaSuccess ||
+            cudaMemset(w->osc, 0, sizeof(Scalars) * lat->nrhs) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(w->osc);
+            w->osc = nullptr;
+            set_error("cudaMalloc of the outer solver scalars failed");
+            return QDD_ERR_NOMEM;
+        }
+    }
+    if (!w->osc_host) {
+        if (cudaMallocHost(&w->osc_host, sizeof(Scalars) * lat->nrhs) != cudaSuccess) {
+            cudaGetLastError();
+            w->osc_host = nullptr;
+            set_error("cudaMallocHost of the outer solver scalars failed");
+            return QDD_ERR_NOMEM;
+        }
+        memset(w->osc_host, 0, sizeof(Scalars) * lat->nrhs);
+    }
+    return QDD_OK;
+}
+
+static SpinorView nested(qdd_lattice *lat, int k) { return SpinorView{lat->work->n_d[k], nullptr}; }
+
 static SpinorView inner(qdd_lattice *lat, int prec, int k)
 {
     return SpinorView{lat->work->in_d[prec][k], lat->work->in_n[prec][k]};
@@ -83,14 +129,14 @@ static SpinorView inner(qdd_lattice *lat, int prec, int k)
 static SpinorView outer(qdd_lattice *lat, int k) { return SpinorView{lat->work->o_d[k], nullptr}; }
 
 static qdd_status blas(qdd_lattice *lat, int prec, int op, std::initializer_list<SpinorView> fs, int aux_slot = 0,
-                       double tol2 = 0.0, unsigned long long active = ~0ull)
+                       double tol2 = 0.0, unsigned long long active = ~0ull, Scalars *sc = nullptr)
 {
     BlasArgs a;
     memset(&a, 0, sizeof(a));
     a.V = lat->g.V;
     int i = 0;
     for (const SpinorView &f : fs) a.f[i++] = f;
-    a.sc = lat->sc;
+    a.sc = sc ? sc : lat->sc;
     a.rs = lat->rs;
     a.aux_slot = aux_slot;
     a.tol2_rel = tol2;
@@ -101,12 +147,15 @@ static qdd_status blas(qdd_lattice *lat, int prec, int op, std::initializer_list
     return e == cudaSuccess ? QDD_OK : cuda_fail(e, "blas kernel");
 }
 
-// Copies the device scalars of every lattice to the host and waits.
-static qdd_status read_scalars(const std::vector<qdd_lattice *> &lats)
+// Copies the device scalars of every lattice (with outer = true: those of
+// the outer BiCGStab) to the host and waits.
+static qdd_status read_scalars(const std::vector<qdd_lattice *> &lats, bool outer = false)
 {
     for (qdd_lattice *lat : lats) {
-        cudaError_t e = cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(Scalars) * lat->nrhs, cudaMemcpyDeviceToHost,
-                                        lat->stream);
+        cudaError_t e = outer ? cudaMemcpyAsync(lat->work->osc_host, lat->work->osc, sizeof(Scalars) * lat->nrhs,
+                                                cudaMemcpyDeviceToHost, lat->stream)
+                              : cudaMemcpyAsync(lat->sc_host, lat->sc, sizeof(Scalars) * lat->nrhs,
+                                                cudaMemcpyDeviceToHost, lat->stream);
         if (e != cudaSuccess) return cuda_fail(e, "reading solver scalars");
     }
     for (qdd_lattice *lat : lats) {
@@ -118,7 +167,7 @@ static qdd_status read_scalars(const std::vector<qdd_lattice *> &lats)
 }
 
 qdd_status run_dslash(qdd_lattice *lat, int prec, int epi, SpinorView out, SpinorView in, SpinorView y, double kappa,
-                      int aux_slot)
+                      int aux_slot, Scalars *sc)
 {
     DslashArgs a;
     memset(&a, 0, sizeof(a));
@@ -130,7 +179,7 @@ qdd_status run_dslash(qdd_lattice *lat, int prec, int epi, SpinorView out, Spino
     a.A = clover_of(lat, prec);
     a.kappa = kappa;
     a.rs = lat->rs;
-    a.sc = lat->sc;
+    a.sc = sc ? sc : lat->sc;
     a.aux_slot = aux_slot;
     a.nrhs = lat->nrhs;
     ProfScope ps(lat, prec == P64 ? QDD_K_DSLASH_F64 : QDD_K_DSLASH);
@@ -262,6 +311,7 @@ struct Member {
     DomainGeom dg;
     std::vector<double> eta2, rr, best;
     std::vector<int> stalls, restarted, done, result;
+    std::vector<int> oit;  // outer BiCGStab iterations (outer_mode 1)
 };
 
 // One BiCGStab iteration (van der Vorst) of every right-hand side of a
@@ -405,6 +455,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
         m.restarted.assign(R, 0);
         m.done.assign(R, 0);
         m.result.assign(R, QDD_ERR_NOT_CONVERGED);
+        m.oit.assign(R, 0);
         if (m.info) memset(m.info, 0, sizeof(qdd_solve_info) * R);
         for (int j = 0; j < i; j++)
             if (L[j] == L[i]) {
@@ -446,43 +497,22 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
     const int chunk = vmax >= (1 << 18) ? 2 : 4;
     IterGraph graph;
     bool have_graph = false;
+    const bool nested_outer = !plain && p->outer_mode == 1;
 
-    for (int outer_it = 0;; outer_it++) {
-        // which right-hand sides still need an inner solve
-        bool any = false;
-        for (Member &m : ms)
-            for (int r = 0; r < m.lat->nrhs; r++) {
-                if (m.done[r]) continue;
-                const double rel = m.eta2[r] > 0 ? std::sqrt(m.rr[r] / m.eta2[r]) : 0.0;
-                if (!std::isfinite(rel)) {
-                    m.done[r] = 1;
-                    m.result[r] = QDD_ERR_NONFINITE;
-                } else if (rel <= tol) {
-                    m.done[r] = 1;
-                    m.result[r] = QDD_OK;
-                } else if (outer_it >= p->max_outer) {
-                    m.done[r] = 1;
-                } else {
-                    any = true;
-                }
-            }
-        if (!any) break;
+    // One inner solve of every lattice: right-hand side r of lattice m is
+    // src(m) / sqrt(nsc[r].aux[slot]), solved to the relative tolerance
+    // sqrt(sc_host[r].aux[AUX_TOL2]) (set by the caller) for the right-hand
+    // sides whose bit is set in active[m]; the solution is left in W_X.
+    auto inner_solve = [&](const std::vector<SpinorView> &src, const std::vector<Scalars *> &nsc, int slot,
+                           const std::vector<unsigned long long> &active) -> qdd_status {
         const auto ti = clk::now();
-        for (Member &m : ms) {
+        qdd_status st;
+        for (size_t i = 0; i < ms.size(); i++) {
+            Member &m = ms[i];
             qdd_lattice *lat = m.lat;
             const int R = lat->nrhs;
-            unsigned long long active = 0;
             for (int r = 0; r < R; r++) {
-                // tolerance of this inner solve relative to |r|: no further than
-                // the outer target needs, with a margin for the gap between the
-                // recursive and the true residual
-                double tol_in = m.rr[r] > 0 ? 0.5 * tol * std::sqrt(m.eta2[r] / m.rr[r]) : 1.0;
-                if (!plain && p->inner_tol > tol_in) tol_in = p->inner_tol;
-                lat->sc_host[r].aux[AUX_TOL2] = tol_in * tol_in;
-                if (!m.done[r]) active |= 1ull << r;
                 m.restarted[r] = 0;
-            }
-            for (int r = 0; r < R; r++) {
                 cudaError_t e = cudaMemcpyAsync(&lat->sc[r].aux[AUX_TOL2], &lat->sc_host[r].aux[AUX_TOL2],
                                                 sizeof(double), cudaMemcpyHostToDevice, lat->stream);
                 if (e != cudaSuccess) return cuda_fail(e, "scalar upload");
@@ -490,13 +520,12 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
             cudaError_t e;
             {
                 ProfScope ps(lat, QDD_K_CONVERT);
-                e = launch_convert_scaled(lat->g.V, prec, inner(lat, prec, W_B), outer(lat, 2), lat->sc, AUX_R2, R,
-                                          lat->stream);
+                e = launch_convert_scaled(lat->g.V, prec, inner(lat, prec, W_B), src[i], nsc[i], slot, R, lat->stream);
             }
             if (e != cudaSuccess) return cuda_fail(e, "convert");
             auto F = [&](int k) { return inner(lat, prec, k); };
-            if ((st = blas(lat, prec, B_INIT, {F(W_B), F(W_R), F(W_RHAT), F(W_X), F(W_P), F(W_V)}, 0, -1.0, active)) !=
-                QDD_OK)
+            if ((st = blas(lat, prec, B_INIT, {F(W_B), F(W_R), F(W_RHAT), F(W_X), F(W_P), F(W_V)}, 0, -1.0,
+                           active[i])) != QDD_OK)
                 return st;
         }
         // inner iterations of every lattice until no right-hand side runs
@@ -563,20 +592,17 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
             }
             if (!running) break;
         }
-        t_inner += std::chrono::duration<double, std::milli>(clk::now() - ti).count();
-        // phi += |r| x ; r = eta - D phi ; |r|^2
-        for (Member &m : ms) {
-            qdd_lattice *lat = m.lat;
-            const int R = lat->nrhs;
-            for (int r = 0; r < R; r++) {
-                if (m.done[r]) continue;
-                const Scalars &h = lat->sc_host[r];
+        // counts, and failures that end a right-hand side
+        for (size_t i = 0; i < ms.size(); i++) {
+            Member &m = ms[i];
+            for (int r = 0; r < m.lat->nrhs; r++) {
+                if (!((active[i] >> r) & 1ull) || m.done[r]) continue;
+                const Scalars &h = m.lat->sc_host[r];
                 if (m.info) {
                     m.info[r].inner_iters += h.iter;
                     const int nsweep = p->n_ras * schwarz_plan(p->schwarz, m.dg).colors;
                     m.info[r].dv_count += 2 * h.iter + (m.use_ras ? 2 * h.iter * (nsweep - 1) : 0);
                     m.info[r].ras_sweeps += m.use_ras ? 2 * h.iter * nsweep : 0;
-                    m.info[r].outer_iters++;
                 }
                 if (h.status == S_NONFINITE) {
                     m.done[r] = 1;
@@ -586,13 +612,230 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                     m.result[r] = QDD_ERR_TIMEOUT;
                 }
             }
-            cudaError_t e;
-            {
-                ProfScope ps(lat, QDD_K_CONVERT);
-                e = launch_accum_scaled(lat->g.V, prec, outer(lat, 1), inner(lat, prec, W_X), lat->sc, AUX_R2, R,
-                                        lat->stream);
+        }
+        t_inner += std::chrono::duration<double, std::milli>(clk::now() - ti).count();
+        return QDD_OK;
+    };
+
+    // Uploads the host copy of the outer scalars of right-hand side r.
+    auto put_osc = [&](qdd_lattice *lat, int r) -> qdd_status {
+        cudaError_t e = cudaMemcpyAsync(&lat->work->osc[r], &lat->work->osc_host[r], sizeof(Scalars),
+                                        cudaMemcpyHostToDevice, lat->stream);
+        return e == cudaSuccess ? QDD_OK : cuda_fail(e, "scalar upload");
+    };
+
+    // One pass of the outer BiCGStab (outer_mode 1) on D e = r from e = 0,
+    // the inner solve as its flexible preconditioner M(y) = |y| inner(y/|y|):
+    //   p = r + beta (p - omega v); phat = M(p); v = D phat; alpha = rho / <rhat, v>;
+    //   s = r - alpha v; shat = M(s); t = D shat; omega = <t, s> / |t|^2;
+    //   e += alpha phat + omega shat; r = s - omega t
+    // until |r| <= 0.5 tol |eta| (or |s| is: then e += alpha phat), then phi += e.
+    auto nested_pass = [&]() -> qdd_status {
+        qdd_status st;
+        std::vector<unsigned long long> active(ms.size(), 0);
+        std::vector<SpinorView> src(ms.size());
+        std::vector<Scalars *> nsc(ms.size());
+        for (size_t i = 0; i < ms.size(); i++) {
+            Member &m = ms[i];
+            qdd_lattice *lat = m.lat;
+            if ((st = ensure_nested(lat)) != QDD_OK) return st;
+            Scalars *oh = lat->work->osc_host;
+            for (int r = 0; r < lat->nrhs; r++) {
+                oh[r].aux[AUX_TOL2] = m.rr[r] > 0 ? 0.25 * tol * tol * m.eta2[r] / m.rr[r] : 1.0;
+                cudaError_t e = cudaMemcpyAsync(&lat->work->osc[r].aux[AUX_TOL2], &oh[r].aux[AUX_TOL2],
+                                                sizeof(double), cudaMemcpyHostToDevice, lat->stream);
+                if (e != cudaSuccess) return cuda_fail(e, "scalar upload");
+                if (!m.done[r]) active[i] |= 1ull << r;
             }
-            if (e != cudaSuccess) return cuda_fail(e, "accumulate");
+            auto N = [&](int k) { return nested(lat, k); };
+            if ((st = blas(lat, P64, B_INIT, {outer(lat, 2), N(N_R), N(N_RHAT), N(N_E), N(N_P), N(N_V)}, 0, -1.0,
+                           active[i], lat->work->osc)) != QDD_OK)
+                return st;
+            nsc[i] = lat->work->osc;
+        }
+        if ((st = read_scalars(L, true)) != QDD_OK) return st;
+        std::vector<std::vector<int>> sdone(ms.size());
+        for (;;) {
+            // the right-hand sides whose outer BiCGStab runs
+            bool any = false;
+            for (size_t i = 0; i < ms.size(); i++) {
+                Member &m = ms[i];
+                active[i] = 0;
+                sdone[i].assign(m.lat->nrhs, 0);
+                for (int r = 0; r < m.lat->nrhs; r++) {
+                    const bool budget = m.oit[r] < p->max_outer;
+                    if (m.lat->work->osc_host[r].status == S_RUN && !m.done[r] && budget) {
+                        active[i] |= 1ull << r;
+                        any = true;
+                    } else if (m.lat->work->osc_host[r].status == S_RUN) {
+                        // out of outer iterations: stop it
+                        m.lat->work->osc_host[r].status = S_CONVERGED;
+                        if ((st = put_osc(m.lat, r)) != QDD_OK) return st;
+                    }
+                }
+            }
+            if (!any) break;
+            // p, phat = M(p), v = D phat with alpha, s, |s|^2
+            for (size_t i = 0; i < ms.size(); i++) {
+                qdd_lattice *lat = ms[i].lat;
+                auto N = [&](int k) { return nested(lat, k); };
+                Scalars *osc = lat->work->osc;
+                if ((st = blas(lat, P64, B_P, {N(N_P), N(N_R), N(N_V)}, 0, 0.0, ~0ull, osc)) != QDD_OK) return st;
+                if ((st = blas(lat, P64, B_NORM, {N(N_P)}, AUX_Y2, 0.0, ~0ull, osc)) != QDD_OK) return st;
+                if ((st = blas(lat, P64, B_ZERO, {N(N_PHAT)})) != QDD_OK) return st;
+                src[i] = N(N_P);
+                for (int r = 0; r < lat->nrhs; r++) lat->sc_host[r].aux[AUX_TOL2] = p->inner_tol * p->inner_tol;
+            }
+            if ((st = inner_solve(src, nsc, AUX_Y2, active)) != QDD_OK) return st;
+            for (size_t i = 0; i < ms.size(); i++) {
+                Member &m = ms[i];
+                qdd_lattice *lat = m.lat;
+                auto N = [&](int k) { return nested(lat, k); };
+                Scalars *osc = lat->work->osc;
+                cudaError_t e;
+                {
+                    ProfScope ps(lat, QDD_K_CONVERT);
+                    e = launch_accum_scaled(lat->g.V, prec, N(N_PHAT), inner(lat, prec, W_X), osc, AUX_Y2, lat->nrhs,
+                                            lat->stream);
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "accumulate");
+                if ((st = run_dslash(lat, P64, EPI_RV, N(N_V), N(N_PHAT), N(N_RHAT), m.kappa, 0, osc)) != QDD_OK)
+                    return st;
+                if ((st = blas(lat, P64, B_S, {N(N_S), N(N_R), N(N_V)}, 0, 0.0, ~0ull, osc)) != QDD_OK) return st;
+                if ((st = blas(lat, P64, B_NORM, {N(N_S)}, AUX_S2, 0.0, ~0ull, osc)) != QDD_OK) return st;
+                if ((st = blas(lat, P64, B_ZERO, {N(N_SHAT)})) != QDD_OK) return st;
+            }
+            if ((st = read_scalars(L, true)) != QDD_OK) return st;
+            // a right-hand side whose |s| already meets the target skips M(s)
+            // and t: it is parked (status not running) until e += alpha phat
+            for (size_t i = 0; i < ms.size(); i++) {
+                qdd_lattice *lat = ms[i].lat;
+                Scalars *oh = lat->work->osc_host;
+                for (int r = 0; r < lat->nrhs; r++) {
+                    if (!((active[i] >> r) & 1ull)) continue;
+                    if (oh[r].status != S_RUN) {
+                        active[i] &= ~(1ull << r);
+                    } else if (oh[r].aux[AUX_S2] <= oh[r].tol2) {
+                        sdone[i][r] = 1;
+                        active[i] &= ~(1ull << r);
+                        oh[r].status = S_CONVERGED;
+                        if ((st = put_osc(lat, r)) != QDD_OK) return st;
+                    }
+                }
+                src[i] = nested(lat, N_S);
+                for (int r = 0; r < lat->nrhs; r++) lat->sc_host[r].aux[AUX_TOL2] = p->inner_tol * p->inner_tol;
+            }
+            if ((st = inner_solve(src, nsc, AUX_S2, active)) != QDD_OK) return st;
+            for (size_t i = 0; i < ms.size(); i++) {
+                Member &m = ms[i];
+                qdd_lattice *lat = m.lat;
+                auto N = [&](int k) { return nested(lat, k); };
+                Scalars *osc = lat->work->osc;
+                Scalars *oh = lat->work->osc_host;
+                cudaError_t e;
+                {
+                    ProfScope ps(lat, QDD_K_CONVERT);
+                    e = launch_accum_scaled(lat->g.V, prec, N(N_SHAT), inner(lat, prec, W_X), osc, AUX_S2, lat->nrhs,
+                                            lat->stream);
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "accumulate");
+                if ((st = run_dslash(lat, P64, EPI_TS, N(N_T), N(N_SHAT), N(N_S), m.kappa, 0, osc)) != QDD_OK)
+                    return st;
+                for (int r = 0; r < lat->nrhs; r++)
+                    if (sdone[i][r]) {  // omega = 0: e += alpha phat, r = s
+                        oh[r].status = S_RUN;
+                        oh[r].omega = make_double2(0.0, 0.0);
+                        if ((st = put_osc(lat, r)) != QDD_OK) return st;
+                    }
+                if ((st = blas(lat, P64, B_XR,
+                               {N(N_E), N(N_PHAT), N(N_SHAT), N(N_R), N(N_S), N(N_T), N(N_RHAT)}, 0, 0.0, ~0ull,
+                               osc)) != QDD_OK)
+                    return st;
+            }
+            if ((st = read_scalars(L, true)) != QDD_OK) return st;
+            for (size_t i = 0; i < ms.size(); i++) {
+                Member &m = ms[i];
+                for (int r = 0; r < m.lat->nrhs; r++) {
+                    if (!((active[i] >> r) & 1ull) && !sdone[i][r]) continue;
+                    m.oit[r]++;
+                    if (m.info) m.info[r].outer_iters++;
+                    const int os = m.lat->work->osc_host[r].status;
+                    if (os == S_NONFINITE) {
+                        m.done[r] = 1;
+                        m.result[r] = QDD_ERR_NONFINITE;
+                    }
+                    // a breakdown ends the pass; the defect-correction loop
+                    // restarts from the true residual
+                }
+            }
+        }
+        for (Member &m : ms)
+            if ((st = blas(m.lat, P64, B_AXPY, {outer(m.lat, 1), nested(m.lat, N_E)})) != QDD_OK) return st;
+        return QDD_OK;
+    };
+
+    for (int outer_it = 0;; outer_it++) {
+        // which right-hand sides still need a correction
+        bool any = false;
+        for (Member &m : ms)
+            for (int r = 0; r < m.lat->nrhs; r++) {
+                if (m.done[r]) continue;
+                const double rel = m.eta2[r] > 0 ? std::sqrt(m.rr[r] / m.eta2[r]) : 0.0;
+                const bool budget = nested_outer ? m.oit[r] < p->max_outer : outer_it < p->max_outer;
+                if (!std::isfinite(rel)) {
+                    m.done[r] = 1;
+                    m.result[r] = QDD_ERR_NONFINITE;
+                } else if (rel <= tol) {
+                    m.done[r] = 1;
+                    m.result[r] = QDD_OK;
+                } else if (!budget || (nested_outer && outer_it >= p->max_outer)) {
+                    m.done[r] = 1;
+                } else {
+                    any = true;
+                }
+            }
+        if (!any) break;
+        if (nested_outer) {
+            if ((st = nested_pass()) != QDD_OK) return st;
+        } else {
+            // one inner solve of r / |r|, then phi += |r| x
+            std::vector<unsigned long long> active(ms.size(), 0);
+            std::vector<SpinorView> src(ms.size());
+            std::vector<Scalars *> nsc(ms.size());
+            for (size_t i = 0; i < ms.size(); i++) {
+                Member &m = ms[i];
+                qdd_lattice *lat = m.lat;
+                for (int r = 0; r < lat->nrhs; r++) {
+                    // tolerance of this inner solve relative to |r|: no further than
+                    // the outer target needs, with a margin for the gap between the
+                    // recursive and the true residual
+                    double tol_in = m.rr[r] > 0 ? 0.5 * tol * std::sqrt(m.eta2[r] / m.rr[r]) : 1.0;
+                    if (!plain && p->inner_tol > tol_in) tol_in = p->inner_tol;
+                    lat->sc_host[r].aux[AUX_TOL2] = tol_in * tol_in;
+                    if (!m.done[r]) active[i] |= 1ull << r;
+                }
+                src[i] = outer(lat, 2);
+                nsc[i] = lat->sc;
+            }
+            if ((st = inner_solve(src, nsc, AUX_R2, active)) != QDD_OK) return st;
+            for (size_t i = 0; i < ms.size(); i++) {
+                Member &m = ms[i];
+                qdd_lattice *lat = m.lat;
+                if (m.info)
+                    for (int r = 0; r < lat->nrhs; r++)
+                        if ((active[i] >> r) & 1ull) m.info[r].outer_iters++;
+                cudaError_t e;
+                {
+                    ProfScope ps(lat, QDD_K_CONVERT);
+                    e = launch_accum_scaled(lat->g.V, prec, outer(lat, 1), inner(lat, prec, W_X), lat->sc, AUX_R2,
+                                            lat->nrhs, lat->stream);
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "accumulate");
+            }
+        }
+        // r = eta - D phi ; |r|^2
+        for (Member &m : ms) {
+            qdd_lattice *lat = m.lat;
             if ((st = run_dslash(lat, P64, EPI_XMY_NORM, outer(lat, 2), outer(lat, 1), outer(lat, 0), m.kappa,
                                  AUX_R2)) != QDD_OK)
                 return st;
