@@ -50,6 +50,7 @@ def test_host_side_calls_without_gpu(libpath):
     assert "sm_103a" in qdd.version()
     p = qdd.default_params()
     assert list(p.block) == [4, 4, 4, 4] and p.n_ras == 3 and p.n_dominv == 4 and p.inner_tol == 1e-3
+    assert p.schwarz == qdd.QDD_SCHWARZ_RAS and p.outer_mode == 0 and p.ras_kernel == 0
     lib = qdd.lib()
     h = ctypes.c_void_p()
     bad_dims = (ctypes.c_int * 4)(8, 0, 8, 8)
@@ -81,3 +82,24 @@ def test_oracle_and_library_share_no_code():
         if f.endswith((".py", ".c")):
             text = open(os.path.join(ROOT, "oracle", f)).read()
             assert "paper_1011_3318_gb300" not in text and "qdd.h" not in text
+
+
+def test_binding_structs_mirror_the_header():
+    """The ctypes mirrors of qdd_solver_params and qdd_solve_info list the
+    header's fields in the header's order."""
+    import re
+    from paper_1011_3318_gb300 import qdd
+    text = open(os.path.join(ROOT, "include", "qdd.h")).read()
+    for cname, cls in (("qdd_solver_params", qdd.SolverParams), ("qdd_solve_info", qdd.SolveInfo)):
+        end = text.index("} " + cname + ";")
+        body = text[text.rindex("typedef struct {", 0, end) + len("typedef struct {"):end]
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        names = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            first, *rest = [x.strip() for x in decl.split(",")]
+            names.append(re.sub(r"\[.*\]", "", first.split()[-1]))
+            names.extend(re.sub(r"\[.*\]", "", x) for x in rest)
+        assert names == [f[0] for f in cls._fields_], cname
