@@ -809,13 +809,15 @@ def run_workload(args):
 
 def run_kernels(spec):
     """Kernel microbenchmark for profilers: builds the 32^4 workload and runs
-    one kernel a few times -- dslash:<prec>, ras:<prec> (one RAS sweep of 4^4
-    blocks, N_dominv = 4) or clover (the clover build)."""
+    one kernel a few times -- dslash:<prec>, ras:<prec>[:<s>] (one RAS sweep of
+    4^4 blocks, N_dominv = 4, extension s, default 0: s = 1, 2 run the
+    thread-block-cluster sweep) or clover (the clover build)."""
     import torch
 
     import synth
     from paper_1011_3318_gb300 import qdd
     kind, _, prec = spec.partition(":")
+    prec, _, ext = prec.partition(":")
     U = synth.gauge_field(DIMS, EPS, GSEED)
     eta = synth.gaussian_source(DIMS, SSEED)
     lat = qdd.create_lattice(DIMS, BC)
@@ -829,9 +831,17 @@ def run_kernels(spec):
         for _ in range(3):
             qdd.dslash_field(lat, b, a, KAPPA, CSW)
     elif kind == "ras":
-        p = qdd.default_params(inner_prec=prec, n_ras=1, n_dominv=4)
+        p = qdd.default_params(inner_prec=prec, n_ras=1, n_dominv=4, overlap=int(ext or 0))
         for _ in range(3):
             qdd.ras_apply(lat, out, deta, KAPPA, CSW, p)
+        # then the sweep alone, timed by the library's per-class CUDA events
+        qdd.set_profiling(lat, True)
+        qdd.profile_read(lat, True)
+        for _ in range(5):
+            qdd.ras_apply(lat, out, deta, KAPPA, CSW, p)
+        ms, n = qdd.profile_read(lat, True)["ras"]
+        qdd.set_profiling(lat, False)
+        log(f"RAS sweep {spec}: {1e3 * ms / max(n, 1):.1f} us per sweep (CUDA events, {n} sweeps)")
     elif kind == "clover":
         for k in range(3):
             qdd.dslash(lat, out, deta, KAPPA + 0.001 * k, CSW, "f32")
@@ -864,7 +874,7 @@ def main():
                          "parameter survey; table1: the paper's slab-domain experiment emulated; schwarz: RAS, "
                          "SAP and AS compared as the preconditioner; outer: defect correction vs outer BiCGStab")
     ap.add_argument("--kernels", default=None,
-                    help="profiler workload: dslash:f16|f32|f64, ras:f16|f32 or clover, three launches at 32^4")
+                    help="profiler workload: dslash:f16|f32|f64, ras:f16|f32[:s] or clover, three launches at 32^4")
     args = ap.parse_args()
     if args.kernels:
         return run_kernels(args.kernels)
