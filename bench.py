@@ -604,8 +604,9 @@ def run_workload(args):
                "runs": runs, "paper_context": paper,
                "dv_ratio_none_over_d0": round(runs["none"]["dv_count"] / max(1, runs["d0"]["dv_count"]), 2),
                "paper_dv_ratio_none_over_d0": round(1328 / 484, 2),
-               "note": "one CTA per slab domain: 8 of 152 SMs do the domain solves, so the times show why "
-                       "the slab layout is the cluster's and the tuned 4^4 blocks are the GPU's"}
+               "note": "each slab domain is spread over many CTAs (the phased sweep, one launch per MR step, "
+                       "as the paper's one domain per GPU); with 8 domains the sweep's launches and per-domain "
+                       "reductions cost more than the tuned 4^4 blocks (4096 CTAs, one launch per sweep)"}
     elif args.workload == "survey":
         U = synth.gauge_field(DIMS, EPS, GSEED)
         eta = synth.gaussian_source(DIMS, SSEED)

@@ -107,10 +107,12 @@ typedef struct {
                            loads), 1 compact per-thread staging (links and clover in the
                            field's storage format), 2 expanded (FP32 18-real links and FP32
                            clover, domains of at most 256 sites), 3 the general kernel
-                           (global scratch) for every extended domain above 512 sites
-                           instead of the thread-block-cluster kernel (auto: one cluster
-                           per domain, one CTA per t-slice, when the domain has 2 to 8
-                           t-slices of at most 512 sites) */
+                           (global scratch, one CTA per domain) for every extended domain
+                           above 512 sites; auto uses for those one thread-block cluster
+                           per domain (one CTA per t-slice) when the domain has 2 to 8
+                           t-slices of at most 512 sites, else, when domains x n_rhs is
+                           below 304, the phased sweep (each domain over many CTAs, one
+                           launch per MR step), else the general kernel */
     int schwarz;        /* member of the Schwarz family used as K (Sec. 1, Sec. 2), a
                            qdd_schwarz: QDD_SCHWARZ_RAS (default, Alg. 1), QDD_SCHWARZ_SAP or
                            QDD_SCHWARZ_AS; n_ras counts cycles for each */

@@ -162,6 +162,11 @@ constexpr int RAS_SMEM_MAX_SITES = 512;
 // Whether larger extended domains fit the cluster kernel (one CTA per
 // t-slice of at most 512 sites, at most 8 slices).
 bool ras_cluster_shape(const DomainGeom &dg);
+// Whether the domains (times right-hand sides) are too few for one CTA each:
+// then every domain is spread over many CTAs (the phased sweep), which needs
+// ras_phased_scratch_bytes of scratch.
+bool ras_use_phased(const DomainGeom &dg, int nrhs);
+size_t ras_phased_scratch_bytes(const DomainGeom &dg, int nrhs);
 
 cudaError_t launch_ras_block(int prec, const RasArgs &a, cudaStream_t st);
 // vout = asum, acc = asum or acc += asum (the additive-Schwarz sum of a sweep)

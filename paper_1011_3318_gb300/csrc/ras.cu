@@ -25,6 +25,10 @@
 //  * ras_gmem_kernel: any domain size.  A persistent grid of `slots` CTAs
 //    loops over the domains; rho, q and v of the current domain live in a
 //    per-CTA slot of global scratch (L2-resident for moderate domains).
+//  * ras_cluster_kernel: 6^4 or 8^4 extended domains (overlap on 4^4 blocks),
+//    one thread-block cluster per domain.
+//  * the phased sweep (ras_phase_*): few large domains, each spread over many
+//    CTAs, one launch per MR step.
 //
 // The same kernels run the other members of the Schwarz family: a sweep of
 // the multiplicative SAP solves only the domains of one colour of the
@@ -1109,6 +1113,215 @@ __global__ void __launch_bounds__(RAS_GMEM_NT) ras_gmem_kernel(const RasArgs a0)
     }
 }
 
+// ---------------------------------------------------------------- phased
+// Few large domains (the paper's slabs: 8 domains of 4 x 32^3 sites and
+// more) leave most SMs idle with one CTA per domain.  The phased sweep spreads
+// every domain over many CTAs and runs the MR iterations as launches: stage
+// (rho = P r, v = 0), then per iteration apply (q = D_Omega' rho and one
+// partial of <q, rho>, |q|^2 per CTA), alpha (one CTA per domain adds the
+// partials in CTA order) and update (v += alpha rho, rho -= alpha q), and
+// finally the restriction.  rho, q and v live in a global-scratch slot per
+// (domain, right-hand side) as for ras_gmem_kernel; kernel boundaries order
+// the iterations.  Items are (domain, right-hand side) pairs, right-hand side
+// fastest; a domain's CTAs are consecutive.
+
+constexpr int RAS_PH_NT = 256;
+
+struct PhaseGrid {
+    int nblk;  // CTAs per item
+};
+
+__device__ __forceinline__ float2 *phase_slot(const RasArgs &a, int item)
+{
+    return a.scratch + (size_t)item * 36 * (size_t)a.dg.nloc;
+}
+
+// the partial sums (3 per CTA) and the alphas (one float2 per item, 16-byte
+// aligned) after the slots
+__device__ __forceinline__ float *phase_partials(const RasArgs &a, int items)
+{
+    return reinterpret_cast<float *>(a.scratch + (size_t)items * 36 * (size_t)a.dg.nloc);
+}
+
+__device__ __forceinline__ float2 *phase_alpha(const RasArgs &a, int items, int nblk)
+{
+    const size_t off = ((size_t)items * nblk * 3 + 3) & ~(size_t)3;
+    return reinterpret_cast<float2 *>(phase_partials(a, items) + off);
+}
+
+template <int P>
+__device__ __forceinline__ bool phase_item(RasArgs &a, int item, int &dom, int &rr)
+{
+    rr = item % a.nrhs;
+    dom = item / a.nrhs;
+    if (a.sc && a.sc[rr].status != S_RUN) return false;
+    a.in = rhs_view<P>(a.in, a.g.V, rr);
+    a.vout = rhs_view<P>(a.vout, a.g.V, rr);
+    a.acc = rhs_view<P>(a.acc, a.g.V, rr);
+    if (a.asum) a.asum += (long long)rr * 6 * a.g.V;
+    return true;
+}
+
+template <int P>
+__global__ void __launch_bounds__(RAS_PH_NT) ras_phase_stage(RasArgs a, PhaseGrid pg)
+{
+    const int item = blockIdx.x / pg.nblk, chunk = blockIdx.x % pg.nblk;
+    int dom, rr;
+    if (!phase_item<P>(a, item, dom, rr) || skip_domain(a, dom)) return;
+    const int n = a.dg.nloc, l = chunk * RAS_PH_NT + threadIdx.x;
+    if (l >= n) return;
+    float2 *rho = phase_slot(a, item), *v = rho + 24 * (size_t)n;
+    DomSite ds;
+    dom_site(a.g, a.dg, dom, l, a.kappa, ds);
+    C<float> r[12], z[12];
+    load_spinor<P>(a.in, a.g.V, ds.x, r);
+#pragma unroll
+    for (int k = 0; k < 12; k++) z[k] = {0.f, 0.f};
+    st_local(rho, n, l, r);
+    st_local(v, n, l, z);
+}
+
+template <int P>
+__global__ void __launch_bounds__(RAS_PH_NT) ras_phase_apply(RasArgs a, PhaseGrid pg, int items)
+{
+    __shared__ double sm[3 * 32];
+    const int item = blockIdx.x / pg.nblk, chunk = blockIdx.x % pg.nblk;
+    int dom, rr;
+    if (!phase_item<P>(a, item, dom, rr) || skip_domain(a, dom)) return;  // uniform over the CTA
+    const int n = a.dg.nloc, l = chunk * RAS_PH_NT + threadIdx.x;
+    float2 *rho = phase_slot(a, item), *q = rho + 12 * (size_t)n;
+    float part[3] = {0.f, 0.f, 0.f};
+    if (l < n) {
+        DomSite ds;
+        dom_site(a.g, a.dg, dom, l, a.kappa, ds);
+        C<float> own[12], qq[12];
+        ld_local(rho, n, l, own);
+        dom_apply<P>(a, ds, own, rho, n, qq);
+        st_local(q, n, l, qq);
+#pragma unroll
+        for (int k = 0; k < 12; k++) {
+            cdot_acc(qq[k], own[k], part[0], part[1]);
+            cnorm_acc(qq[k], part[2]);
+        }
+    }
+    double red[3];
+    block_sum<3, float>(part, red, sm);
+    if (threadIdx.x == 0) {
+        float *pp = phase_partials(a, items) + ((size_t)item * pg.nblk + chunk) * 3;
+        pp[0] = (float)red[0];
+        pp[1] = (float)red[1];
+        pp[2] = (float)red[2];
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(RAS_PH_NT) ras_phase_alpha(RasArgs a, PhaseGrid pg, int items)
+{
+    __shared__ double sm[3 * 32 + 3];
+    const int item = blockIdx.x;
+    int dom, rr;
+    if (!phase_item<P>(a, item, dom, rr) || skip_domain(a, dom)) return;
+    const float *pp = phase_partials(a, items) + (size_t)item * pg.nblk * 3;
+    double red[3] = {0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < pg.nblk; b += RAS_PH_NT) {
+        red[0] += pp[3 * b];
+        red[1] += pp[3 * b + 1];
+        red[2] += pp[3 * b + 2];
+    }
+    block_sum<3>(red, sm);
+    if (threadIdx.x == 0) {
+        float2 *alpha = phase_alpha(a, items, pg.nblk);
+        alpha[item] = red[2] > 0.0 ? make_float2((float)(red[0] / red[2]), (float)(red[1] / red[2]))
+                                   : make_float2(0.f, 0.f);
+    }
+}
+
+template <int P>
+__global__ void __launch_bounds__(RAS_PH_NT) ras_phase_update(RasArgs a, PhaseGrid pg, int items)
+{
+    const int item = blockIdx.x / pg.nblk, chunk = blockIdx.x % pg.nblk;
+    int dom, rr;
+    if (!phase_item<P>(a, item, dom, rr) || skip_domain(a, dom)) return;
+    const int n = a.dg.nloc, l = chunk * RAS_PH_NT + threadIdx.x;
+    if (l >= n) return;
+    const float2 al2 = phase_alpha(a, items, pg.nblk)[item];
+    const C<float> al = {al2.x, al2.y};
+    float2 *rho = phase_slot(a, item), *q = rho + 12 * (size_t)n, *v = rho + 24 * (size_t)n;
+    C<float> r[12], qq[12], vv[12];
+    ld_local(rho, n, l, r);
+    ld_local(q, n, l, qq);
+    ld_local(v, n, l, vv);
+#pragma unroll
+    for (int k = 0; k < 12; k++) {
+        vv[k] = cfma(al, r[k], vv[k]);
+        r[k] = cfma(cneg(al), qq[k], r[k]);
+    }
+    st_local(v, n, l, vv);
+    st_local(rho, n, l, r);
+}
+
+template <int P>
+__global__ void __launch_bounds__(RAS_PH_NT) ras_phase_output(RasArgs a, PhaseGrid pg)
+{
+    const int item = blockIdx.x / pg.nblk, chunk = blockIdx.x % pg.nblk;
+    int dom, rr;
+    if (!phase_item<P>(a, item, dom, rr)) return;
+    const int n = a.dg.nloc, l = chunk * RAS_PH_NT + threadIdx.x;
+    if (l >= n) return;
+    DomSite ds;
+    dom_site(a.g, a.dg, dom, l, a.kappa, ds);
+    if (skip_domain(a, dom)) {
+        if (ds.bulk) zero_outputs<P>(a, ds.x);
+        return;
+    }
+    const float2 *v = phase_slot(a, item) + 24 * (size_t)n;
+    if (a.asum) {
+        C<float> vv[12];
+        ld_local(v, n, l, vv);
+        as_add(a, ds.x, vv);
+    } else if (ds.bulk) {
+        C<float> vv[12];
+        ld_local(v, n, l, vv);
+        write_outputs<P>(a, ds.x, vv);
+    }
+}
+
+// The phased sweep is used when the domains (times right-hand sides) are
+// too few to fill the GPU with one CTA each.
+bool ras_use_phased(const DomainGeom &dg, int nrhs)
+{
+    return dg.nloc > RAS_SMEM_MAX_SITES && (long long)dg.ndom * nrhs < 2 * 152 && !ras_cluster_shape(dg);
+}
+
+size_t ras_phased_scratch_bytes(const DomainGeom &dg, int nrhs)
+{
+    const long long items = (long long)dg.ndom * nrhs;
+    const long long nblk = (dg.nloc + RAS_PH_NT - 1) / RAS_PH_NT;
+    return (size_t)items * 36 * (size_t)dg.nloc * sizeof(float2) +
+           (size_t)((items * nblk * 3 + 3) & ~3LL) * sizeof(float) + (size_t)items * sizeof(float2);
+}
+
+template <int P>
+static cudaError_t launch_phased(const RasArgs &a, cudaStream_t st)
+{
+    if (a.fuse != RAS_FUSE_NONE || !a.scratch) return cudaErrorInvalidValue;
+    const int items = a.dg.ndom * a.nrhs;
+    PhaseGrid pg;
+    pg.nblk = (a.dg.nloc + RAS_PH_NT - 1) / RAS_PH_NT;
+    const unsigned grid = (unsigned)((long long)items * pg.nblk);
+    ras_phase_stage<P><<<grid, RAS_PH_NT, 0, st>>>(a, pg);
+    note_launch();
+    for (int it = 0; it < a.n_iter; it++) {
+        ras_phase_apply<P><<<grid, RAS_PH_NT, 0, st>>>(a, pg, items);
+        ras_phase_alpha<P><<<items, RAS_PH_NT, 0, st>>>(a, pg, items);
+        ras_phase_update<P><<<grid, RAS_PH_NT, 0, st>>>(a, pg, items);
+        note_launch(3);
+    }
+    ras_phase_output<P><<<grid, RAS_PH_NT, 0, st>>>(a, pg);
+    note_launch();
+    return cudaGetLastError();
+}
+
 template <int P, int NT, bool SC, bool EXP = false>
 static cudaError_t launch_smem(const RasArgs &a, cudaStream_t st)
 {
@@ -1376,6 +1589,9 @@ static cudaError_t launch_p(const RasArgs &a, cudaStream_t st)
             if (ok || e != cudaSuccess) return e;
         }
     }
+    if constexpr (P == P16 || P == P32) {
+        if (a.variant != 3 && ras_use_phased(a.dg, a.nrhs)) return launch_phased<P>(a, st);
+    }
     // the general kernel has no fused update (the caller checks ras_can_fuse)
     if (a.fuse != RAS_FUSE_NONE || !a.scratch || a.slots < 1) return cudaErrorInvalidValue;
     const long long items = (long long)a.dg.ndom * a.nrhs;
@@ -1427,7 +1643,13 @@ size_t ras_scratch_bytes(const DomainGeom &dg, int slots, int nrhs)
     if (dg.nloc <= RAS_SMEM_MAX_SITES) return 0;
     const long long items = (long long)dg.ndom * nrhs;
     const int s = slots < items ? slots : (int)items;
-    return (size_t)s * 36 * (size_t)dg.nloc * sizeof(float2);
+    const size_t gmem = (size_t)s * 36 * (size_t)dg.nloc * sizeof(float2);
+    // the phased sweep needs a slot per item plus its partial sums
+    if (ras_use_phased(dg, nrhs)) {
+        const size_t ph = ras_phased_scratch_bytes(dg, nrhs);
+        return ph > gmem ? ph : gmem;
+    }
+    return gmem;
 }
 
 bool domain_geom(const Geom &g, const int block[4], int s, DomainGeom *dg, std::string *why)
