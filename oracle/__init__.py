@@ -19,6 +19,9 @@ the paper it follows (Osaki & Ishikawa, Lattice 2010):
 * ``solve_nested`` the same with the paper's FP64 outer BiCGStab (Sec. 3).
 
 Parity status of every function is pinned by ``tests/test_oracle_pins.py``.
+``oracle/slab.py`` runs the paper's cluster decomposition (one x-slab domain
+per rank, Sec. 4) on CPU ranks with these functions as its per-site pieces
+(``tests/test_slab_ranks.py``).
 """
 
 from __future__ import annotations
