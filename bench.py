@@ -549,6 +549,9 @@ def run_workload(args):
                blocks, N_dominv 4, FP16 inner, 1..3 cycles, d in {0, 2} (AS:
                one cycle, d in {2, 4}, as AS with d = 0 is RAS), each solve
                timed once after an untimed one;
+      blocks -- the 32^4 workload over the RAS block shapes 8^4, 4^4, 8x4^3,
+               overlap s = 0, 1, 2 (d = 0, 2, 4) and FP32 / FP16 inner solves,
+               NRAS 1, N_dominv 4, each solve timed once after an untimed one;
       outer -- the 32^4 workload solved with FP64 defect correction and with
                the paper's FP64 outer BiCGStab (Sec. 3) around the same inner
                solve (4^4 blocks, NRAS 1, N_dominv 4), inner tolerance 1e-1,
@@ -681,6 +684,35 @@ def run_workload(args):
                "equal_cost": "a cycle solves every domain once in each variant (SAP: red then black); "
                              "domain_solves_per_site counts them over the whole solve",
                "best": best, "grid": grid}
+    elif args.workload == "blocks":
+        U = synth.gauge_field(DIMS, EPS, GSEED)
+        eta = synth.gaussian_source(DIMS, SSEED)
+        st = torch.cuda.Stream()
+        lat = qdd.create_lattice(DIMS, BC, stream=st)
+        qdd.load_gauge(lat, torch.from_numpy(U).cuda())
+        d_eta = torch.from_numpy(eta).cuda()
+        d_phi = torch.empty_like(d_eta)
+        op = oracle.Op(DIMS, BC, U, KAPPA, CSW, store_clover=False)
+        grid = []
+        for blk in ((8, 8, 8, 8), (4, 4, 4, 4), (8, 4, 4, 4)):
+            for ov in (0, 1, 2):
+                for prec in ("f32", "f16"):
+                    p = qdd.default_params(inner_prec=prec, block=blk, overlap=ov, n_ras=1, n_dominv=4,
+                                           max_inner=400, max_outer=12)
+                    qdd.solve(lat, d_phi, d_eta, KAPPA, CSW, TOL, p, raise_on_failure=False)  # untimed
+                    ms, infos = time_steps(torch, st, lambda: qdd.solve(lat, d_phi, d_eta, KAPPA, CSW, TOL, p,
+                                                                        raise_on_failure=False), 1)
+                    i = infos[0]
+                    res = op.true_residual(eta, d_phi.cpu().numpy())
+                    ok = i["status"] == 0 and res <= TOL
+                    grid.append({"block": list(blk), "d": 2 * ov, "inner_prec": prec, "ms": round(ms, 2) if ok else None,
+                                 "inner_iters": i["inner_iters"], "dv_count": i["dv_count"],
+                                 "oracle_true_rel_residual": res})
+        done = [g for g in grid if g["ms"] is not None]
+        rec = {"workload": "blocks",
+               "metric": "32^4 solve time to 1e-10 over RAS block shapes 8^4, 4^4, 8x4^3, d = 0, 2, 4, FP32 and FP16 inner",
+               "unit": "ms", "ras": {"n_ras": 1, "n_dominv": 4}, "best": min(done, key=lambda g: g["ms"]),
+               "converged": len(done), "points": len(grid), "grid": grid}
     elif args.workload == "outer":
         U = synth.gauge_field(DIMS, EPS, GSEED)
         eta = synth.gaussian_source(DIMS, SSEED)
@@ -869,11 +901,13 @@ def main():
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
                     help="use --block/--overlap/--n-dominv/--n-ras as given instead of tuning them")
     ap.add_argument("--tune-trials", dest="tune_trials", type=int, default=42)
-    ap.add_argument("--workload", choices=("solve", "mrhs", "batch", "survey", "table1", "schwarz", "outer"),
+    ap.add_argument("--workload", choices=("solve", "mrhs", "batch", "survey", "table1", "schwarz", "outer",
+                                           "blocks"),
                     default="solve",
                     help="solve: the 32^4 headline; mrhs / batch: the batched workloads; survey: the Sec. 5 "
                          "parameter survey; table1: the paper's slab-domain experiment emulated; schwarz: RAS, "
-                         "SAP and AS compared as the preconditioner; outer: defect correction vs outer BiCGStab")
+                         "SAP and AS compared as the preconditioner; outer: defect correction vs outer BiCGStab; "
+                         "blocks: block shapes x overlaps x inner precisions")
     ap.add_argument("--kernels", default=None,
                     help="profiler workload: dslash:f16|f32|f64, ras:f16|f32[:s] or clover, three launches at 32^4")
     args = ap.parse_args()
