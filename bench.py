@@ -842,15 +842,18 @@ def run_workload(args):
 
 def run_kernels(spec):
     """Kernel microbenchmark for profilers: builds the 32^4 workload and runs
-    one kernel a few times -- dslash:<prec>, ras:<prec>[:<s>] (one RAS sweep of
-    4^4 blocks, N_dominv = 4, extension s, default 0: s = 1, 2 run the
-    thread-block-cluster sweep) or clover (the clover build)."""
+    one kernel a few times -- dslash:<prec>, ras:<prec>[:<s>[:<bx>x<by>x<bz>x<bt>]]
+    (one RAS sweep, N_dominv = 4, extension s, default 0, blocks default 4^4:
+    s = 1, 2 run the thread-block-cluster sweep, 4x32x32x32 slabs the phased
+    sweep) or clover (the clover build)."""
     import torch
 
     import synth
     from paper_1011_3318_gb300 import qdd
     kind, _, prec = spec.partition(":")
     prec, _, ext = prec.partition(":")
+    ext, _, blk = ext.partition(":")
+    block = tuple(int(b) for b in blk.split("x")) if blk else (4, 4, 4, 4)
     U = synth.gauge_field(DIMS, EPS, GSEED)
     eta = synth.gaussian_source(DIMS, SSEED)
     lat = qdd.create_lattice(DIMS, BC)
@@ -864,7 +867,7 @@ def run_kernels(spec):
         for _ in range(3):
             qdd.dslash_field(lat, b, a, KAPPA, CSW)
     elif kind == "ras":
-        p = qdd.default_params(inner_prec=prec, n_ras=1, n_dominv=4, overlap=int(ext or 0))
+        p = qdd.default_params(inner_prec=prec, n_ras=1, n_dominv=4, overlap=int(ext or 0), block=block)
         for _ in range(3):
             qdd.ras_apply(lat, out, deta, KAPPA, CSW, p)
         # then the sweep alone, timed by the library's per-class CUDA events
@@ -909,7 +912,8 @@ def main():
                          "SAP and AS compared as the preconditioner; outer: defect correction vs outer BiCGStab; "
                          "blocks: block shapes x overlaps x inner precisions")
     ap.add_argument("--kernels", default=None,
-                    help="profiler workload: dslash:f16|f32|f64, ras:f16|f32[:s] or clover, three launches at 32^4")
+                    help="profiler workload: dslash:f16|f32|f64, ras:f16|f32[:s[:bxxbyxbzxbt]] or clover, three launches "
+                         "at 32^4")
     args = ap.parse_args()
     if args.kernels:
         return run_kernels(args.kernels)
