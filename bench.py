@@ -549,6 +549,9 @@ def run_workload(args):
                blocks, N_dominv 4, FP16 inner, 1..3 cycles, d in {0, 2} (AS:
                one cycle, d in {2, 4}, as AS with d = 0 is RAS), each solve
                timed once after an untimed one;
+      small -- the 8^4 plain FP64 configuration and the 16^4 FP32-inner
+               configuration without and with RAS (4^4, N_dominv 4, NRAS 3):
+               time, iterations, global D count and sweeps, 3 timed solves;
       blocks -- the 32^4 workload over the RAS block shapes 8^4, 4^4, 8x4^3,
                overlap s = 0, 1, 2 (d = 0, 2, 4) and FP32 / FP16 inner solves,
                NRAS 1, N_dominv 4, each solve timed once after an untimed one;
@@ -684,6 +687,33 @@ def run_workload(args):
                "equal_cost": "a cycle solves every domain once in each variant (SAP: red then black); "
                              "domain_solves_per_site counts them over the whole solve",
                "best": best, "grid": grid}
+    elif args.workload == "small":
+        # the two small configurations: 8^4 plain FP64 BiCGStab (kappa 0.12),
+        # and 16^4 FP32 inner + FP64 defect correction without and with RAS
+        # (4^4, s = 0, N_dominv 4, NRAS 3, inner tol 1e-3), kappa 0.12
+        runs = {}
+        for name, dims, kw in (("8^4 plain FP64", (8, 8, 8, 8), dict(inner_prec="f64")),
+                               ("16^4 FP32 inner, no RAS", (16, 16, 16, 16), dict(inner_prec="f32", use_ras=0)),
+                               ("16^4 FP32 inner, RAS 4^4", (16, 16, 16, 16),
+                                dict(inner_prec="f32", block=(4, 4, 4, 4), n_ras=3, n_dominv=4))):
+            U = synth.gauge_field(dims, EPS, GSEED)
+            eta = synth.gaussian_source(dims, SSEED)
+            st = torch.cuda.Stream()
+            lat = qdd.create_lattice(dims, BC, stream=st)
+            qdd.load_gauge(lat, torch.from_numpy(U).cuda())
+            d_eta = torch.from_numpy(eta).cuda()
+            d_phi = torch.empty_like(d_eta)
+            p = qdd.default_params(inner_tol=1e-3, **kw)
+            qdd.solve(lat, d_phi, d_eta, 0.12, CSW, TOL, p)  # untimed
+            ms, infos = time_steps(torch, st, lambda: qdd.solve(lat, d_phi, d_eta, 0.12, CSW, TOL, p), 3)
+            i = infos[-1]
+            op = oracle.Op(dims, BC, U, 0.12, CSW, store_clover=False)
+            runs[name] = {"ms": round(ms, 3), "outer_iters": i["outer_iters"], "inner_iters": i["inner_iters"],
+                          "dv_count": i["dv_count"], "ras_sweeps": i["ras_sweeps"],
+                          "oracle_true_rel_residual": op.true_residual(eta, d_phi.cpu().numpy())}
+            qdd.destroy_lattice(lat)
+        rec = {"workload": "small", "metric": "time to 1e-10 on the 8^4 and 16^4 configurations",
+               "unit": "ms", "runs": runs}
     elif args.workload == "blocks":
         U = synth.gauge_field(DIMS, EPS, GSEED)
         eta = synth.gaussian_source(DIMS, SSEED)
@@ -905,12 +935,12 @@ def main():
                     help="use --block/--overlap/--n-dominv/--n-ras as given instead of tuning them")
     ap.add_argument("--tune-trials", dest="tune_trials", type=int, default=42)
     ap.add_argument("--workload", choices=("solve", "mrhs", "batch", "survey", "table1", "schwarz", "outer",
-                                           "blocks"),
+                                           "blocks", "small"),
                     default="solve",
                     help="solve: the 32^4 headline; mrhs / batch: the batched workloads; survey: the Sec. 5 "
                          "parameter survey; table1: the paper's slab-domain experiment emulated; schwarz: RAS, "
                          "SAP and AS compared as the preconditioner; outer: defect correction vs outer BiCGStab; "
-                         "blocks: block shapes x overlaps x inner precisions")
+                         "blocks: block shapes x overlaps x inner precisions; small: the 8^4 and 16^4 configurations")
     ap.add_argument("--kernels", default=None,
                     help="profiler workload: dslash:f16|f32|f64, ras:f16|f32[:s[:bxxbyxbzxbt]] or clover, three launches "
                          "at 32^4")
