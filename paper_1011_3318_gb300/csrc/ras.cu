@@ -1123,7 +1123,10 @@ __global__ void __launch_bounds__(RAS_GMEM_NT) ras_gmem_kernel(const RasArgs a0)
 // finally the restriction.  rho, q and v live in a global-scratch slot per
 // (domain, right-hand side) as for ras_gmem_kernel; kernel boundaries order
 // the iterations.  Items are (domain, right-hand side) pairs, right-hand side
-// fastest; a domain's CTAs are consecutive.
+// fastest; CTA b works on chunk b / items of item b % items, so that the CTAs
+// running together cover the same local sites of every domain: neighbouring
+// slabs share the cache lines of the fields (a 4-site-wide slab uses half of
+// each 128-byte line of a plane), which are then fetched once.
 
 constexpr int RAS_PH_NT = 256;
 
@@ -1165,7 +1168,8 @@ __device__ __forceinline__ bool phase_item(RasArgs &a, int item, int &dom, int &
 template <int P>
 __global__ void __launch_bounds__(RAS_PH_NT) ras_phase_stage(RasArgs a, PhaseGrid pg)
 {
-    const int item = blockIdx.x / pg.nblk, chunk = blockIdx.x % pg.nblk;
+    const int items = gridDim.x / pg.nblk;
+    const int item = blockIdx.x % items, chunk = blockIdx.x / items;
     int dom, rr;
     if (!phase_item<P>(a, item, dom, rr) || skip_domain(a, dom)) return;
     const int n = a.dg.nloc, l = chunk * RAS_PH_NT + threadIdx.x;
@@ -1185,7 +1189,7 @@ template <int P>
 __global__ void __launch_bounds__(RAS_PH_NT) ras_phase_apply(RasArgs a, PhaseGrid pg, int items)
 {
     __shared__ double sm[3 * 32];
-    const int item = blockIdx.x / pg.nblk, chunk = blockIdx.x % pg.nblk;
+    const int item = blockIdx.x % items, chunk = blockIdx.x / items;
     int dom, rr;
     if (!phase_item<P>(a, item, dom, rr) || skip_domain(a, dom)) return;  // uniform over the CTA
     const int n = a.dg.nloc, l = chunk * RAS_PH_NT + threadIdx.x;
@@ -1239,7 +1243,7 @@ __global__ void __launch_bounds__(RAS_PH_NT) ras_phase_alpha(RasArgs a, PhaseGri
 template <int P>
 __global__ void __launch_bounds__(RAS_PH_NT) ras_phase_update(RasArgs a, PhaseGrid pg, int items)
 {
-    const int item = blockIdx.x / pg.nblk, chunk = blockIdx.x % pg.nblk;
+    const int item = blockIdx.x % items, chunk = blockIdx.x / items;
     int dom, rr;
     if (!phase_item<P>(a, item, dom, rr) || skip_domain(a, dom)) return;
     const int n = a.dg.nloc, l = chunk * RAS_PH_NT + threadIdx.x;
@@ -1263,7 +1267,8 @@ __global__ void __launch_bounds__(RAS_PH_NT) ras_phase_update(RasArgs a, PhaseGr
 template <int P>
 __global__ void __launch_bounds__(RAS_PH_NT) ras_phase_output(RasArgs a, PhaseGrid pg)
 {
-    const int item = blockIdx.x / pg.nblk, chunk = blockIdx.x % pg.nblk;
+    const int items = gridDim.x / pg.nblk;
+    const int item = blockIdx.x % items, chunk = blockIdx.x / items;
     int dom, rr;
     if (!phase_item<P>(a, item, dom, rr)) return;
     const int n = a.dg.nloc, l = chunk * RAS_PH_NT + threadIdx.x;
