@@ -367,6 +367,68 @@ def test_ras_sweeps_converge_to_inverse(small_system):
     assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-3
 
 
+def mr_dense(M, r, n):
+    """Minimal residual from zero on a dense matrix, n steps (the domain
+    solver's definition written with numpy): q = M rho, alpha = <q, rho>/<q, q>,
+    v += alpha rho, rho -= alpha q."""
+    v = np.zeros_like(r)
+    rho = r.copy()
+    for _ in range(n):
+        q = M @ rho
+        qq = np.vdot(q, q).real
+        if qq == 0:
+            break
+        a = np.vdot(q, rho) / qq
+        v = v + a * rho
+        rho = rho - a * q
+    return v
+
+
+def test_mr_domain_solver_matches_dense_mr(oracle_mod):
+    """N_dominv MR steps of the oracle's domain solve equal the same steps on
+    the dense Dirichlet matrix, for several step counts (an off-by-one in the
+    iteration count or a swapped inner product fails)."""
+    dims, block, s = (6, 6, 2, 2), (2, 2, 2, 2), 1
+    op = oracle_mod.Op(dims, BC_AP, synth.gauge_field(dims, 0.3, 95), 0.12, 1.0)
+    for dom in (0, 4):
+        sites, _ = op.domain_sites(block, s, dom)
+        n = sites.size * 12
+        Dd = dense(lambda v: op.domain_apply(block, s, dom, v.reshape(-1, 4, 3)), n)
+        r = synth.gaussian_source((sites.size, 1, 1, 1), 96 + dom)
+        for k in (2, 3, 5):
+            got = op.domain_solve(block, s, dom, r, n_dominv=k)
+            assert rel(got.reshape(-1), mr_dense(Dd, r.reshape(-1), k)) < 1e-12
+
+
+@pytest.mark.parametrize("s", [0, 1])
+def test_ras_with_mr_domain_solves_matches_dense_alg1(oracle_mod, s):
+    """Alg. 1 with the MR domain solver (a non-linear map, so Eq. 2 does not
+    apply) written densely with numpy: per sweep, every domain's MR on its
+    Dirichlet matrix, restricted to the bulk and summed, then phi += v and
+    r -= D v."""
+    dims, block = (6, 6, 2, 2), (2, 2, 2, 2)
+    op = oracle_mod.Op(dims, BC_AP, synth.gauge_field(dims, 0.3, 97), 0.12, 1.0)
+    Dm = dense(lambda v: op.dslash(v.reshape(op.V, 4, 3)), op.V * 12)
+    doms = []
+    for dom in range(op.ndomains(block, s)):
+        sites, bulk = op.domain_sites(block, s, dom)
+        idx = (sites[:, None] * 12 + np.arange(12)[None]).reshape(-1)
+        doms.append((idx, np.repeat(bulk, 12), Dm[np.ix_(idx, idx)]))
+    eta = synth.gaussian_source(dims, 98).reshape(-1)
+    for n_ras, n_dominv in ((1, 3), (2, 3), (3, 2)):
+        phi = np.zeros_like(eta)
+        r = eta.copy()
+        for _ in range(n_ras):
+            v = np.zeros_like(eta)
+            for idx, keep, M in doms:
+                vl = mr_dense(M, r[idx], n_dominv)
+                v[idx[keep]] += vl[keep]
+            phi = phi + v
+            r = r - Dm @ v
+        got = op.ras(eta.reshape(op.V, 4, 3), block, s=s, n_ras=n_ras, n_dominv=n_dominv)
+        assert rel(got.reshape(-1), phi) < 1e-12
+
+
 # ---------------------------------------------------------------- Schwarz variants
 def block_color(dims, block, dom):
     """Red/black colour of a domain: parity of the sum of its block coordinates."""
