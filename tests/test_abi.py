@@ -30,6 +30,29 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_header_is_plain_c(tmp_path, libpath):
+    """The boundary is a C ABI: the header compiles as C99 and as C++ with
+    no CUDA or torch headers, and a C program linked against the library
+    runs its host-side calls."""
+    src = tmp_path / "use.c"
+    src.write_text('#include "qdd.h"\n'
+                   'int main(void) { qdd_solver_params p; qdd_default_params(&p);\n'
+                   '  return p.schwarz == QDD_SCHWARZ_RAS && p.outer_mode == 0 ? 0 : 1; }\n')
+    inc = os.path.join(ROOT, "include")
+    for cc, std in (("gcc", "-std=c99"), ("g++", "-std=c++11")):
+        args = [cc, std, "-Wall", "-Wextra", "-Werror", "-fsyntax-only", "-I", inc]
+        if cc == "g++":
+            args += ["-x", "c++"]
+        p = subprocess.run(args + [str(src)], capture_output=True, text=True)
+        assert p.returncode == 0, p.stderr
+    libdir = os.path.dirname(libpath)
+    exe = tmp_path / "use"
+    p = subprocess.run(["gcc", "-std=c99", "-I", inc, str(src), "-L", libdir, "-lqdd", "-Wl,-rpath," + libdir,
+                        "-o", str(exe)], capture_output=True, text=True)
+    assert p.returncode == 0, p.stderr
+    assert subprocess.run([str(exe)], timeout=60).returncode == 0
+
+
 def test_library_exports_every_declared_symbol(libpath):
     out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
     exported = set(re.findall(r"\bT (qdd_[a-z_0-9]+)", out))
