@@ -519,6 +519,20 @@ def test_sap_and_as_match_dense_schwarz_operators(schwarz_system, s):
         assert rel(add.reshape(-1), stationary(Dm, [S_as], e, ncyc)) < 1e-11
 
 
+def test_sap_with_an_odd_block_count(oracle_mod):
+    """Three blocks in x: domains 0 and 2 have the same colour and touch across
+    the periodic wrap; a half-sweep then solves them additively, which the
+    colour sums S_c express."""
+    dims, block = (6, 4, 2, 2), (2, 2, 2, 2)
+    op = oracle_mod.Op(dims, BC_AP, synth.gauge_field(dims, 0.3, 305), 0.12, 1.0)
+    Dm = dense(lambda v: op.dslash(v.reshape(op.V, 4, 3)), op.V * 12)
+    eta = synth.gaussian_source(dims, 306)
+    sweeps = [dense_domain_sweep(op, block, 0, True, c) for c in (0, 1)]
+    for ncyc in (1, 2):
+        sap = op.ras(eta, block, s=0, n_ras=ncyc, exact=True, schwarz="sap")
+        assert rel(sap.reshape(-1), stationary(Dm, sweeps, eta.reshape(-1), ncyc)) < 1e-11
+
+
 def test_as_without_overlap_is_ras(schwarz_system):
     """With d = 0 the extended domains are the bulk blocks: AS and RAS coincide
     (the restriction removes nothing)."""
