@@ -242,6 +242,27 @@ def test_plain_bicgstab_matches_dense_solve(small_system):
     assert op.true_residual(eta, phi) < 1e-12
 
 
+def test_true_residual_matches_dense_residual(small_system):
+    """The checker behind every solve's "<= 1e-10" (the Sec. 5 stopping rule
+    |eta - D phi| / |eta|) against the residual of the dense matrix computed
+    with numpy, for a random phi, a near-solution and the LAPACK solution;
+    phi = 0 gives exactly 1 and the ratio is invariant under a common scale
+    (a missing square root or a wrong normalisation fails here)."""
+    op, Dm, eta, x = small_system
+    rng = np.random.default_rng(53)
+    e = eta.reshape(-1)
+    rnd = (rng.standard_normal(e.size) + 1j * rng.standard_normal(e.size)).reshape(op.V, 4, 3)
+    near = x + 1e-6 * rnd
+    for phi in (rnd, near, x):
+        want = np.linalg.norm(e - Dm @ phi.reshape(-1)) / np.linalg.norm(e)
+        got = op.true_residual(eta, phi)
+        assert abs(got - want) <= 1e-14 * max(want, 1e-300) + 1e-16, (got, want)
+    assert 1e-9 < op.true_residual(eta, near) < 1e-4
+    assert op.true_residual(eta, x) < 1e-13
+    assert op.true_residual(eta, np.zeros_like(eta)) == pytest.approx(1.0, abs=1e-15)
+    assert op.true_residual(3.0 * eta, 3.0 * near) == pytest.approx(op.true_residual(eta, near), rel=1e-12)
+
+
 def test_nested_solve_matches_dense_solve(small_system):
     op, Dm, eta, x = small_system
     phi, info = op.solve(eta, 1e-11, inner_tol=1e-3, ras=dict(block=(2, 2, 2, 2), s=0, n_ras=3, n_dominv=4))
@@ -314,6 +335,35 @@ def test_mr_domain_solver_properties(oracle_mod):
         res.append(np.linalg.norm(r - op.domain_apply(block, s, 3, v)))
     assert all(res[k + 1] <= res[k] * (1 + 1e-12) for k in range(len(res) - 1))
     assert res[-1] < 1e-6 * res[0]
+
+
+def test_mr_steps_minimise_the_residual_along_their_direction(oracle_mod):
+    """Each MR step of the domain solve (Alg. 1 line 5 read as minimal
+    residual) moves v along the current residual rho_k = r - D v_k with the
+    complex step that minimises |rho_k - alpha D rho_k|: the step taken by
+    the oracle is parallel to rho_k, and moving its coefficient by 1e-3 in
+    the real or the imaginary direction makes the new residual larger (a
+    conjugated or mis-normalised alpha fails).  No MR formula is restated."""
+    dims, block, s, dom = (4, 4, 4, 4), (2, 2, 2, 2), 0, 5
+    op = oracle_mod.Op(dims, BC_AP, synth.gauge_field(dims, 0.3, 73), 0.12, 1.0)
+    r = synth.gaussian_source((16, 1, 1, 1), 74)
+    v_prev = np.zeros_like(r)
+    for k in range(4):
+        v_next = op.domain_solve(block, s, dom, r, n_dominv=k + 1)
+        rho = r - op.domain_apply(block, s, dom, v_prev)
+        step = (v_next - v_prev).reshape(-1)
+        rf = rho.reshape(-1)
+        alpha = np.vdot(rf, step) / np.vdot(rf, rf)
+        assert np.linalg.norm(step - alpha * rf) <= 1e-12 * np.linalg.norm(step)
+        q = op.domain_apply(block, s, dom, rho).reshape(-1)
+        best = np.linalg.norm(rf - alpha * q)
+        assert best < np.linalg.norm(rf)
+        for d in (1e-3, -1e-3, 1e-3j, -1e-3j):
+            assert np.linalg.norm(rf - (alpha + d * abs(alpha)) * q) > best * (1 + 1e-9)
+        # a conjugated coefficient is not the minimiser
+        if abs(alpha.imag) > 1e-6 * abs(alpha):
+            assert np.linalg.norm(rf - np.conj(alpha) * q) > best * (1 + 1e-9)
+        v_prev = v_next
 
 
 def test_ras_equals_eq2_with_exact_domain_solves(oracle_mod):
