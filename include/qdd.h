@@ -143,21 +143,29 @@ typedef struct {
     int status;                 /* qdd_status of the solve */
     double true_rel_residual;   /* |eta - D phi| / |eta| with the FP64 D */
     double t_total_ms;          /* wall time of the call */
-    double t_outer_ms;          /* FP64 residuals, conversions and accumulation */
-    double t_inner_ms;          /* inner solves */
+    double t_outer_ms;          /* FP64 residuals, conversions and accumulation (outer level, Sec. 3) */
+    double t_inner_ms;          /* inner solves (inner level, Sec. 3) */
+    /* Time per kernel class (D, RAS sweeps, BLAS) is not kept here: with
+     * qdd_set_profiling on, qdd_profile_read returns it, measured with CUDA
+     * events on the lattice's stream. */
 } qdd_solve_info;
 
 /* Library version string. */
 const char *qdd_version(void);
 
-/* Description of the last error on the calling thread ("" if none). */
+/* Description of the last error on the calling thread ("" if none).  The
+ * paper defines no error reporting; every failure of the calls below, which
+ * implement Eq. 1, Alg. 1 and Sec. 3, is described here. */
 const char *qdd_last_error(void);
 
 /* Fills *p with the defaults listed in qdd_solver_params. */
 void qdd_default_params(qdd_solver_params *p);
 
 /* Creates a lattice of dims[4] = (Lx, Ly, Lz, Lt) sites with boundary signs
- * bc[4] (+1 / -1) on the current CUDA device.  Every spinor the lattice
+ * bc[4] (+1 / -1) on the current CUDA device: the four-dimensional lattice
+ * on which Eq. 1 acts and which Sec. 4 decomposes into domains (the paper's
+ * workload of Sec. 5 is 32^4; its fermion boundary is not stated, the
+ * benchmark takes antiperiodic time, bc = {1, 1, 1, -1}).  Every spinor the lattice
  * works on holds n_rhs (1..QDD_MAX_RHS) right-hand sides, processed together
  * by every kernel (links and clover are read once per site block for all of
  * them).  cuda_stream is a cudaStream_t (NULL: the legacy default stream);
@@ -169,8 +177,9 @@ void qdd_default_params(qdd_solver_params *p);
 qdd_status qdd_create_lattice(qdd_lattice **out, const int dims[4], const int bc[4], int n_rhs,
                               void *cuda_stream);
 
-/* Frees the lattice and everything it owns (fields created from it must be
- * destroyed first).  NULL is accepted. */
+/* Frees the lattice of qdd_create_lattice (the lattice of Eq. 1 and Sec. 4)
+ * and everything it owns (fields created from it must be destroyed first).
+ * NULL is accepted. */
 qdd_status qdd_destroy_lattice(qdd_lattice *lat);
 
 /* Loads the gauge field U (canonical FP64, host or device) and derives the
@@ -257,8 +266,9 @@ qdd_status qdd_dslash_field(qdd_lattice *lat, qdd_field *out, const qdd_field *i
 /* K_RAS of qdd_ras_apply on caller-owned fields, with no device allocation.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot let the library call cudaMalloc when the preconditioner runs --
- * code inside a CUDA stream capture, programs that own all device memory
- * through their own pool, and loops where an allocation would stall the GPU.
+ * programs that own all device memory through their own pool or arena, and
+ * loops where an allocation (or the synchronisation of a cudaFree) would
+ * stall the GPU.
  * out = K_RAS in with params->block, overlap, n_dominv, n_ras and schwarz
  * (RAS or SAP; AS with overlap > 0 needs a summation buffer and is rejected
  * with QDD_ERR_ARG); out, in, rho and v are four different fields of this
@@ -268,12 +278,15 @@ qdd_status qdd_dslash_field(qdd_lattice *lat, qdd_field *out, const qdd_field *i
  * 16 MiB device array inside the library (present on every GPU that loads
  * it, until the process exits): an extended domain may have at most 58254
  * sites (36 * 8 bytes each), and larger ones are rejected with QDD_ERR_ARG.
+ * The lattice's device must be the current device (QDD_ERR_STATE otherwise).
  * The first call on a device looks up that array's device address
  * (cudaGetSymbolAddress); make it before any stream capture begins.  All
  * calls share the array, so calls whose kernels overlap on the GPU race and
  * give wrong results.  Stream-ordered on the lattice's stream; needs a gauge
  * field (QDD_ERR_STATE otherwise); builds the clover term for (kappa, c_sw)
- * if it is not cached, which launches a kernel but allocates nothing. */
+ * if it is not cached, which launches a kernel but allocates nothing; if
+ * that build is due while the lattice's stream is being captured, the call
+ * returns QDD_ERR_STATE and does nothing. */
 qdd_status qdd_ras_field_noalloc(qdd_lattice *lat, qdd_field *out, const qdd_field *in, qdd_field *rho,
                                  qdd_field *v, double kappa, double c_sw, const qdd_solver_params *params);
 

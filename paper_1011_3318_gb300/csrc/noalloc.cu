@@ -1,14 +1,13 @@
 // noalloc.cu -- K_RAS on caller-owned fields without any device allocation.
 //
-// Who needs it: callers that must not allocate device memory at the moment
-// they apply the preconditioner -- code running while a CUDA stream is being
-// captured into a graph (cudaMalloc is not allowed there), host programs that
-// manage all device memory in their own pool or arena and forbid libraries
-// from calling cudaMalloc behind their back, and latency-critical loops where
-// an allocation (and the implicit synchronisation of cudaFree) would stall
-// the device.  qdd_ras_apply allocates its general-kernel scratch on first
-// use with a given blocking; this entry point instead takes the scratch from
-// a fixed array compiled into the library.
+// Who needs it: callers that must not let a library allocate device memory
+// when it applies the preconditioner -- host programs that manage all device
+// memory in their own pool or arena and forbid libraries from calling
+// cudaMalloc behind their back, and latency-critical loops where an
+// allocation (and the implicit synchronisation of cudaFree) would stall the
+// device.  qdd_ras_apply allocates its general-kernel scratch on first use
+// with a given blocking; this entry point instead takes the scratch from a
+// fixed array compiled into the library.
 //
 // The scratch is the file-scope array below: QDD_NOALLOC_SCRATCH_BYTES (16 MiB)
 // on every GPU that loads this library, held until the process exits.  Host
@@ -16,7 +15,7 @@
 // host-side stand-in, not device memory); the device address is obtained once
 // per device with cudaGetSymbolAddress, with that device current, on the
 // first call made on that device.  Make that first call before any stream
-// capture begins.
+// capture begins.  The call must be made with the lattice's device current.
 //
 // Every call shares the one array and overwrites it; the kernel initialises
 // all the scratch it reads (residual and solution of each domain) before
@@ -38,12 +37,18 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[QDD_NOALLOC_SCR
 std::mutex g_mu;
 void *g_scratch_dev[MAX_DEVICES] = {};
 
-// Device address of g_noalloc_scratch on the current device (set up once).
-qdd_status scratch_address(void **out)
+// Device address of g_noalloc_scratch on the lattice's device, which must be
+// the current device (set up once per device).
+qdd_status scratch_address(int lat_device, void **out)
 {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return qdd::cuda_fail(e, "cudaGetDevice");
+    if (dev != lat_device) {
+        qdd::set_error("the current device is not the lattice's device: make device " + std::to_string(lat_device) +
+                       " current before calling");
+        return QDD_ERR_STATE;
+    }
     if (dev < 0 || dev >= MAX_DEVICES) {
         qdd::set_error("device index out of range for the no-allocation scratch");
         return QDD_ERR_ARG;
@@ -112,10 +117,22 @@ extern "C" qdd_status qdd_ras_field_noalloc(qdd_lattice *lat, qdd_field *out, co
                   std::to_string(QDD_NOALLOC_SCRATCH_BYTES / (36 * sizeof(float2))) + " sites per domain)");
         return QDD_ERR_ARG;
     }
-    qdd_status st = ensure_clover(lat, kappa, c_sw);  // a kernel launch, no allocation
-    if (st != QDD_OK) return st;
     void *scratch = nullptr;
-    if ((st = scratch_address(&scratch)) != QDD_OK) return st;
+    qdd_status st = scratch_address(lat->device, &scratch);
+    if (st != QDD_OK) return st;
+    if (lat->has_gauge && !(lat->clover_valid && lat->kappa_c == kappa && lat->csw_c == c_sw)) {
+        // the clover build below would only be recorded, not run, while the
+        // stream is captured, yet the cache would be marked as built
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        cudaError_t e = cudaStreamIsCapturing(lat->stream, &cs);
+        if (e != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+            if (e != cudaSuccess) cudaGetLastError();
+            set_error("the clover term for this kappa and c_sw is not built and the lattice's stream is being "
+                      "captured: make one call with these parameters before the capture");
+            return QDD_ERR_STATE;
+        }
+    }
+    if ((st = ensure_clover(lat, kappa, c_sw)) != QDD_OK) return st;  // a kernel launch, no allocation
 
     RasArgs ra;
     memset(&ra, 0, sizeof(ra));
@@ -149,14 +166,21 @@ extern "C" qdd_status qdd_ras_field_noalloc(qdd_lattice *lat, qdd_field *out, co
         ra.acc = out->view();
         ra.accumulate = j > 0;
         ra.color = sp.colors == 2 ? 1 + j % 2 : 0;
-        cudaError_t e = launch_ras_block_gmem(prec, ra, lat->stream);
+        cudaError_t e;
+        {
+            ProfScope ps(lat, QDD_K_RAS);
+            e = launch_ras_block_gmem(prec, ra, lat->stream);
+        }
         if (e != cudaSuccess) return cuda_fail(e, "RAS block kernel");
         if (!last) {
             // rho = rho_in - D v (no reduction, so no scratch)
             da.out = rho->view();
             da.in = v->view();
             da.y = ra.in;
-            e = launch_dslash(prec, EPI_XMY, da, lat->stream);
+            {
+                ProfScope ps(lat, QDD_K_DSLASH);
+                e = launch_dslash(prec, EPI_XMY, da, lat->stream);
+            }
             if (e != cudaSuccess) return cuda_fail(e, "dslash kernel");
         }
     }

@@ -10,7 +10,7 @@ import pytest
 import torch
 
 import synth
-from gpu_common import qdd, rel  # noqa: F401
+from gpu_common import check_field, qdd, rel  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -46,7 +46,7 @@ def test_cluster_sweep_matches_oracle_and_general_kernel(qdd, oracle_mod, dims, 
     cl = _ras(qdd, lat, eta, **kw)
     gm = _ras(qdd, lat, eta, ras_kernel=3, **kw)
     ref = oracle_mod.Op(dims, bc, U, 0.12, 1.0).ras(eta, block, s=s, n_ras=2, n_dominv=4)
-    assert rel(cl, ref) <= TOL[prec]
+    check_field(cl, ref, TOL[prec], dims, block)
     assert rel(cl, gm) <= TOL_KERNELS[prec]
 
 
@@ -59,7 +59,7 @@ def test_cluster_sweep_schwarz_variants(qdd, oracle_mod, schwarz):
     qdd.load_gauge(lat, U)
     out = _ras(qdd, lat, eta, block=block, overlap=s, n_ras=2, n_dominv=3, inner_prec="f32", schwarz=schwarz)
     ref = oracle_mod.Op(dims, bc, U, 0.12, 1.0).ras(eta, block, s=s, n_ras=2, n_dominv=3, schwarz=schwarz)
-    assert rel(out, ref) <= TOL["f32"]
+    check_field(out, ref, TOL["f32"], dims, block)
 
 
 def test_cluster_sweep_multi_rhs(qdd, oracle_mod):
@@ -71,7 +71,7 @@ def test_cluster_sweep_multi_rhs(qdd, oracle_mod):
     out = _ras(qdd, lat, np.stack(etas), block=block, overlap=s, n_ras=2, n_dominv=4, inner_prec="f16")
     op = oracle_mod.Op(dims, bc, U, 0.12, 1.0)
     for k in range(n):
-        assert rel(out[k], op.ras(etas[k], block, s=s, n_ras=2, n_dominv=4)) <= TOL["f16"]
+        check_field(out[k], op.ras(etas[k], block, s=s, n_ras=2, n_dominv=4), TOL["f16"], dims, block)
 
 
 def test_more_than_eight_slices_use_the_general_kernel(qdd, oracle_mod):
@@ -83,7 +83,7 @@ def test_more_than_eight_slices_use_the_general_kernel(qdd, oracle_mod):
     qdd.load_gauge(lat, U)
     out = _ras(qdd, lat, eta, block=block, overlap=s, n_ras=1, n_dominv=3, inner_prec="f32")
     ref = oracle_mod.Op(dims, bc, U, 0.12, 1.0).ras(eta, block, s=s, n_ras=1, n_dominv=3)
-    assert rel(out, ref) <= TOL["f32"]
+    check_field(out, ref, TOL["f32"], dims, block)
 
 
 @pytest.mark.parametrize("s", [1, 2])

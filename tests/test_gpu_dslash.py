@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import synth
-from gpu_common import TOL_D, max_elem, qdd, rel  # noqa: F401
+from gpu_common import TOL_D, max_elem, qdd, rel, workload_32  # noqa: F401
 
 pytestmark = pytest.mark.gpu
 
@@ -57,8 +57,7 @@ def test_dslash_full_size_sampled(qdd, oracle_mod):
     (internal fields, one dslash launch), checked at sampled sites, including
     the corners and every face, against the oracle computed site by site."""
     dims, bc, kappa, csw = (32, 32, 32, 32), (1, 1, 1, -1), 0.125, 1.0
-    U = synth.gauge_field(dims, 0.3, 1)
-    psi = synth.gaussian_source(dims, 2)
+    U, psi = workload_32()
     V = int(np.prod(dims))
     lat = qdd.create_lattice(dims, bc)
     qdd.load_gauge(lat, torch.from_numpy(U).cuda())
