@@ -111,7 +111,8 @@ class ClockSampler:
 # ------------------------------------------------------------------ helpers
 # the files that define device code: a change to any of them invalidates the
 # committed ncu traffic figures
-KERNEL_SOURCES = ("device.cuh", "df64.cuh", "qdd_internal.h", "lib.h", "dslash.cu", "ras.cu", "blas.cu", "lattice.cu")
+KERNEL_SOURCES = ("device.cuh", "pair.cuh", "df64.cuh", "qdd_internal.h", "lib.h", "dslash.cu", "ras.cu", "blas.cu",
+                  "lattice.cu")
 
 
 def kernel_source_hash():
@@ -876,8 +877,9 @@ def run_workload(args):
     return 0
 
 
-def run_kernels(spec):
-    """Kernel microbenchmark for profilers: builds the 32^4 workload and runs
+def run_kernels(spec, dims=None):
+    """Kernel microbenchmark for profilers: builds the 32^4 workload (or the
+    lattice `dims`, with the same generators) and runs
     one kernel a few times -- dslash:<prec>, ras:<prec>[:<s>[:<bx>x<by>x<bz>x<bt>]]
     (one RAS sweep, N_dominv = 4, extension s, default 0, blocks default 4^4:
     s = 1, 2 run the thread-block-cluster sweep, 4x32x32x32 slabs the phased
@@ -890,9 +892,10 @@ def run_kernels(spec):
     prec, _, ext = prec.partition(":")
     ext, _, blk = ext.partition(":")
     block = tuple(int(b) for b in blk.split("x")) if blk else (4, 4, 4, 4)
-    U = synth.gauge_field(DIMS, EPS, GSEED)
-    eta = synth.gaussian_source(DIMS, SSEED)
-    lat = qdd.create_lattice(DIMS, BC)
+    dims = tuple(dims or DIMS)
+    U = synth.gauge_field(dims, EPS, GSEED)
+    eta = synth.gaussian_source(dims, SSEED)
+    lat = qdd.create_lattice(dims, BC)
     qdd.load_gauge(lat, torch.from_numpy(U).cuda())
     deta = torch.from_numpy(eta).cuda()
     out = torch.empty_like(deta)
@@ -950,9 +953,11 @@ def main():
     ap.add_argument("--kernels", default=None,
                     help="profiler workload: dslash:f16|f32|f64, ras:f16|f32[:s[:bxxbyxbzxbt]] or clover, three launches "
                          "at 32^4")
+    ap.add_argument("--kernel-dims", dest="kernel_dims", type=lambda s: tuple(int(x) for x in s.split(",")),
+                    default=None, help="lattice of the --kernels workload (default 32,32,32,32)")
     args = ap.parse_args()
     if args.kernels:
-        return run_kernels(args.kernels)
+        return run_kernels(args.kernels, args.kernel_dims)
     if args.workload != "solve":
         return run_workload(args)
     args.warmup = max(3, args.warmup)

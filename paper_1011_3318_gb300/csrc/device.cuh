@@ -333,6 +333,8 @@ __device__ __forceinline__ void load_clover(const CloverView &A, long long V, lo
             a[4 * k] = (T)e.x; a[4 * k + 1] = (T)e.y; a[4 * k + 2] = (T)e.z; a[4 * k + 3] = (T)e.w;
         }
     } else {
+        // word m of the FP16 clover holds entry m of block 0 (low half) and
+        // entry m of block 1 (high half)
         const uint4 *p = (const uint4 *)A.d;
         float n = A.n[i];
 #pragma unroll
@@ -342,8 +344,8 @@ __device__ __forceinline__ void load_clover(const CloverView &A, long long V, lo
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 float2 f2 = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
-                a[8 * k + 2 * j] = (T)(f2.x * n);
-                a[8 * k + 2 * j + 1] = (T)(f2.y * n);
+                a[4 * k + j] = (T)(f2.x * n);
+                a[36 + 4 * k + j] = (T)(f2.y * n);
             }
         }
     }
@@ -363,8 +365,8 @@ __device__ __forceinline__ T load_clover_u(const CloverView &A, long long V, lon
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 float2 f2 = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
-                a[8 * k + 2 * j] = (T)f2.x;
-                a[8 * k + 2 * j + 1] = (T)f2.y;
+                a[4 * k + j] = (T)f2.x;
+                a[36 + 4 * k + j] = (T)f2.y;
             }
         }
         return (T)A.n[i];
@@ -452,20 +454,16 @@ __device__ __forceinline__ void load_clover_block(const CloverView &A, long long
             a[4 * k] = (T)e.x; a[4 * k + 1] = (T)e.y; a[4 * k + 2] = (T)e.z; a[4 * k + 3] = (T)e.w;
         }
     } else {
-        // halves [36 H, 36 H + 36) lie in the uint4 words 4 H .. 4 H + 4
+        // block H is the low (H = 0) or high (H = 1) half of every word
         const uint4 *p = (const uint4 *)A.d;
 #pragma unroll
-        for (int k = 0; k < 5; k++) {
-            const uint4 e = p[(4 * H + k) * v + i];
+        for (int k = 0; k < 9; k++) {
+            const uint4 e = p[k * v + i];
             unsigned w[4] = {e.x, e.y, e.z, e.w};
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const int pos = 8 * k + 2 * j - 4 * H;
-                if (pos >= 0 && pos < 36) {
-                    const float2 f2 = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
-                    a[pos] = (T)f2.x;
-                    a[pos + 1] = (T)f2.y;
-                }
+                const float2 f2 = __half22float2(*reinterpret_cast<__half2 *>(&w[j]));
+                a[4 * k + j] = (T)(H == 0 ? f2.x : f2.y);
             }
         }
     }

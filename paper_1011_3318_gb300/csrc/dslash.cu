@@ -14,6 +14,7 @@
 
 #include "device.cuh"
 #include "lib.h"
+#include "pair.cuh"
 
 namespace qdd {
 
@@ -33,7 +34,8 @@ __device__ __forceinline__ void dslash_site(const DslashArgs &a, long long V, lo
     C<T> y[12];
     if constexpr (EARLY_Y) load_spinor<P>(a.y, V, x, y);
     C<T> acc[12];
-    apply_D_site<P>(a.g, a.in, a.U, a.A, (T)a.kappa, x, acc);
+    if constexpr (P == P16) apply_D_site_f16x2(a.g, a.in, a.U, a.A, (float)a.kappa, x, acc);
+    else apply_D_site<P>(a.g, a.in, a.U, a.A, (T)a.kappa, x, acc);
     if constexpr (HAS_Y && !EARLY_Y) load_spinor<P>(a.y, V, x, y);
 
     if constexpr (EPI == EPI_XMY || EPI == EPI_XMY_NORM) {
@@ -122,11 +124,11 @@ __device__ __forceinline__ void dslash_body(DslashArgs a)
     }
 }
 
-// FP16 sites fit in 80 registers (with a few bytes of spill), which allows 3
-// resident blocks of 256 threads per SM instead of 2; the reducing FP16
-// epilogues, whose threads loop over sites, keep 2 blocks (at 80 registers
-// their loop spills).  FP32 and FP64 keep the compiler's register choice (a
-// register bound there makes them spill heavily).
+// FP32 and FP64 keep the compiler's register choice (a register bound there
+// makes them spill heavily).  The FP16 kernel works on packed FP32 pairs
+// (pair.cuh) with up to 128 registers, two blocks of 256 threads per SM: at 3
+// blocks (80 registers) or 5 blocks of 128 threads (96 registers) it measured
+// 5-10% slower.
 template <int P, int EPI, int NT>
 __global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
 {
@@ -134,7 +136,7 @@ __global__ void __launch_bounds__(NT) dslash_kernel(DslashArgs a)
 }
 
 template <int EPI, int NT>
-__global__ void __launch_bounds__(NT, (EPI == EPI_RV || EPI == EPI_TS) ? 2 : 3) dslash_f16_kernel(DslashArgs a)
+__global__ void __launch_bounds__(NT, 2) dslash_f16_kernel(DslashArgs a)
 {
     dslash_body<P16, EPI, NT>(a);
 }

@@ -409,8 +409,9 @@ __global__ void __launch_bounds__(CL_THREADS) clover_build_kernel(Geom g, const 
             unsigned wv[4];
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                __half2 hh = __floats2half2_rn((float)sP[8 * k + 2 * q][site] * inv,
-                                               (float)sP[8 * k + 2 * q + 1][site] * inv);
+                // word 4 k + q holds entry 4 k + q of both chiral blocks
+                __half2 hh = __floats2half2_rn((float)sP[4 * k + q][site] * inv,
+                                               (float)sP[36 + 4 * k + q][site] * inv);
                 wv[q] = *reinterpret_cast<unsigned *>(&hh);
             }
             A16[k * V + x] = make_uint4(wv[0], wv[1], wv[2], wv[3]);

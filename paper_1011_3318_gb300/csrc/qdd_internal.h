@@ -14,7 +14,9 @@
 //   clover F64  double2[36][V]     two Hermitian 6x6 chiral blocks packed as
 //   clover F32  float4 [18][V]     6 real diagonals + 15 complex lower
 //   clover F16  uint4  [9][V]      off-diagonals (i > j, row-major) each,
-//               + float[V] norm    72 reals per site
+//               + float[V] norm    72 reals per site; in FP16, word m holds
+//                                  entry m of block 0 (low half) and entry m
+//                                  of block 1 (high half)
 //
 // The clover blocks act on complex components k = 0..5 (spins 0, 1) and
 // k = 6..11 (spins 2, 3): in the DeGrand-Rossi basis gamma_5 = diag(1,1,-1,-1)
