@@ -202,7 +202,7 @@ cudaError_t launch_dslash(int prec, int epi, const DslashArgs &a, cudaStream_t s
     switch (prec) {
     case P64: return launch_prec<P64>(epi, a, st);
     case P32: return launch_prec<P32>(epi, a, st);
-    case P16: return launch_prec<P16>(epi, a, st);
+    case P16: return a.nrhs >= 2 ? launch_dslash_mrhs_f16(epi, a, st) : launch_prec<P16>(epi, a, st);
     }
     return cudaErrorInvalidValue;
 }

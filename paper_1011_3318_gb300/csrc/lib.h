@@ -65,6 +65,10 @@ struct DslashArgs {
 };
 
 cudaError_t launch_dslash(int prec, int epi, const DslashArgs &a, cudaStream_t st);
+// FP16 D on two right-hand sides per thread (links and clover decoded once
+// for both); nrhs >= 2.  launch_dslash uses it for FP16 lattices with
+// several right-hand sides.
+cudaError_t launch_dslash_mrhs_f16(int epi, const DslashArgs &a, cudaStream_t st);
 
 // Field conversions between the canonical FP64 layout and internal layouts.
 // Canonical multi-RHS layout: double[nrhs][V][4][3][2].
