@@ -82,35 +82,32 @@ __device__ __forceinline__ void load_link16(const LinkView &u, unsigned v, int m
 }
 
 // One hop on spin pairs: acc += c (1 + s gamma_mu) (x) M psi with s = -1 and
-// M = U (forward) or s = +1 and M = U^dag (backward); psi the neighbour's FP16
-// words, c the hop coefficient (times the neighbour's norm).
+// M = U (forward) or s = +1 and M = U^dag (backward).  psi enters as pairs:
+// UR, UI the upper spins (0, 1) of each colour, and DA, DB the lower spins --
+// for MU = 2, 3 in the order (spin 2, spin 3) as real and imaginary parts, for
+// MU = 0, 1 (whose X exchanges the spins) in the order (spin 3, spin 2).
 template <int MU, bool FWD>
-__device__ __forceinline__ void hop_pair16(const unsigned (&w)[12], const C<float> (&U)[9], float c, f2 (&AUR)[3],
-                                           f2 (&AUI)[3], f2 (&ADR)[3], f2 (&ADI)[3])
+__device__ __forceinline__ void hop_core(const f2 (&UR)[3], const f2 (&UI)[3], const f2 (&DA)[3],
+                                         const f2 (&DB)[3], const C<float> (&U)[9], float c, f2 (&AUR)[3],
+                                         f2 (&AUI)[3], f2 (&ADR)[3], f2 (&ADI)[3])
 {
     constexpr float s = FWD ? -1.f : 1.f;
     // h = u + s X_mu d on spin pairs (R: real parts, I: imaginary parts)
     f2 HR[3], HI[3];
 #pragma unroll
     for (int a = 0; a < 3; a++) {
-        const f2 UR = make_float2(hre(w[a]), hre(w[3 + a])), UI = make_float2(him(w[a]), him(w[3 + a]));
         if constexpr (MU == 3) {            // X = 1
-            const f2 DR = make_float2(hre(w[6 + a]), hre(w[9 + a])), DI = make_float2(him(w[6 + a]), him(w[9 + a]));
-            HR[a] = pfma(DR, bc2(s), UR);
-            HI[a] = pfma(DI, bc2(s), UI);
+            HR[a] = pfma(DA[a], bc2(s), UR[a]);
+            HI[a] = pfma(DB[a], bc2(s), UI[a]);
         } else if constexpr (MU == 2) {     // X = diag(i, -i)
-            const f2 DR = make_float2(hre(w[6 + a]), hre(w[9 + a])), DI = make_float2(him(w[6 + a]), him(w[9 + a]));
-            HR[a] = pfma(DI, make_float2(-s, s), UR);
-            HI[a] = pfma(DR, make_float2(s, -s), UI);
-        } else {                            // X_x, X_y exchange the spins: d in the order (spin 3, spin 2)
-            const f2 DRs = make_float2(hre(w[9 + a]), hre(w[6 + a])), DIs = make_float2(him(w[9 + a]), him(w[6 + a]));
-            if constexpr (MU == 0) {        // X = [[0, i], [i, 0]]
-                HR[a] = pfma(DIs, bc2(-s), UR);
-                HI[a] = pfma(DRs, bc2(s), UI);
-            } else {                        // X = [[0, -1], [1, 0]]
-                HR[a] = pfma(DRs, make_float2(-s, s), UR);
-                HI[a] = pfma(DIs, make_float2(-s, s), UI);
-            }
+            HR[a] = pfma(DB[a], make_float2(-s, s), UR[a]);
+            HI[a] = pfma(DA[a], make_float2(s, -s), UI[a]);
+        } else if constexpr (MU == 0) {     // X = [[0, i], [i, 0]], d exchanged
+            HR[a] = pfma(DB[a], bc2(-s), UR[a]);
+            HI[a] = pfma(DA[a], bc2(s), UI[a]);
+        } else {                            // X = [[0, -1], [1, 0]], d exchanged
+            HR[a] = pfma(DA[a], make_float2(-s, s), UR[a]);
+            HI[a] = pfma(DB[a], make_float2(-s, s), UI[a]);
         }
     }
     const f2 cc = bc2(c);
@@ -154,6 +151,29 @@ __device__ __forceinline__ void hop_pair16(const unsigned (&w)[12], const C<floa
             ADI[a].y = fmaf(-sc, WI.x, ADI[a].y);
         }
     }
+}
+
+// The same hop with psi given as the 12 FP16 words of the neighbour (one
+// complex component k = 3 spin + colour each): the lower spins are converted
+// straight into the order hop_core expects.
+template <int MU, bool FWD>
+__device__ __forceinline__ void hop_pair16(const unsigned (&w)[12], const C<float> (&U)[9], float c, f2 (&AUR)[3],
+                                           f2 (&AUI)[3], f2 (&ADR)[3], f2 (&ADI)[3])
+{
+    f2 UR[3], UI[3], DA[3], DB[3];
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+        UR[a] = make_float2(hre(w[a]), hre(w[3 + a]));
+        UI[a] = make_float2(him(w[a]), him(w[3 + a]));
+        if constexpr (MU >= 2) {
+            DA[a] = make_float2(hre(w[6 + a]), hre(w[9 + a]));
+            DB[a] = make_float2(him(w[6 + a]), him(w[9 + a]));
+        } else {
+            DA[a] = make_float2(hre(w[9 + a]), hre(w[6 + a]));
+            DB[a] = make_float2(him(w[9 + a]), him(w[6 + a]));
+        }
+    }
+    hop_core<MU, FWD>(UR, UI, DA, DB, U, c, AUR, AUI, ADR, ADI);
 }
 
 // The data of both hops in direction MU at site x: the two neighbours' FP16
@@ -219,24 +239,20 @@ __device__ __forceinline__ void hop_dir16(const Geom &g, const SpinorView &in, c
     hop_apply16<MU>(h, AUR, AUI, ADR, ADI);
 }
 
-// acc += sc A psi (INIT: acc = sc A psi) for the FP16 clover at site i and
-// the spinor words w: the two chiral 6x6 blocks as pairs (block 0, block 1).  Word m of the FP16
-// clover holds entry m of both blocks, so one conversion per half gives the
-// pair, and the entries stream in storage order: each is applied to both rows
-// it belongs to (an off-diagonal entry L_rj, r > j, gives L_rj psi_j to row r
-// and conj(L_rj) psi_r to row j).
+// acc += sc A psi (INIT: acc = sc A psi) for the FP16 clover planes p (plane
+// k of the site at p[k * v + i]; global or shared memory) and psi as chiral
+// pairs SR[j] = (psi[j].re, psi[6 + j].re), SI[j] likewise, j = 3 spin +
+// colour: the two chiral 6x6 blocks as pairs (block 0, block 1).  Word m of
+// the FP16 clover holds entry m of both blocks, so one conversion per half
+// gives the pair, and the entries stream in storage order: each is applied to
+// both rows it belongs to (an off-diagonal entry L_rj, r > j, gives L_rj psi_j
+// to row r and conj(L_rj) psi_r to row j).
 template <bool INIT>
-__device__ __forceinline__ void clover_pair16(const CloverView &A, unsigned v, unsigned i, const unsigned (&w)[12],
-                                              float sc, f2 (&AUR)[3], f2 (&AUI)[3], f2 (&ADR)[3], f2 (&ADI)[3])
+__device__ __forceinline__ void clover_core(const uint4 *p, unsigned v, unsigned i, const f2 (&SR)[6],
+                                            const f2 (&SI)[6], float sc, f2 (&AUR)[3], f2 (&AUI)[3], f2 (&ADR)[3],
+                                            f2 (&ADI)[3])
 {
-    // psi as chiral pairs: SR[j] = (psi[j].re, psi[6 + j].re), j = 3 spin + colour
-    f2 SR[6], SI[6], OR[6], OI[6];
-#pragma unroll
-    for (int j = 0; j < 6; j++) {
-        SR[j] = make_float2(hre(w[j]), hre(w[6 + j]));
-        SI[j] = make_float2(him(w[j]), him(w[6 + j]));
-    }
-    const uint4 *p = (const uint4 *)A.d;
+    f2 OR[6], OI[6];
     f2 e[36];   // entry m of both blocks (the compiler keeps only the live ones)
 #pragma unroll
     for (int k = 0; k < 9; k++) {
@@ -287,6 +303,20 @@ __device__ __forceinline__ void clover_pair16(const CloverView &A, unsigned v, u
             ADI[a].y = fmaf(sc, OI[3 + a].y, ADI[a].y);
         }
     }
+}
+
+// The clover term for psi given as the 12 FP16 words of the site.
+template <bool INIT>
+__device__ __forceinline__ void clover_pair16(const CloverView &A, unsigned v, unsigned i, const unsigned (&w)[12],
+                                              float sc, f2 (&AUR)[3], f2 (&AUI)[3], f2 (&ADR)[3], f2 (&ADI)[3])
+{
+    f2 SR[6], SI[6];
+#pragma unroll
+    for (int j = 0; j < 6; j++) {
+        SR[j] = make_float2(hre(w[j]), hre(w[6 + j]));
+        SI[j] = make_float2(him(w[j]), him(w[6 + j]));
+    }
+    clover_core<INIT>((const uint4 *)A.d, v, i, SR, SI, sc, AUR, AUI, ADR, ADI);
 }
 
 // (D in)(x) for FP16 fields on packed pairs; the result in the scalar

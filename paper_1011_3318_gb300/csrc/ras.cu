@@ -40,8 +40,9 @@
 #include <cstring>
 
 #include "device.cuh"
-#include "tma.cuh"
 #include "lib.h"
+#include "pair.cuh"
+#include "tma.cuh"
 
 namespace qdd {
 
@@ -131,6 +132,35 @@ __device__ __forceinline__ void st_local(float2 *base, int stride, int l, const 
     float4 *b = reinterpret_cast<float4 *>(base);
 #pragma unroll
     for (int q = 0; q < 6; q++) b[q * stride + l] = make_float4(s[2 * q].r, s[2 * q].i, s[2 * q + 1].r, s[2 * q + 1].i);
+}
+
+// The split spin-pair layout of the packed domain solve (ras_mr_domain_x2):
+// float4 [6][stride], group g = 3 h + a (h = 0: spins 0, 1; h = 1: spins 2, 3;
+// a the colour) holds (psi[2h][a].re, psi[2h+1][a].re, psi[2h][a].im,
+// psi[2h+1][a].im), i.e. the real-part pair and the imaginary-part pair of
+// the two spins.  Same footprint as ld_local / st_local.
+__device__ __forceinline__ void st_split(float2 *base, int stride, int l, const C<float> (&s)[12])
+{
+    float4 *b = reinterpret_cast<float4 *>(base);
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int a = 0; a < 3; a++)
+            b[(3 * h + a) * stride + l] =
+                make_float4(s[6 * h + a].r, s[6 * h + 3 + a].r, s[6 * h + a].i, s[6 * h + 3 + a].i);
+}
+
+__device__ __forceinline__ void ld_split(const float2 *base, int stride, int l, C<float> (&s)[12])
+{
+    const float4 *b = reinterpret_cast<const float4 *>(base);
+#pragma unroll
+    for (int h = 0; h < 2; h++)
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const float4 v = b[(3 * h + a) * stride + l];
+            s[6 * h + a] = {v.x, v.z};
+            s[6 * h + 3 + a] = {v.y, v.w};
+        }
 }
 
 template <int P, int MU>
@@ -390,8 +420,22 @@ __device__ __forceinline__ void smem_hops(const LocSite &s, int l, const float2 
 template <int P, int NT, bool SC, bool EXP>
 __device__ __forceinline__ void ras_mr_domain(const RasArgs &a, const LocSite &s, float2 *srho, float2 *sv,
                                               unsigned char *sA, const LinkView &lU, const CloverView &lA,
+                                              float (&wpart)[3][NT / 32]);
+
+template <int NT>
+__device__ __forceinline__ void ras_mr_domain_x2(const RasArgs &a, const LocSite &s, float2 *srho, float2 *sv,
+                                                 const unsigned char *sA, const float *sAn, const LinkView &lU,
+                                                 float (&wpart)[3][NT / 32]);
+
+template <int P, int NT, bool SC, bool EXP>
+__device__ __forceinline__ void ras_mr_domain(const RasArgs &a, const LocSite &s, float2 *srho, float2 *sv,
+                                              unsigned char *sA, const LinkView &lU, const CloverView &lA,
                                               float (&wpart)[3][NT / 32])
 {
+    if constexpr (P == P16 && SC && !EXP) {
+        ras_mr_domain_x2<NT>(a, s, srho, sv, sA, lA.n, lU, wpart);
+        return;
+    }
     const long long V = a.g.V;
     const int l = threadIdx.x;
     const bool act = s.m & M_ACT;
@@ -485,6 +529,181 @@ __device__ __forceinline__ void ras_mr_domain(const RasArgs &a, const LocSite &s
     }
 }
 
+// Whether a sweep kernel runs the packed domain solve (FP16 storage with the
+// clover staged in shared memory in its compact form): then rho and v live
+// in the split spin-pair layout.
+template <int P, bool SC, bool EXP> struct SplitRho {
+    static constexpr bool value = P == P16 && SC && !EXP;
+};
+
+// Both hops of direction MU on the split residual in shared memory (float4
+// groups), links from the staged FP16 planes.
+template <int MU>
+__device__ __forceinline__ void smem_hops_x2(const LocSite &s, int l, const float4 *R4, const LinkView &sU,
+                                             float kappa, int NT, f2 (&AUR)[3], f2 (&AUI)[3],
+                                             f2 (&ADR)[3], f2 (&ADI)[3])
+{
+    const int ls = s.ls[MU], e = s.e[MU];
+    // the neighbour's spin pairs; for MU = 0, 1 the lower spins exchanged
+    // (float4 loads: scalar loads at a 16-byte stride would cost four
+    // shared-memory wavefronts each)
+    auto pairs = [&](int n, f2 (&UR)[3], f2 (&UI)[3], f2 (&DA)[3], f2 (&DB)[3]) {
+#pragma unroll
+        for (int a = 0; a < 3; a++) {
+            const float4 u = R4[a * NT + n];
+            const float4 d = R4[(3 + a) * NT + n];
+            UR[a] = make_float2(u.x, u.y);
+            UI[a] = make_float2(u.z, u.w);
+            if constexpr (MU >= 2) {
+                DA[a] = make_float2(d.x, d.y);
+                DB[a] = make_float2(d.z, d.w);
+            } else {
+                DA[a] = make_float2(d.y, d.x);
+                DB[a] = make_float2(d.w, d.z);
+            }
+        }
+    };
+    // dropped hops (Dirichlet boundary) run with coefficient 0 on the site's
+    // own data instead of branching around them: a branch around the packed
+    // accumulators made the compiler move them at every join
+    const bool kf = s.m & (1u << MU), kb = s.m & (1u << (4 + MU));
+    if (MU == 3 ? kf : true) {   // t hops: uniform over a warp of these domains, branched
+        const int nf = !kf ? l : (s.m & (1u << (16 + MU))) ? l - (e - 1) * ls : l + ls;
+        f2 UR[3], UI[3], DA[3], DB[3];
+        C<float> U[9];
+        pairs(nf, UR, UI, DA, DB);
+        load_link16(sU, (unsigned)NT, MU, (unsigned)l, U);
+        const float c = !kf ? 0.f : (s.m & (1u << (8 + MU))) ? kappa : -kappa;
+        hop_core<MU, true>(UR, UI, DA, DB, U, c, AUR, AUI, ADR, ADI);
+    }
+    if (MU == 3 ? kb : true) {
+        const int nb = !kb ? l : (s.m & (1u << (20 + MU))) ? l + (e - 1) * ls : l - ls;
+        f2 UR[3], UI[3], DA[3], DB[3];
+        C<float> U[9];
+        pairs(nb, UR, UI, DA, DB);
+        load_link16(sU, (unsigned)NT, MU, (unsigned)nb, U);
+        const float c = !kb ? 0.f : (s.m & (1u << (12 + MU))) ? kappa : -kappa;
+        hop_core<MU, false>(UR, UI, DA, DB, U, c, AUR, AUI, ADR, ADI);
+    }
+}
+
+// ras_mr_domain on packed FP32 pairs (FFMA2, pair.cuh) for FP16 fields with
+// the compact staged clover: rho and v in the split layout (st_split), the
+// clover's two chiral blocks and the hops' two spins as pairs.  The same MR
+// arithmetic in FP32; only its grouping into instructions differs.
+// Measured at 32^4 (ncu, per site and MR iteration): 15% fewer instructions
+// than the scalar solve, but about 300 register moves that the compiler adds
+// around the packed operations take most of the saving; the sweep runs 3%
+// faster on 4x4x4x2 domains and as fast on 4^4 domains.
+template <int NT>
+__device__ __forceinline__ void ras_mr_domain_x2(const RasArgs &a, const LocSite &s, float2 *srho, float2 *sv,
+                                                 const unsigned char *sA, const float *sAn, const LinkView &lU,
+                                                 float (&wpart)[3][NT / 32])
+{
+    const int l = threadIdx.x;
+    const bool act = s.m & M_ACT;
+    float4 *R4 = reinterpret_cast<float4 *>(srho);
+    float4 *V4 = reinterpret_cast<float4 *>(sv);
+    const uint4 *Ap = reinterpret_cast<const uint4 *>(sA);
+    for (int it = 0; it < a.n_iter; it++) {
+        __syncthreads();
+        f2 AUR[3], AUI[3], ADR[3], ADI[3];
+#pragma unroll
+        for (int c = 0; c < 3; c++) AUR[c] = AUI[c] = ADR[c] = ADI[c] = make_float2(0.f, 0.f);
+        if (act) {
+            // clover: rho as chiral pairs (spin sp with spin 2 + sp)
+            f2 SR[6], SI[6];
+#pragma unroll
+            for (int c = 0; c < 3; c++) {
+                const float4 up = R4[c * NT + l], dn = R4[(3 + c) * NT + l];
+                SR[c] = make_float2(up.x, dn.x);
+                SR[3 + c] = make_float2(up.y, dn.y);
+                SI[c] = make_float2(up.z, dn.z);
+                SI[3 + c] = make_float2(up.w, dn.w);
+            }
+            clover_core<true>(Ap, (unsigned)NT, (unsigned)l, SR, SI, sAn[l], AUR, AUI, ADR, ADI);
+            smem_hops_x2<0>(s, l, R4, lU, a.kappa, NT, AUR, AUI, ADR, ADI);
+            smem_hops_x2<1>(s, l, R4, lU, a.kappa, NT, AUR, AUI, ADR, ADI);
+            smem_hops_x2<2>(s, l, R4, lU, a.kappa, NT, AUR, AUI, ADR, ADI);
+            smem_hops_x2<3>(s, l, R4, lU, a.kappa, NT, AUR, AUI, ADR, ADI);
+        }
+        // <q, rho> = sum conj(q) rho and |q|^2 on pairs, then over the domain
+        // in FP32 (warp sums, per-warp partials read by every thread)
+        f2 RR[6], RI[6];
+        float red[3];
+        {
+            f2 d0 = make_float2(0.f, 0.f), d1 = d0, d2 = d0;
+#pragma unroll
+            for (int g = 0; g < 6; g++) {
+                const float4 r = R4[g * NT + l];
+                RR[g] = make_float2(r.x, r.y);
+                RI[g] = make_float2(r.z, r.w);
+                const f2 QR = g < 3 ? AUR[g] : ADR[g - 3], QI = g < 3 ? AUI[g] : ADI[g - 3];
+                d0 = pfma(QR, RR[g], d0);
+                d0 = pfma(QI, RI[g], d0);
+                d1 = pfma(QR, RI[g], d1);
+                d1 = pfma(pneg(QI), RR[g], d1);
+                d2 = pfma(QR, QR, d2);
+                d2 = pfma(QI, QI, d2);
+            }
+            float qr = d0.x + d0.y, qi = d1.x + d1.y, qq = d2.x + d2.y;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                qr += __shfl_xor_sync(0xffffffffu, qr, o);
+                qi += __shfl_xor_sync(0xffffffffu, qi, o);
+                qq += __shfl_xor_sync(0xffffffffu, qq, o);
+            }
+            if ((l & 31) == 0) {
+                wpart[0][l >> 5] = qr;
+                wpart[1][l >> 5] = qi;
+                wpart[2][l >> 5] = qq;
+            }
+            __syncthreads();
+            red[0] = red[1] = red[2] = 0.f;
+#pragma unroll
+            for (int w = 0; w < NT / 32; w++) {
+                red[0] += wpart[0][w];
+                red[1] += wpart[1][w];
+                red[2] += wpart[2][w];
+            }
+        }
+        // every thread is past the barrier: rho can be updated in place
+        if (red[2] > 0.f) {
+            const float inv = 1.0f / red[2];
+            const f2 ar = bc2(red[0] * inv), ai = bc2(red[1] * inv), an = bc2(-red[1] * inv);
+#pragma unroll
+            for (int g = 0; g < 6; g++) {
+                const f2 QR = g < 3 ? AUR[g] : ADR[g - 3], QI = g < 3 ? AUI[g] : ADI[g - 3];
+                const float4 vq = V4[g * NT + l];
+                f2 VR = make_float2(vq.x, vq.y), VI = make_float2(vq.z, vq.w);
+                // v += alpha rho
+                VR = pfma(ar, RR[g], VR);
+                VR = pfma(an, RI[g], VR);
+                VI = pfma(ar, RI[g], VI);
+                VI = pfma(ai, RR[g], VI);
+                // rho -= alpha q
+                f2 NR = pfma(pneg(ar), QR, RR[g]);
+                NR = pfma(ai, QI, NR);
+                f2 NI = pfma(pneg(ar), QI, RI[g]);
+                NI = pfma(an, QR, NI);
+                V4[g * NT + l] = make_float4(VR.x, VR.y, VI.x, VI.y);
+                R4[g * NT + l] = make_float4(NR.x, NR.y, NI.x, NI.y);
+            }
+        }
+    }
+    if (a.asum) {  // additive Schwarz: no restriction, overlaps summed
+        if (act) {
+            C<float> vv[12];
+            ld_split(sv, NT, l, vv);
+            as_add(a, s.x, vv);
+        }
+    } else if (s.m & M_BULK) {  // restriction R_{Omega}
+        C<float> vv[12];
+        ld_split(sv, NT, l, vv);
+        write_outputs<P16>(a, s.x, vv);
+    }
+}
+
 template <int P, int NT, bool SC, bool EXP>
 __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(RasArgs a)
 {
@@ -527,8 +746,13 @@ __global__ void __launch_bounds__(NT, NT == 256 ? 2 : 1) ras_smem_kernel(RasArgs
             // the fused update's result, on the bulk sites (each written once)
             if (a.fuse != RAS_FUSE_NONE && (s.m & M_BULK)) store_spinor<P>(a.in, V, s.x, r);
         }
-        st_local(srho, NT, l, r);
-        st_local(sv, NT, l, z);
+        if constexpr (SplitRho<P, SC, EXP>::value) {
+            st_split(srho, NT, l, r);
+            st_split(sv, NT, l, z);
+        } else {
+            st_local(srho, NT, l, r);
+            st_local(sv, NT, l, z);
+        }
         if (act) {
             if constexpr (EXP) {
 #pragma unroll 1
@@ -687,8 +911,13 @@ __global__ void __launch_bounds__(NT, 512 / NT) ras_tma_kernel(RasArgs a, const 
         C<float> z[12];
 #pragma unroll
         for (int q = 0; q < 12; q++) z[q] = {0.f, 0.f};
-        st_local(srho, NT, l, r);
-        st_local(sv, NT, l, z);
+        if constexpr (SplitRho<P, SC, false>::value) {
+            st_split(srho, NT, l, r);
+            st_split(sv, NT, l, z);
+        } else {
+            st_local(srho, NT, l, r);
+            st_local(sv, NT, l, z);
+        }
         if (a.fuse != RAS_FUSE_NONE) store_spinor<P>(a.in, a.g.V, s.x, r);
     }
     ras_mr_domain<P, NT, SC, false>(a, s, srho, sv, sA, lU, lA, wpart);
