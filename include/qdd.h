@@ -237,6 +237,25 @@ qdd_status qdd_solve_batch(qdd_lattice *const *lats, double *const *phi, const d
                            const double *kappa, const double *c_sw, double tol,
                            const qdd_solver_params *params, qdd_solve_info *info);
 
+/* qdd_solve_batch with parameters per lattice: params[i] (params may be NULL,
+ * and so may params[i]) for lattice i; a NULL entry takes the tuning cache's
+ * parameters for lattice i's shape (qdd_tuned_params), else the defaults.
+ * The lattices may differ in RAS blocking, overlap, n_dominv, n_ras, Schwarz
+ * variant, sweep kernel, inner precision (QDD_F32 or QDD_F16), inner
+ * tolerance and iteration budgets -- each size gets the parameters the
+ * paper's survey (Sec. 5) finds best for it; they must agree on the plain
+ * FP64 solver (inner_prec QDD_F64) against the nested one and on
+ * outer_mode (QDD_ERR_ARG otherwise).  Otherwise as qdd_solve_batch. */
+qdd_status qdd_solve_batch_each(qdd_lattice *const *lats, double *const *phi, const double *const *eta, int n,
+                                const double *kappa, const double *c_sw, double tol,
+                                const qdd_solver_params *const *params, qdd_solve_info *info);
+
+/* The tuning cache: the parameters the last qdd_autotune in this process
+ * chose for a lattice of the same extents, boundary signs and right-hand-side
+ * count (the paper's parameter survey of Sec. 5, kept per lattice shape).
+ * QDD_ERR_STATE if that shape was never tuned. */
+qdd_status qdd_tuned_params(const qdd_lattice *lat, qdd_solver_params *params);
+
 /* Chooses the RAS parameters that minimise the time of a whole solve of
  * D phi = eta (the paper's parameter survey of Sec. 5, done by timing):
  * coordinate search over (n_dominv, n_ras), block shapes of 16 to 256 sites,
@@ -244,8 +263,9 @@ qdd_status qdd_solve_batch(qdd_lattice *const *lats, double *const *phi, const d
  * tighter inner tolerances (3e-4 with FP16 storage, 1e-4 and 1e-5 with
  * FP32 storage); at most max_trials solves.  params is the starting point
  * (inner_prec QDD_F32 or QDD_F16, use_ras = 1) and receives the best
- * parameters; best_ms (may be NULL) receives the best solve time.  eta is a
- * canonical FP64 spinor, host or device.  Runs synchronously. */
+ * parameters, which are also kept in the tuning cache for the lattice's shape
+ * (qdd_tuned_params); best_ms (may be NULL) receives the best solve time.
+ * eta is a canonical FP64 spinor, host or device.  Runs synchronously. */
 qdd_status qdd_autotune(qdd_lattice *lat, const double *eta, double kappa, double c_sw, double tol,
                         qdd_solver_params *params, int max_trials, double *best_ms);
 

@@ -145,6 +145,17 @@ qdd_status finish_out(qdd_lattice *lat, double *dst, const double *dev, bool hos
 
 bool valid_prec(int p) { return p == QDD_F64 || p == QDD_F32 || p == QDD_F16; }
 
+bool valid_params(const qdd_solver_params &p)
+{
+    return valid_prec(p.inner_prec) && p.max_inner >= 1 && p.max_outer >= 1 && p.n_ras >= 1 && p.n_dominv >= 0 &&
+           valid_schwarz(p.schwarz) && (p.outer_mode == 0 || p.outer_mode == 1) &&
+           (p.inner_prec == QDD_F64 || (p.inner_tol > 0 && p.inner_tol < 1));
+}
+
+qdd_status solve_batch_common(qdd_lattice *const *lats, double *const *phi, const double *const *eta, int n,
+                              const double *kappa, const double *c_sw, double tol,
+                              const qdd_solver_params *const *ps, qdd_solve_info *info);
+
 // The in/out field pair of precision prec of the canonical-layout entry points.
 qdd_status io_fields(qdd_lattice *lat, int prec, SpinorView *fin, SpinorView *fout)
 {
@@ -156,6 +167,43 @@ qdd_status io_fields(qdd_lattice *lat, int prec, SpinorView *fin, SpinorView *fo
     *fin = SpinorView{lat->io_d[prec][0], lat->io_n[prec][0]};
     *fout = SpinorView{lat->io_d[prec][1], lat->io_n[prec][1]};
     return QDD_OK;
+}
+
+}  // namespace
+
+namespace {
+
+qdd_status solve_batch_common(qdd_lattice *const *lats, double *const *phi, const double *const *eta, int n,
+                              const double *kappa, const double *c_sw, double tol,
+                              const qdd_solver_params *const *ps, qdd_solve_info *info)
+{
+    std::vector<const double *> deta(n);
+    std::vector<double *> dphi(n);
+    std::vector<bool> host(n);
+    std::vector<qdd_solve_info *> infos(n, nullptr);
+    size_t off = 0;
+    qdd_status st;
+    for (int i = 0; i < n; i++) {
+        if (!lats[i] || !phi[i] || !eta[i]) {
+            set_error("null lattice or buffer in the batch");
+            return QDD_ERR_ARG;
+        }
+        bool h = false;
+        if ((st = stage_in(lats[i], eta[i], &lats[i]->stage_a, &deta[i])) != QDD_OK) return st;
+        if ((st = stage_out(lats[i], phi[i], &lats[i]->stage_b, &dphi[i], &h)) != QDD_OK) return st;
+        host[i] = h;
+        if (info) infos[i] = info + off;
+        off += lats[i]->nrhs;
+    }
+    qdd_status res = solve_batch_impl(lats, dphi.data(), deta.data(), n, kappa, c_sw, tol, ps,
+                                      info ? infos.data() : nullptr);
+    if (res != QDD_OK && res != QDD_ERR_NOT_CONVERGED && res != QDD_ERR_BREAKDOWN && res != QDD_ERR_NONFINITE)
+        return res;
+    std::string keep = g_err;
+    for (int i = 0; i < n; i++)
+        if ((st = finish_out(lats[i], phi[i], dphi[i], host[i])) != QDD_OK) return st;
+    g_err = keep;
+    return res;
 }
 
 }  // namespace
@@ -445,9 +493,7 @@ qdd_status qdd_solve(qdd_lattice *lat, double *phi, const double *eta, double ka
     qdd_solver_params p;
     if (params) p = *params;
     else qdd_default_params(&p);
-    if (!valid_prec(p.inner_prec) || p.max_inner < 1 || p.max_outer < 1 || p.n_ras < 1 || p.n_dominv < 0 ||
-        !valid_schwarz(p.schwarz) || (p.outer_mode != 0 && p.outer_mode != 1) ||
-        (p.inner_prec != QDD_F64 && !(p.inner_tol > 0 && p.inner_tol < 1))) {
+    if (!valid_params(p)) {
         set_error("invalid solver parameters");
         return QDD_ERR_ARG;
     }
@@ -495,39 +541,53 @@ qdd_status qdd_solve_batch(qdd_lattice *const *lats, double *const *phi, const d
     qdd_solver_params p;
     if (params) p = *params;
     else qdd_default_params(&p);
-    if (!valid_prec(p.inner_prec) || p.max_inner < 1 || p.max_outer < 1 || p.n_ras < 1 || p.n_dominv < 0 ||
-        !valid_schwarz(p.schwarz) || (p.outer_mode != 0 && p.outer_mode != 1) ||
-        (p.inner_prec != QDD_F64 && !(p.inner_tol > 0 && p.inner_tol < 1))) {
+    if (!valid_params(p)) {
         set_error("invalid solver parameters");
         return QDD_ERR_ARG;
     }
-    std::vector<const double *> deta(n);
-    std::vector<double *> dphi(n);
-    std::vector<bool> host(n);
-    std::vector<qdd_solve_info *> infos(n, nullptr);
-    size_t off = 0;
-    qdd_status st;
+    std::vector<const qdd_solver_params *> ps(n, &p);
+    return solve_batch_common(lats, phi, eta, n, kappa, c_sw, tol, ps.data(), info);
+}
+
+qdd_status qdd_solve_batch_each(qdd_lattice *const *lats, double *const *phi, const double *const *eta, int n,
+                                const double *kappa, const double *c_sw, double tol,
+                                const qdd_solver_params *const *params, qdd_solve_info *info)
+{
+    g_err.clear();
+    if (!lats || !phi || !eta || !kappa || !c_sw || n < 1 || !(tol > 0)) {
+        set_error("invalid argument");
+        return QDD_ERR_ARG;
+    }
+    std::vector<qdd_solver_params> own(n);
+    std::vector<const qdd_solver_params *> ps(n);
     for (int i = 0; i < n; i++) {
-        if (!lats[i] || !phi[i] || !eta[i]) {
-            set_error("null lattice or buffer in the batch");
+        if (!lats[i]) {
+            set_error("null lattice in the batch");
             return QDD_ERR_ARG;
         }
-        bool h = false;
-        if ((st = stage_in(lats[i], eta[i], &lats[i]->stage_a, &deta[i])) != QDD_OK) return st;
-        if ((st = stage_out(lats[i], phi[i], &lats[i]->stage_b, &dphi[i], &h)) != QDD_OK) return st;
-        host[i] = h;
-        if (info) infos[i] = info + off;
-        off += lats[i]->nrhs;
+        if (params && params[i]) own[i] = *params[i];
+        else if (!tuned_lookup(lats[i], &own[i])) qdd_default_params(&own[i]);
+        if (!valid_params(own[i])) {
+            set_error("invalid solver parameters for lattice " + std::to_string(i));
+            return QDD_ERR_ARG;
+        }
+        ps[i] = &own[i];
     }
-    qdd_status res = solve_batch_impl(lats, dphi.data(), deta.data(), n, kappa, c_sw, tol, &p,
-                                      info ? infos.data() : nullptr);
-    if (res != QDD_OK && res != QDD_ERR_NOT_CONVERGED && res != QDD_ERR_BREAKDOWN && res != QDD_ERR_NONFINITE)
-        return res;
-    std::string keep = g_err;
-    for (int i = 0; i < n; i++)
-        if ((st = finish_out(lats[i], phi[i], dphi[i], host[i])) != QDD_OK) return st;
-    g_err = keep;
-    return res;
+    return solve_batch_common(lats, phi, eta, n, kappa, c_sw, tol, ps.data(), info);
+}
+
+qdd_status qdd_tuned_params(const qdd_lattice *lat, qdd_solver_params *params)
+{
+    g_err.clear();
+    if (!lat || !params) {
+        set_error("invalid argument");
+        return QDD_ERR_ARG;
+    }
+    if (!tuned_lookup(lat, params)) {
+        set_error("no tuned parameters for this lattice shape (run qdd_autotune first)");
+        return QDD_ERR_STATE;
+    }
+    return QDD_OK;
 }
 
 qdd_status qdd_autotune(qdd_lattice *lat, const double *eta, double kappa, double c_sw, double tol,
@@ -548,7 +608,9 @@ qdd_status qdd_autotune(qdd_lattice *lat, const double *eta, double kappa, doubl
     double *dphi = nullptr;
     if ((st = ensure_stage(lat, &lat->stage_b)) != QDD_OK) return st;
     dphi = lat->stage_b;
-    return autotune_impl(lat, dphi, deta, kappa, c_sw, tol, params, max_trials, best_ms);
+    if ((st = autotune_impl(lat, dphi, deta, kappa, c_sw, tol, params, max_trials, best_ms)) != QDD_OK) return st;
+    tuned_store(lat, *params);
+    return QDD_OK;
 }
 
 qdd_status qdd_field_create(qdd_lattice *lat, qdd_prec prec, qdd_field **out)

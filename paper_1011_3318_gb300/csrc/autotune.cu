@@ -16,6 +16,8 @@
 //      1e-4 and 1e-5 with FP32 storage.
 #include <chrono>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "lib.h"
@@ -36,7 +38,44 @@ bool same_ras(const qdd_solver_params &a, const qdd_solver_params &b)
            a.inner_tol == b.inner_tol && a.schwarz == b.schwarz && a.outer_mode == b.outer_mode;
 }
 
+// Tuning cache, keyed by the lattice's extents, boundary signs and
+// right-hand-side count.
+struct ShapeKey {
+    int L[4], bc[4], nrhs;
+    bool operator<(const ShapeKey &o) const { return memcmp(this, &o, sizeof(ShapeKey)) < 0; }
+};
+
+std::mutex g_tuned_mu;
+std::map<ShapeKey, qdd_solver_params> g_tuned;
+
+ShapeKey shape_key(const qdd_lattice *lat)
+{
+    ShapeKey k;
+    memset(&k, 0, sizeof(k));
+    for (int mu = 0; mu < 4; mu++) {
+        k.L[mu] = lat->g.L[mu];
+        k.bc[mu] = lat->g.bc[mu];
+    }
+    k.nrhs = lat->nrhs;
+    return k;
+}
+
 }  // namespace
+
+void tuned_store(const qdd_lattice *lat, const qdd_solver_params &p)
+{
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    g_tuned[shape_key(lat)] = p;
+}
+
+bool tuned_lookup(const qdd_lattice *lat, qdd_solver_params *p)
+{
+    std::lock_guard<std::mutex> lk(g_tuned_mu);
+    auto it = g_tuned.find(shape_key(lat));
+    if (it == g_tuned.end()) return false;
+    *p = it->second;
+    return true;
+}
 
 qdd_status autotune_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, double kappa, double csw,
                          double tol, qdd_solver_params *p, int max_trials, double *best_ms)

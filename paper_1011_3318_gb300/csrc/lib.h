@@ -277,10 +277,17 @@ qdd_status ras_apply_fields(qdd_lattice *lat, int prec, const qdd_solver_params 
 bool ras_can_fuse(int prec, const DomainGeom &dg, int fuse, int schwarz = QDD_SCHWARZ_RAS);
 qdd_status solve_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, double kappa, double csw, double tol,
                       const qdd_solver_params *p, qdd_solve_info *info);
+// A batch of n lattices, lattice i solved with the parameters *ps[i] (they
+// must agree on the plain FP64 solver against the nested one, and on
+// outer_mode).
 qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, const double *const *eta_dev, int n,
-                            const double *kappa, const double *csw, double tol, const qdd_solver_params *p,
+                            const double *kappa, const double *csw, double tol, const qdd_solver_params *const *ps,
                             qdd_solve_info *const *infos);
 void work_free(qdd_work *w);
+// The tuning cache: the parameters qdd_autotune chose, per lattice shape
+// (extents, boundary signs, right-hand-side count), for the process.
+void tuned_store(const qdd_lattice *lat, const qdd_solver_params &p);
+bool tuned_lookup(const qdd_lattice *lat, qdd_solver_params *p);
 qdd_status autotune_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, double kappa, double csw,
                          double tol, qdd_solver_params *p, int max_trials, double *best_ms);
 }  // namespace qdd

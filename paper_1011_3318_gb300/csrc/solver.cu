@@ -307,6 +307,8 @@ struct Member {
     const double *eta_dev;
     double kappa, csw;
     qdd_solve_info *info;  // nrhs entries (may be null)
+    qdd_solver_params prm; // this lattice's solver parameters
+    int prec;              // its inner precision
     bool use_ras;
     DomainGeom dg;
     std::vector<double> eta2, rr, best;
@@ -317,9 +319,11 @@ struct Member {
 // One BiCGStab iteration (van der Vorst) of every right-hand side of a
 // lattice, right-preconditioned by K_RAS when use_ras: D K chi = b,
 // x = K chi (Eq. 3).
-qdd_status enqueue_iteration(Member &m, int prec, const qdd_solver_params *p)
+qdd_status enqueue_iteration(Member &m)
 {
     qdd_lattice *lat = m.lat;
+    const int prec = m.prec;
+    const qdd_solver_params *p = &m.prm;
     auto F = [&](int k) { return inner(lat, prec, k); };
     const SpinorView phat = m.use_ras ? F(W_PHAT) : F(W_P);
     const SpinorView shat = m.use_ras ? F(W_SHAT) : F(W_S);
@@ -371,7 +375,7 @@ struct IterGraph {
     }
 };
 
-qdd_status build_graph(std::vector<Member> &ms, int prec, const qdd_solver_params *p, int chunk, IterGraph &g)
+qdd_status build_graph(std::vector<Member> &ms, int chunk, IterGraph &g)
 {
     cudaStream_t s0 = ms[0].lat->stream;
     g.events.resize(ms.size() + 1, nullptr);
@@ -395,7 +399,7 @@ qdd_status build_graph(std::vector<Member> &ms, int prec, const qdd_solver_param
     for (size_t i = 1; i < ms.size(); i++) cudaStreamWaitEvent(ms[i].lat->stream, g.events[0], 0);
     for (int c = 0; c < chunk && st == QDD_OK; c++)
         for (Member &m : ms)
-            if (st == QDD_OK) st = enqueue_iteration(m, prec, p);
+            if (st == QDD_OK) st = enqueue_iteration(m);
     for (size_t i = 1; i < ms.size(); i++) {
         cudaEventRecord(g.events[i], ms[i].lat->stream);
         cudaStreamWaitEvent(s0, g.events[i], 0);
@@ -420,14 +424,20 @@ qdd_status build_graph(std::vector<Member> &ms, int prec, const qdd_solver_param
 }  // namespace
 
 qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, const double *const *eta_dev, int n,
-                            const double *kappa, const double *csw, double tol, const qdd_solver_params *p,
+                            const double *kappa, const double *csw, double tol, const qdd_solver_params *const *ps,
                             qdd_solve_info *const *infos)
 {
     using clk = std::chrono::steady_clock;
     const auto t0 = clk::now();
     double t_inner = 0.0;
-    const int prec = p->inner_prec;
-    const bool plain = prec == P64;
+    // plain FP64 BiCGStab or nested solve, and the outer level, are common to
+    // the batch; everything else is per lattice
+    const bool plain = ps[0]->inner_prec == P64;
+    for (int i = 1; i < n; i++)
+        if ((ps[i]->inner_prec == P64) != plain || ps[i]->outer_mode != ps[0]->outer_mode) {
+            set_error("the lattices of a batch must share the plain FP64 solver or the nested one, and outer_mode");
+            return QDD_ERR_ARG;
+        }
     std::vector<Member> ms(n);
     std::vector<qdd_lattice *> L(n);
     qdd_status st;
@@ -439,10 +449,12 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
         m.kappa = kappa[i];
         m.csw = csw[i];
         m.info = infos ? infos[i] : nullptr;
-        m.use_ras = !plain && p->use_ras;
+        m.prm = *ps[i];
+        m.prec = m.prm.inner_prec;
+        m.use_ras = !plain && m.prm.use_ras;
         if (m.use_ras) {
             std::string why;
-            if (!domain_geom(m.lat->g, p->block, p->overlap, &m.dg, &why)) {
+            if (!domain_geom(m.lat->g, m.prm.block, m.prm.overlap, &m.dg, &why)) {
                 set_error("invalid RAS blocking: " + why);
                 return QDD_ERR_ARG;
             }
@@ -467,7 +479,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
         qdd_lattice *lat = m.lat;
         if ((st = ensure_clover(lat, m.kappa, m.csw)) != QDD_OK) return st;
         if ((st = ensure_outer(lat)) != QDD_OK) return st;
-        if ((st = ensure_inner(lat, prec)) != QDD_OK) return st;
+        if ((st = ensure_inner(lat, m.prec)) != QDD_OK) return st;
         SpinorView eta = outer(lat, 0), phi = outer(lat, 1), r = outer(lat, 2);
         cudaError_t e;
         {
@@ -497,7 +509,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
     const int chunk = vmax >= (1 << 18) ? 2 : 4;
     IterGraph graph;
     bool have_graph = false;
-    const bool nested_outer = !plain && p->outer_mode == 1;
+    const bool nested_outer = !plain && ps[0]->outer_mode == 1;
 
     // One inner solve of every lattice: right-hand side r of lattice m is
     // src(m) / sqrt(nsc[r].aux[slot]), solved to the relative tolerance
@@ -510,6 +522,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
         for (size_t i = 0; i < ms.size(); i++) {
             Member &m = ms[i];
             qdd_lattice *lat = m.lat;
+            const int prec = m.prec;
             const int R = lat->nrhs;
             for (int r = 0; r < R; r++) {
                 m.restarted[r] = 0;
@@ -535,8 +548,8 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                     // one eager iteration first: it sets kernel attributes and
                     // allocates scratch outside the capture
                     for (Member &m : ms)
-                        if ((st = enqueue_iteration(m, prec, p)) != QDD_OK) return st;
-                    if ((st = build_graph(ms, prec, p, chunk, graph)) != QDD_OK) return st;
+                        if ((st = enqueue_iteration(m)) != QDD_OK) return st;
+                    if ((st = build_graph(ms, chunk, graph)) != QDD_OK) return st;
                     have_graph = true;
                 } else {
                     // the graph runs on the first lattice's stream: order it after
@@ -558,7 +571,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
             } else {
                 for (int c = 0; c < chunk; c++)
                     for (Member &m : ms)
-                        if ((st = enqueue_iteration(m, prec, p)) != QDD_OK) return st;
+                        if ((st = enqueue_iteration(m)) != QDD_OK) return st;
             }
             if ((st = read_scalars(L)) != QDD_OK) return st;
             bool running = false;
@@ -568,7 +581,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                 for (int r = 0; r < lat->nrhs; r++) {
                     const Scalars &h = lat->sc_host[r];
                     if (h.status == S_RUN) {
-                        if (h.iter >= p->max_inner) {
+                        if (h.iter >= m.prm.max_inner) {
                             // out of inner iterations: stop this right-hand side
                             const int conv = S_CONVERGED;
                             cudaMemcpyAsync(&lat->sc[r].status, &conv, sizeof(int), cudaMemcpyHostToDevice,
@@ -586,6 +599,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                     }
                 }
                 if (restart) {
+                    const int prec = m.prec;
                     auto F = [&](int k) { return inner(lat, prec, k); };
                     if ((st = blas(lat, prec, B_RESTART, {F(W_RHAT), F(W_R), F(W_P), F(W_V)})) != QDD_OK) return st;
                 }
@@ -600,7 +614,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                 const Scalars &h = m.lat->sc_host[r];
                 if (m.info) {
                     m.info[r].inner_iters += h.iter;
-                    const int nsweep = p->n_ras * schwarz_plan(p->schwarz, m.dg).colors;
+                    const int nsweep = m.prm.n_ras * schwarz_plan(m.prm.schwarz, m.dg).colors;
                     m.info[r].dv_count += 2 * h.iter + (m.use_ras ? 2 * h.iter * (nsweep - 1) : 0);
                     m.info[r].ras_sweeps += m.use_ras ? 2 * h.iter * nsweep : 0;
                 }
@@ -663,7 +677,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                 active[i] = 0;
                 sdone[i].assign(m.lat->nrhs, 0);
                 for (int r = 0; r < m.lat->nrhs; r++) {
-                    const bool budget = m.oit[r] < p->max_outer;
+                    const bool budget = m.oit[r] < m.prm.max_outer;
                     if (m.lat->work->osc_host[r].status == S_RUN && !m.done[r] && budget) {
                         active[i] |= 1ull << r;
                         any = true;
@@ -677,14 +691,15 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
             if (!any) break;
             // p, phat = M(p), v = D phat with alpha, s, |s|^2
             for (size_t i = 0; i < ms.size(); i++) {
-                qdd_lattice *lat = ms[i].lat;
+                const Member &m = ms[i];
+                qdd_lattice *lat = m.lat;
                 auto N = [&](int k) { return nested(lat, k); };
                 Scalars *osc = lat->work->osc;
                 if ((st = blas(lat, P64, B_P, {N(N_P), N(N_R), N(N_V)}, 0, 0.0, ~0ull, osc)) != QDD_OK) return st;
                 if ((st = blas(lat, P64, B_NORM, {N(N_P)}, AUX_Y2, 0.0, ~0ull, osc)) != QDD_OK) return st;
                 if ((st = blas(lat, P64, B_ZERO, {N(N_PHAT)})) != QDD_OK) return st;
                 src[i] = N(N_P);
-                for (int r = 0; r < lat->nrhs; r++) lat->sc_host[r].aux[AUX_TOL2] = p->inner_tol * p->inner_tol;
+                for (int r = 0; r < lat->nrhs; r++) lat->sc_host[r].aux[AUX_TOL2] = m.prm.inner_tol * m.prm.inner_tol;
             }
             if ((st = inner_solve(src, nsc, AUX_Y2, active)) != QDD_OK) return st;
             for (size_t i = 0; i < ms.size(); i++) {
@@ -695,7 +710,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                 cudaError_t e;
                 {
                     ProfScope ps(lat, QDD_K_CONVERT);
-                    e = launch_accum_scaled(lat->g.V, prec, N(N_PHAT), inner(lat, prec, W_X), osc, AUX_Y2, lat->nrhs,
+                    e = launch_accum_scaled(lat->g.V, m.prec, N(N_PHAT), inner(lat, m.prec, W_X), osc, AUX_Y2, lat->nrhs,
                                             lat->stream);
                 }
                 if (e != cudaSuccess) return cuda_fail(e, "accumulate");
@@ -709,7 +724,8 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
             // a right-hand side whose |s| already meets the target skips M(s)
             // and t: it is parked (status not running) until e += alpha phat
             for (size_t i = 0; i < ms.size(); i++) {
-                qdd_lattice *lat = ms[i].lat;
+                const Member &m = ms[i];
+                qdd_lattice *lat = m.lat;
                 Scalars *oh = lat->work->osc_host;
                 for (int r = 0; r < lat->nrhs; r++) {
                     if (!((active[i] >> r) & 1ull)) continue;
@@ -723,7 +739,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                     }
                 }
                 src[i] = nested(lat, N_S);
-                for (int r = 0; r < lat->nrhs; r++) lat->sc_host[r].aux[AUX_TOL2] = p->inner_tol * p->inner_tol;
+                for (int r = 0; r < lat->nrhs; r++) lat->sc_host[r].aux[AUX_TOL2] = m.prm.inner_tol * m.prm.inner_tol;
             }
             if ((st = inner_solve(src, nsc, AUX_S2, active)) != QDD_OK) return st;
             for (size_t i = 0; i < ms.size(); i++) {
@@ -735,7 +751,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                 cudaError_t e;
                 {
                     ProfScope ps(lat, QDD_K_CONVERT);
-                    e = launch_accum_scaled(lat->g.V, prec, N(N_SHAT), inner(lat, prec, W_X), osc, AUX_S2, lat->nrhs,
+                    e = launch_accum_scaled(lat->g.V, m.prec, N(N_SHAT), inner(lat, m.prec, W_X), osc, AUX_S2, lat->nrhs,
                                             lat->stream);
                 }
                 if (e != cudaSuccess) return cuda_fail(e, "accumulate");
@@ -781,14 +797,14 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
             for (int r = 0; r < m.lat->nrhs; r++) {
                 if (m.done[r]) continue;
                 const double rel = m.eta2[r] > 0 ? std::sqrt(m.rr[r] / m.eta2[r]) : 0.0;
-                const bool budget = nested_outer ? m.oit[r] < p->max_outer : outer_it < p->max_outer;
+                const bool budget = nested_outer ? m.oit[r] < m.prm.max_outer : outer_it < m.prm.max_outer;
                 if (!std::isfinite(rel)) {
                     m.done[r] = 1;
                     m.result[r] = QDD_ERR_NONFINITE;
                 } else if (rel <= tol) {
                     m.done[r] = 1;
                     m.result[r] = QDD_OK;
-                } else if (!budget || (nested_outer && outer_it >= p->max_outer)) {
+                } else if (!budget || (nested_outer && outer_it >= m.prm.max_outer)) {
                     m.done[r] = 1;
                 } else {
                     any = true;
@@ -810,7 +826,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                     // the outer target needs, with a margin for the gap between the
                     // recursive and the true residual
                     double tol_in = m.rr[r] > 0 ? 0.5 * tol * std::sqrt(m.eta2[r] / m.rr[r]) : 1.0;
-                    if (!plain && p->inner_tol > tol_in) tol_in = p->inner_tol;
+                    if (!plain && m.prm.inner_tol > tol_in) tol_in = m.prm.inner_tol;
                     lat->sc_host[r].aux[AUX_TOL2] = tol_in * tol_in;
                     if (!m.done[r]) active[i] |= 1ull << r;
                 }
@@ -827,7 +843,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                 cudaError_t e;
                 {
                     ProfScope ps(lat, QDD_K_CONVERT);
-                    e = launch_accum_scaled(lat->g.V, prec, outer(lat, 1), inner(lat, prec, W_X), lat->sc, AUX_R2,
+                    e = launch_accum_scaled(lat->g.V, m.prec, outer(lat, 1), inner(lat, m.prec, W_X), lat->sc, AUX_R2,
                                             lat->nrhs, lat->stream);
                 }
                 if (e != cudaSuccess) return cuda_fail(e, "accumulate");
@@ -895,7 +911,8 @@ qdd_status solve_impl(qdd_lattice *lat, double *phi_dev, const double *eta_dev, 
     double *phis[1] = {phi_dev};
     const double *etas[1] = {eta_dev};
     qdd_solve_info *infos[1] = {info};
-    return solve_batch_impl(lats, phis, etas, 1, &kappa, &csw, tol, p, info ? infos : nullptr);
+    const qdd_solver_params *ps[1] = {p};
+    return solve_batch_impl(lats, phis, etas, 1, &kappa, &csw, tol, ps, info ? infos : nullptr);
 }
 
 }  // namespace qdd

@@ -45,7 +45,7 @@ ABI = ("qdd_version", "qdd_last_error", "qdd_default_params", "qdd_create_lattic
        "qdd_load_gauge", "qdd_dslash", "qdd_ras_apply", "qdd_solve", "qdd_field_create", "qdd_field_destroy",
        "qdd_field_import", "qdd_field_export", "qdd_dslash_field", "qdd_kernel_launches", "qdd_set_profiling",
        "qdd_profile_read", "qdd_measure_fma_peak", "qdd_ras_field_noalloc", "qdd_autotune", "qdd_solve_batch",
-       "qdd_test_ras_wait")
+       "qdd_solve_batch_each", "qdd_tuned_params", "qdd_test_ras_wait")
 
 # Kernel classes of the per-class GPU timers (qdd_profile).
 KCLASS = ("dslash", "dslash_f64", "ras", "blas", "convert", "clover")
@@ -106,6 +106,11 @@ def _load():
     lib.qdd_solve_batch.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), ctypes.c_double,
                                     ctypes.POINTER(SolverParams), ctypes.POINTER(SolveInfo)]
+    lib.qdd_solve_batch_each.argtypes = [ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                                         ctypes.c_double, ctypes.POINTER(ctypes.POINTER(SolverParams)),
+                                         ctypes.POINTER(SolveInfo)]
+    lib.qdd_tuned_params.argtypes = [P, ctypes.POINTER(SolverParams)]
     lib.qdd_autotune.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  ctypes.POINTER(SolverParams), ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.qdd_ras_field_noalloc.argtypes = [P, P, P, P, P, ctypes.c_double, ctypes.c_double,
@@ -252,10 +257,12 @@ def solve(lat: Lattice, phi, eta, kappa: float, c_sw: float, tol: float, params:
     return out[0] if lat.n_rhs == 1 else out
 
 
-def solve_batch(lats, phis, etas, kappas, c_sws, tol: float, params: SolverParams | None = None,
-                raise_on_failure: bool = True):
+def solve_batch(lats, phis, etas, kappas, c_sws, tol: float, params=None, raise_on_failure: bool = True):
     """Solve independent systems (one per lattice) in lockstep; returns one
-    list of info dicts per lattice."""
+    list of info dicts per lattice.  params: one SolverParams for every
+    lattice (qdd_solve_batch), or a list with one SolverParams or None per
+    lattice (qdd_solve_batch_each: None takes the tuning cache's parameters
+    for that lattice's shape, else the defaults)."""
     n = len(lats)
     keep = []
     ph = (ctypes.c_void_p * n)()
@@ -269,10 +276,18 @@ def solve_batch(lats, phis, etas, kappas, c_sws, tol: float, params: SolverParam
     cs = (ctypes.c_double * n)(*[float(c) for c in c_sws])
     total = sum(l.n_rhs for l in lats)
     infos = (SolveInfo * total)()
-    st = _lib.qdd_solve_batch(hs, ph, et, n, ka, cs, float(tol), ctypes.byref(params) if params is not None else None,
-                              infos)
+    if isinstance(params, (list, tuple)):
+        if len(params) != n:
+            raise ValueError("one parameter set (or None) per lattice")
+        pp = (ctypes.POINTER(SolverParams) * n)(*[ctypes.pointer(p) if p is not None else None for p in params])
+        st = _lib.qdd_solve_batch_each(hs, ph, et, n, ka, cs, float(tol), pp, infos)
+        what = "qdd_solve_batch_each"
+    else:
+        st = _lib.qdd_solve_batch(hs, ph, et, n, ka, cs, float(tol),
+                                  ctypes.byref(params) if params is not None else None, infos)
+        what = "qdd_solve_batch"
     if raise_on_failure:
-        _check(st, "qdd_solve_batch")
+        _check(st, what)
     flat = _info_dicts(infos, st)
     out, o = [], 0
     for l in lats:
@@ -291,6 +306,18 @@ def autotune(lat: Lattice, eta, kappa: float, c_sw: float, tol: float, params: S
     _check(_lib.qdd_autotune(lat.handle, pe, float(kappa), float(c_sw), float(tol), ctypes.byref(p), int(max_trials),
                              ctypes.byref(best)), "qdd_autotune")
     return p, best.value
+
+
+def tuned_params(lat: Lattice):
+    """The tuning cache's parameters for this lattice's shape (set by
+    autotune on a lattice of the same extents, boundary signs and
+    right-hand-side count), or None."""
+    p = SolverParams()
+    st = _lib.qdd_tuned_params(lat.handle, ctypes.byref(p))
+    if st == QDD_ERR_STATE:
+        return None
+    _check(st, "qdd_tuned_params")
+    return p
 
 
 class Field:

@@ -112,3 +112,58 @@ def test_batch_matches_single_solves(qdd, oracle_mod):
     qdd.solve_batch(lats, phis, etas, [0.12] * 3, [1.0] * 3, 1e-11)
     for a, b in zip(phis, singles):
         assert rel(a, b) < 1e-8
+
+
+@pytest.mark.parametrize("graph", [False, True])
+def test_uneven_batch_per_lattice_parameters(qdd, oracle_mod, graph):
+    """Each lattice of a batch solved with its own RAS blocking, n_ras,
+    n_dominv and inner precision (qdd_solve_batch_each): every system meets
+    the oracle's FP64 residual, and each lattice's sweep count follows its
+    own n_ras."""
+    draws = [((8, 8, 8, 8), 0.3, 0.12, dict(block=(4, 4, 4, 4), n_ras=1, n_dominv=4, inner_prec="f16")),
+             ((8, 8, 4, 8), 0.25, 0.118, dict(block=(4, 4, 4, 2), n_ras=2, n_dominv=3, inner_prec="f32")),
+             ((4, 4, 4, 12), 0.35, 0.12, dict(block=(2, 2, 2, 2), n_ras=3, n_dominv=2, inner_prec="f16"))]
+    lats, phis, etas, ops, params = [], [], [], [], []
+    for k, (dims, eps, kappa, kw) in enumerate(draws):
+        U = synth.gauge_field(dims, eps, 300 + k)
+        eta = synth.gaussian_source(dims, 400 + k)
+        lat = qdd.create_lattice(dims, BC, stream=torch.cuda.Stream() if graph else None)
+        qdd.load_gauge(lat, torch.from_numpy(U).cuda())
+        lats.append(lat)
+        etas.append(torch.from_numpy(eta).cuda())
+        phis.append(torch.zeros_like(etas[-1]))
+        ops.append((oracle_mod.Op(dims, BC, U, kappa, 1.0), eta))
+        params.append(qdd.default_params(**kw))
+    infos = qdd.solve_batch(lats, phis, etas, [d[2] for d in draws], [1.0] * 3, 1e-10, params)
+    torch.cuda.synchronize()
+    for k in range(3):
+        op, eta = ops[k]
+        info = infos[k][0]
+        assert info["status"] == 0 and op.true_residual(eta, phis[k].cpu().numpy()) <= 1e-10
+        assert info["ras_sweeps"] == 2 * info["inner_iters"] * params[k].n_ras
+
+
+def test_tuning_cache_feeds_the_batch(qdd, oracle_mod):
+    """qdd_autotune keeps its choice per lattice shape; a batch entry without
+    parameters takes it (and a shape never tuned takes the defaults)."""
+    dims, kappa = (8, 8, 8, 8), 0.12
+    U = synth.gauge_field(dims, 0.3, 311)
+    eta = torch.from_numpy(synth.gaussian_source(dims, 312)).cuda()
+    lat = qdd.create_lattice(dims, BC)
+    qdd.load_gauge(lat, torch.from_numpy(U).cuda())
+    p, _ = qdd.autotune(lat, eta, kappa, 1.0, 1e-10, qdd.default_params(inner_prec="f16"), max_trials=6)
+    got = qdd.tuned_params(lat)
+    assert got is not None and list(got.block) == list(p.block) and got.n_ras == p.n_ras
+    assert got.n_dominv == p.n_dominv and got.inner_prec == p.inner_prec
+    other = qdd.create_lattice((4, 4, 4, 8), BC)
+    assert qdd.tuned_params(other) is None
+    U2 = synth.gauge_field((4, 4, 4, 8), 0.3, 313)
+    qdd.load_gauge(other, U2)
+    eta2 = synth.gaussian_source((4, 4, 4, 8), 314)
+    phi = torch.zeros_like(eta)
+    phi2 = np.zeros_like(eta2)
+    infos = qdd.solve_batch([lat, other], [phi, phi2], [eta, eta2], [kappa, kappa], [1.0, 1.0], 1e-10, [None, None])
+    torch.cuda.synchronize()
+    assert oracle_mod.Op(dims, BC, U, kappa, 1.0).true_residual(eta.cpu().numpy(), phi.cpu().numpy()) <= 1e-10
+    assert oracle_mod.Op((4, 4, 4, 8), BC, U2, kappa, 1.0).true_residual(eta2, phi2) <= 1e-10
+    assert infos[0][0]["ras_sweeps"] == 2 * infos[0][0]["inner_iters"] * p.n_ras
