@@ -111,7 +111,7 @@ class ClockSampler:
 # ------------------------------------------------------------------ helpers
 # the files that define device code: a change to any of them invalidates the
 # committed ncu traffic figures
-KERNEL_SOURCES = ("device.cuh", "pair.cuh", "df64.cuh", "qdd_internal.h", "lib.h", "dslash.cu", "dslash_mrhs.cu", "ras.cu", "blas.cu",
+KERNEL_SOURCES = ("device.cuh", "pair.cuh", "df64.cuh", "qdd_internal.h", "lib.h", "dslash.cu", "ras.cu", "blas.cu",
                   "lattice.cu")
 
 
@@ -124,9 +124,10 @@ def kernel_source_hash():
 
 
 def ncu_traffic(kernel_class):
-    """DRAM bytes per launch of a kernel class from the committed ncu summary
-    profiles/traffic.md, if it was taken on the current kernel sources (its
-    'sources hash' line matches), else None."""
+    """DRAM bytes per launch of a kernel class (with the RAS block shape of
+    the solve it was captured in, e.g. "ras 4x4x4x2") from the committed ncu
+    summary profiles/traffic.md, if it was taken on the current kernel
+    sources (its 'sources hash' line matches), else None."""
     p = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(p):
         return None
@@ -441,12 +442,13 @@ def run_ours(args, rank, world):
         ms_l = prof["ras"][0] / max(1, prof["ras"][1])
         flops = ras_sweep_flops(blk, ov, nd)
         ach = flops / (ms_l * 1e-3) / 1e12
-        tma = (params.ras_kernel == 0 and ov == 0 and blk[0] * blk[1] * blk[2] * blk[3] == 256
+        tma = (params.ras_kernel == 0 and ov == 0 and blk[0] * blk[1] * blk[2] * blk[3] in (128, 256)
                and blk[0] % 4 == 0 and DIMS[0] % 4 == 0)
         name = "ras_tma_kernel (RAS sweep, TMA staging)" if tma else "ras_smem_kernel (RAS sweep)"
         roof = {"kernel": name, "bound": "alu", "achieved": round(ach, 2),
                 "peak": round(fp32_alu_peak, 1), "unit": "TFLOP/s", "frac": round(ach / fp32_alu_peak, 3),
-                "traffic": ncu_traffic("ras"), "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
+                "traffic": ncu_traffic("ras " + "x".join(map(str, blk))),
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz",
                 "us_per_launch": round(ms_l * 1e3, 1), "share": round(prof["ras"][0] / total, 3)}
     else:
         cls = dom if dom in ("dslash", "dslash_f64") else "dslash"
@@ -464,7 +466,8 @@ def run_ours(args, rank, world):
     ach_d = bps_d * V / (ms_d * 1e-3) / 1e9
     roof_dslash = {"kernel": f"dslash kernel ({args.prec}, D with fused dot-product epilogue, in the solve)",
                    "bound": "hbm", "achieved": round(ach_d, 1), "peak": hbm, "unit": "GB/s",
-                   "frac": round(ach_d / hbm, 3), "traffic": ncu_traffic("dslash"), "bytes_per_site": bps_d,
+                   "frac": round(ach_d / hbm, 3), "traffic": ncu_traffic("dslash " + "x".join(map(str, blk))),
+                   "bytes_per_site": bps_d,
                    "us_per_launch": round(ms_d * 1e3, 1)}
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
@@ -920,10 +923,11 @@ def run_workload(args):
 def run_kernels(spec, dims=None):
     """Kernel microbenchmark for profilers: builds the 32^4 workload (or the
     lattice `dims`, with the same generators) and runs
-    one kernel a few times -- dslash:<prec>, ras:<prec>[:<s>[:<bx>x<by>x<bz>x<bt>]]
-    (one RAS sweep, N_dominv = 4, extension s, default 0, blocks default 4^4:
-    s = 1, 2 run the thread-block-cluster sweep, 4x32x32x32 slabs the phased
-    sweep) or clover (the clover build)."""
+    one kernel a few times -- dslash:<prec>,
+    ras:<prec>[:<s>[:<bx>x<by>x<bz>x<bt>[:<n_dominv>]]] (one RAS sweep,
+    extension s, default 0, blocks default 4^4, N_dominv default 4: s = 1, 2
+    run the thread-block-cluster sweep, 4x32x32x32 slabs the phased sweep),
+    mrhs:<n> (the FP16 D on n right-hand sides) or clover (the clover build)."""
     import torch
 
     import synth
@@ -931,7 +935,9 @@ def run_kernels(spec, dims=None):
     kind, _, prec = spec.partition(":")
     prec, _, ext = prec.partition(":")
     ext, _, blk = ext.partition(":")
+    blk, _, ndv = blk.partition(":")
     block = tuple(int(b) for b in blk.split("x")) if blk else (4, 4, 4, 4)
+    n_dominv = int(ndv) if ndv else 4
     dims = tuple(dims or DIMS)
     U = synth.gauge_field(dims, EPS, GSEED)
     eta = synth.gaussian_source(dims, SSEED)
@@ -946,7 +952,7 @@ def run_kernels(spec, dims=None):
         for _ in range(3):
             qdd.dslash_field(lat, b, a, KAPPA, CSW)
     elif kind == "ras":
-        p = qdd.default_params(inner_prec=prec, n_ras=1, n_dominv=4, overlap=int(ext or 0), block=block)
+        p = qdd.default_params(inner_prec=prec, n_ras=1, n_dominv=n_dominv, overlap=int(ext or 0), block=block)
         for _ in range(3):
             qdd.ras_apply(lat, out, deta, KAPPA, CSW, p)
         # then the sweep alone, timed by the library's per-class CUDA events
@@ -960,6 +966,17 @@ def run_kernels(spec, dims=None):
     elif kind == "clover":
         for k in range(3):
             qdd.dslash(lat, out, deta, KAPPA + 0.001 * k, CSW, "f32")
+    elif kind == "mrhs":
+        # the FP16 D on a lattice with n right-hand sides (two per thread)
+        n = int(prec or 12)
+        latm = qdd.create_lattice(dims, BC, n_rhs=n)
+        qdd.load_gauge(latm, torch.from_numpy(U).cuda())
+        src = torch.stack([torch.from_numpy(synth.gaussian_source(dims, SSEED + r)) for r in range(n)]).cuda()
+        a = qdd.field_create(latm, "f16")
+        b = qdd.field_create(latm, "f16")
+        qdd.field_import(a, src)
+        for _ in range(3):
+            qdd.dslash_field(latm, b, a, KAPPA, CSW)
     else:
         raise SystemExit(f"unknown kernel {spec}")
     torch.cuda.synchronize()
@@ -982,7 +999,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="no_cpu_baseline", action="store_true")
     ap.add_argument("--no-autotune", dest="no_autotune", action="store_true",
                     help="use --block/--overlap/--n-dominv/--n-ras as given instead of tuning them")
-    ap.add_argument("--tune-trials", dest="tune_trials", type=int, default=42)
+    ap.add_argument("--tune-trials", dest="tune_trials", type=int, default=56)
     ap.add_argument("--workload", choices=("solve", "mrhs", "batch", "survey", "table1", "schwarz", "outer",
                                            "blocks", "small"),
                     default="solve",
@@ -991,8 +1008,8 @@ def main():
                          "SAP and AS compared as the preconditioner; outer: defect correction vs outer BiCGStab; "
                          "blocks: block shapes x overlaps x inner precisions; small: the 8^4 and 16^4 configurations")
     ap.add_argument("--kernels", default=None,
-                    help="profiler workload: dslash:f16|f32|f64, ras:f16|f32[:s[:bxxbyxbzxbt]] or clover, three launches "
-                         "at 32^4")
+                    help="profiler workload: dslash:f16|f32|f64, ras:f16|f32[:s[:bxxbyxbzxbt[:n_dominv]]], "
+                         "mrhs:<n right-hand sides> (FP16) or clover, three launches at 32^4")
     ap.add_argument("--kernel-dims", dest="kernel_dims", type=lambda s: tuple(int(x) for x in s.split(",")),
                     default=None, help="lattice of the --kernels workload (default 32,32,32,32)")
     args = ap.parse_args()

@@ -11,10 +11,11 @@
 // whose spin pairs are exchanged by the off-diagonal projectors, no lane ever
 // has to move.  Link and clover entries enter as broadcast pairs.
 //
-// Grid: blockIdx.x covers the sites (the reducing epilogues stride over the
-// lattice with a grid of resident blocks), blockIdx.y the pairs of right-hand
-// sides; consecutive threads take consecutive sites, so every load of a warp
-// is one contiguous segment of a field plane.  An odd last pair computes its
+// Grid: (site block x pair of right-hand sides) with the pair fastest, so
+// that consecutive blocks read the same links and clover (from L2); the
+// reducing epilogues stride over the lattice with a grid of resident blocks.
+// Consecutive threads take consecutive sites, so every load of a warp is one
+// contiguous segment of a field plane.  An odd last pair computes its
 // second lane from the first right-hand side and discards it.  A right-hand
 // side whose solve has stopped is skipped: nothing of it is stored or
 // reduced.
@@ -242,7 +243,11 @@ __global__ void __launch_bounds__(MR_NT, 2) dslash_mrhs_f16_kernel(DslashArgs a)
     constexpr int NRED = (EPI == EPI_XMY_NORM) ? 1 : (EPI == EPI_RV || EPI == EPI_TS) ? 3 : 0;
     const long long V = a.g.V;
     const unsigned v = (unsigned)V;
-    const int ra = 2 * blockIdx.y;
+    // pair of right-hand sides fastest: consecutive blocks work on the same
+    // sites and share their links and clover through L2
+    const unsigned pairs = (unsigned)(a.nrhs + 1) / 2;
+    const unsigned pr = blockIdx.x % pairs, sb = blockIdx.x / pairs, nsb = gridDim.x / pairs;
+    const int ra = 2 * (int)pr;
     const bool has_b = ra + 1 < a.nrhs;
     const int rb = has_b ? ra + 1 : ra;
     // a right-hand side whose solve has stopped takes no part (uniform per block)
@@ -313,7 +318,7 @@ __global__ void __launch_bounds__(MR_NT, 2) dslash_mrhs_f16_kernel(DslashArgs a)
     };
 
     if constexpr (NRED > 0) {
-        for (long long x = (long long)blockIdx.x * MR_NT + threadIdx.x; x < V; x += (long long)gridDim.x * MR_NT)
+        for (long long x = (long long)sb * MR_NT + threadIdx.x; x < V; x += (long long)nsb * MR_NT)
             site((unsigned)x);
         // one grid reduction per active right-hand side (each with its own
         // partial sums and arrival counter)
@@ -322,11 +327,11 @@ __global__ void __launch_bounds__(MR_NT, 2) dslash_mrhs_f16_kernel(DslashArgs a)
             const bool act = l == 0 ? act_a : act_b;
             if (!act) continue;   // uniform over the block
             const int r = l == 0 ? ra : rb;
-            float pr[NRED];
+            float pl[NRED];
             double red[NRED];
 #pragma unroll
-            for (int k = 0; k < NRED; k++) pr[k] = l == 0 ? part[k].x : part[k].y;
-            if (grid_sum<NRED, float>(pr, red, rs_partials(a.rs, r), rs_counter(a.rs, r), blockIdx.x, gridDim.x)) {
+            for (int k = 0; k < NRED; k++) pl[k] = l == 0 ? part[k].x : part[k].y;
+            if (grid_sum<NRED, float>(pl, red, rs_partials(a.rs, r), rs_counter(a.rs, r), sb, nsb)) {
                 double r3[3] = {0.0, 0.0, 0.0};
 #pragma unroll
                 for (int k = 0; k < NRED; k++) r3[k] = red[k];
@@ -334,7 +339,7 @@ __global__ void __launch_bounds__(MR_NT, 2) dslash_mrhs_f16_kernel(DslashArgs a)
             }
         }
     } else {
-        const long long x = (long long)blockIdx.x * MR_NT + threadIdx.x;
+        const long long x = (long long)sb * MR_NT + threadIdx.x;
         if (x < V) site((unsigned)x);
     }
 }
@@ -373,7 +378,7 @@ static cudaError_t launch_mrhs_epi(const DslashArgs &a, cudaStream_t st)
         if (nb > per_pair) nb = per_pair;
         if (nb > a.rs.max_blocks) nb = a.rs.max_blocks;
     }
-    kernel<<<dim3((unsigned)nb, pairs), MR_NT, 0, st>>>(a);
+    kernel<<<(unsigned)(nb * pairs), MR_NT, 0, st>>>(a);
     note_launch();
     return cudaGetLastError();
 }
