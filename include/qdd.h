@@ -192,6 +192,16 @@ qdd_status qdd_destroy_lattice(qdd_lattice *lat);
  * such call and kept until the lattice is destroyed.  Synchronous. */
 qdd_status qdd_load_gauge(qdd_lattice *lat, const double *U);
 
+/* qdd_load_gauge followed by the clover term for (kappa, c_sw) (the O(a)
+ * improvement of Sec. 5), in one pass: for host U with Lt a multiple of 8
+ * and at least 16, the links are copied in 8 groups of t-slices and the
+ * clover of each group is built as soon as its two neighbouring groups are
+ * converted, so that the build overlaps the copy of the remaining links;
+ * otherwise it is built after the conversion.  The clover cache then holds (kappa, c_sw), and calls with
+ * these parameters need no build.  Errors as qdd_load_gauge; QDD_ERR_ARG
+ * also for a non-finite kappa or c_sw.  Synchronous. */
+qdd_status qdd_load_gauge_clover(qdd_lattice *lat, const double *U, double kappa, double c_sw);
+
 /* out = D in (Eq. 1), computed in precision prec (QDD_F64: FP64 throughout;
  * QDD_F32: FP32 fields and arithmetic; QDD_F16: FP16 storage with per-site
  * norms, FP32 arithmetic).  in/out canonical FP64 spinors, host or device,

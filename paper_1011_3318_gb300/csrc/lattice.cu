@@ -291,7 +291,8 @@ constexpr int CL_SITES = 32;
 constexpr int CL_THREADS = 6 * CL_SITES;
 
 __global__ void __launch_bounds__(CL_THREADS) clover_build_kernel(Geom g, const float4 *Udf, double kappa, double csw,
-                                                                   double2 *A64, float4 *A32, uint4 *A16, float *A16n)
+                                                                   double2 *A64, float4 *A32, uint4 *A16, float *A16n,
+                                                                   long long site0, long long site1)
 {
     __shared__ float sQ[6][9][4][CL_SITES];  // Q per plane: [entry][re.h re.l im.h im.l][site]
     __shared__ double sP[72][CL_SITES];      // packed clover
@@ -300,8 +301,8 @@ __global__ void __launch_bounds__(CL_THREADS) clover_build_kernel(Geom g, const 
     const int t = threadIdx.x;
     {
         const int site = t % CL_SITES, plane = t / CL_SITES;
-        const long long x = (long long)blockIdx.x * CL_SITES + site;
-        if (x < V) {
+        const long long x = site0 + (long long)blockIdx.x * CL_SITES + site;
+        if (x < site1) {
             // planes (0,1) (0,2) (0,3) (1,2) (1,3) (2,3)
             const int mu = (plane >= 3) + (plane >= 5);
             const int nu = plane < 3 ? plane + 1 : plane < 5 ? plane - 1 : 3;
@@ -397,8 +398,8 @@ __global__ void __launch_bounds__(CL_THREADS) clover_build_kernel(Geom g, const 
     __syncthreads();
     for (int w = t; w < 36 * CL_SITES; w += CL_THREADS) {
         const int site = w % CL_SITES, k = w / CL_SITES;
-        const long long x = (long long)blockIdx.x * CL_SITES + site;
-        if (x >= V) continue;
+        const long long x = site0 + (long long)blockIdx.x * CL_SITES + site;
+        if (x >= site1) continue;
         A64[k * V + x] = make_double2(sP[2 * k][site], sP[2 * k + 1][site]);
         if (k < 18)
             A32[k * V + x] = make_float4((float)sP[4 * k][site], (float)sP[4 * k + 1][site], (float)sP[4 * k + 2][site],
@@ -421,11 +422,13 @@ __global__ void __launch_bounds__(CL_THREADS) clover_build_kernel(Geom g, const 
 }
 
 cudaError_t launch_clover_build(const Geom &g, const void *Udf, double kappa, double csw, void *A64, void *A32,
-                                void *A16, float *A16n, cudaStream_t st)
+                                void *A16, float *A16n, cudaStream_t st, long long site0, long long site1)
 {
-    const unsigned nb = (unsigned)((g.V + CL_SITES - 1) / CL_SITES);
+    if (site1 < 0) site1 = g.V;
+    if (site1 <= site0) return cudaSuccess;
+    const unsigned nb = (unsigned)((site1 - site0 + CL_SITES - 1) / CL_SITES);
     clover_build_kernel<<<nb, CL_THREADS, 0, st>>>(g, (const float4 *)Udf, kappa, csw, (double2 *)A64, (float4 *)A32,
-                                            (uint4 *)A16, A16n);
+                                            (uint4 *)A16, A16n, site0, site1);
     note_launch();
     return cudaGetLastError();
 }

@@ -83,9 +83,11 @@ cudaError_t launch_gauge_convert(const Geom &g, const double *U, void *U64, void
                                  unsigned long long *maxdev, cudaStream_t st, long long site0 = 0,
                                  long long site1 = -1);
 
-// Clover term from the double-float links, stored in all three precisions.
+// Clover term from the double-float links, stored in all three precisions,
+// for the sites [site0, site1) (site1 < 0: up to V); it reads the links of
+// the sites within one step in two directions of them.
 cudaError_t launch_clover_build(const Geom &g, const void *Udf, double kappa, double csw, void *A64, void *A32,
-                                void *A16, float *A16n, cudaStream_t st);
+                                void *A16, float *A16n, cudaStream_t st, long long site0 = 0, long long site1 = -1);
 
 // BLAS of the Krylov solvers (K-B4 in the design notes).
 struct BlasArgs {

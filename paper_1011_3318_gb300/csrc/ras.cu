@@ -589,12 +589,11 @@ __device__ __forceinline__ void smem_hops_x2(const LocSite &s, int l, const floa
 
 // ras_mr_domain on packed FP32 pairs (FFMA2, pair.cuh) for FP16 fields with
 // the compact staged clover: rho and v in the split layout (st_split), the
-// clover's two chiral blocks and the hops' two spins as pairs.  The same MR
+// hops' two spins as pairs.  The same MR
 // arithmetic in FP32; only its grouping into instructions differs.
-// Measured at 32^4 (ncu, per site and MR iteration): 15% fewer instructions
-// than the scalar solve, but about 300 register moves that the compiler adds
-// around the packed operations take most of the saving; the sweep runs 3%
-// faster on 4x4x4x2 domains and as fast on 4^4 domains.
+// The clover term stays scalar (see below).  Measured at 32^4 against the
+// all-scalar solve: 4x4x4x2 domains, N_dominv 3: 240.5 -> 215.7 us; 4^4
+// domains, N_dominv 4: 328 -> 304 us.
 template <int NT>
 __device__ __forceinline__ void ras_mr_domain_x2(const RasArgs &a, const LocSite &s, float2 *srho, float2 *sv,
                                                  const unsigned char *sA, const float *sAn, const LinkView &lU,
@@ -611,17 +610,22 @@ __device__ __forceinline__ void ras_mr_domain_x2(const RasArgs &a, const LocSite
 #pragma unroll
         for (int c = 0; c < 3; c++) AUR[c] = AUI[c] = ADR[c] = ADI[c] = make_float2(0.f, 0.f);
         if (act) {
-            // clover: rho as chiral pairs (spin sp with spin 2 + sp)
-            f2 SR[6], SI[6];
+            // the clover term in scalar FP32 arithmetic: written on the
+            // packed pairs (block 0, block 1) the compiler added about 250
+            // register moves per site and iteration, and the solve ran 7%
+            // slower
+            {
+                C<float> own[12], o[12];
+                float av[72];
+                ld_split(srho, NT, l, own);
+                const float na = load_clover_u<P16>(CloverView{sA, sAn}, NT, l, av);
+                clover_apply(av, own, o);
 #pragma unroll
-            for (int c = 0; c < 3; c++) {
-                const float4 up = R4[c * NT + l], dn = R4[(3 + c) * NT + l];
-                SR[c] = make_float2(up.x, dn.x);
-                SR[3 + c] = make_float2(up.y, dn.y);
-                SI[c] = make_float2(up.z, dn.z);
-                SI[3 + c] = make_float2(up.w, dn.w);
+                for (int c = 0; c < 3; c++) {
+                    AUR[c] = make_float2(na * o[c].r, na * o[3 + c].r); AUI[c] = make_float2(na * o[c].i, na * o[3 + c].i);
+                    ADR[c] = make_float2(na * o[6 + c].r, na * o[9 + c].r); ADI[c] = make_float2(na * o[6 + c].i, na * o[9 + c].i);
+                }
             }
-            clover_core<true>(Ap, (unsigned)NT, (unsigned)l, SR, SI, sAn[l], AUR, AUI, ADR, ADI);
             smem_hops_x2<0>(s, l, R4, lU, a.kappa, NT, AUR, AUI, ADR, ADI);
             smem_hops_x2<1>(s, l, R4, lU, a.kappa, NT, AUR, AUI, ADR, ADI);
             smem_hops_x2<2>(s, l, R4, lU, a.kappa, NT, AUR, AUI, ADR, ADI);

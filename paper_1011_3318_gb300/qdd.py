@@ -45,7 +45,7 @@ ABI = ("qdd_version", "qdd_last_error", "qdd_default_params", "qdd_create_lattic
        "qdd_load_gauge", "qdd_dslash", "qdd_ras_apply", "qdd_solve", "qdd_field_create", "qdd_field_destroy",
        "qdd_field_import", "qdd_field_export", "qdd_dslash_field", "qdd_kernel_launches", "qdd_set_profiling",
        "qdd_profile_read", "qdd_measure_fma_peak", "qdd_ras_field_noalloc", "qdd_autotune", "qdd_solve_batch",
-       "qdd_solve_batch_each", "qdd_tuned_params", "qdd_test_ras_wait")
+       "qdd_solve_batch_each", "qdd_tuned_params", "qdd_load_gauge_clover", "qdd_test_ras_wait")
 
 # Kernel classes of the per-class GPU timers (qdd_profile).
 KCLASS = ("dslash", "dslash_f64", "ras", "blas", "convert", "clover")
@@ -89,6 +89,7 @@ def _load():
     lib.qdd_create_lattice.argtypes = [ctypes.POINTER(P), I4, I4, ctypes.c_int, P]
     lib.qdd_destroy_lattice.argtypes = [P]
     lib.qdd_load_gauge.argtypes = [P, P]
+    lib.qdd_load_gauge_clover.argtypes = [P, P, ctypes.c_double, ctypes.c_double]
     lib.qdd_dslash.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_int]
     lib.qdd_ras_apply.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double, ctypes.POINTER(SolverParams)]
     lib.qdd_solve.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
@@ -216,9 +217,14 @@ def destroy_lattice(lat: Lattice) -> None:
         lat.handle = None
 
 
-def load_gauge(lat: Lattice, U) -> None:
+def load_gauge(lat: Lattice, U, kappa: float | None = None, c_sw: float | None = None) -> None:
+    """Load the links; with kappa and c_sw also build the clover term in the
+    same pass (qdd_load_gauge_clover)."""
     p, _keep = _ptr(U)
-    _check(_lib.qdd_load_gauge(lat.handle, p), "qdd_load_gauge")
+    if kappa is None and c_sw is None:
+        _check(_lib.qdd_load_gauge(lat.handle, p), "qdd_load_gauge")
+    else:
+        _check(_lib.qdd_load_gauge_clover(lat.handle, p, float(kappa), float(c_sw)), "qdd_load_gauge_clover")
 
 
 def dslash(lat: Lattice, out, inp, kappa: float, c_sw: float, prec="f64") -> None:

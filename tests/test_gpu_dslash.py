@@ -105,3 +105,39 @@ def test_load_gauge_rejects_nan_links(qdd):
     with pytest.raises(qdd.QddError) as e:
         qdd.load_gauge(lat, U)
     assert e.value.status == qdd.QDD_ERR_ARG
+
+
+@pytest.mark.parametrize("dims,host", [((16, 16, 8, 32), True), ((8, 8, 4, 16), True), ((8, 8, 4, 16), False), ((6, 4, 4, 10), True)])
+def test_load_gauge_with_clover(qdd, oracle_mod, dims, host):
+    """qdd_load_gauge_clover builds the clover term while the links load (for
+    host links and Lt = 16 or 32, in 8 groups of t-slices as the neighbouring
+    groups arrive; otherwise after the conversion): D equals the oracle's, and bit
+    for bit the D of a lattice whose clover is built lazily by the first D."""
+    bc, kappa, csw = (1, 1, 1, -1), 0.124, 1.3
+    U = synth.gauge_field(dims, 0.3, 21)
+    psi = synth.gaussian_source(dims, 22)
+    ref = oracle_mod.Op(dims, bc, U, kappa, csw).dslash(psi)
+    a = qdd.create_lattice(dims, bc)
+    qdd.load_gauge(a, U if host else torch.from_numpy(U).cuda(), kappa, csw)
+    b = qdd.create_lattice(dims, bc)
+    qdd.load_gauge(b, U)
+    for prec in ("f64", "f32", "f16"):
+        oa, ob = np.empty_like(psi), np.empty_like(psi)
+        qdd.dslash(a, oa, psi, kappa, csw, prec)
+        qdd.dslash(b, ob, psi, kappa, csw, prec)
+        assert np.array_equal(oa, ob), prec
+        assert rel(oa, ref) <= TOL_D[prec] and max_elem(oa, ref) <= 10 * TOL_D[prec], prec
+
+
+def test_load_gauge_with_clover_rejects_non_su3(qdd):
+    dims = (8, 8, 4, 16)
+    U = synth.gauge_field(dims, 0.3, 23)
+    U[300, 1] *= np.exp(0.2j)
+    lat = qdd.create_lattice(dims)
+    with pytest.raises(qdd.QddError) as e:
+        qdd.load_gauge(lat, U, 0.12, 1.0)
+    assert e.value.status == qdd.QDD_ERR_ARG
+    psi = synth.gaussian_source(dims, 24)
+    with pytest.raises(qdd.QddError) as e:
+        qdd.dslash(lat, np.empty_like(psi), psi, 0.12, 1.0, "f32")
+    assert e.value.status == qdd.QDD_ERR_STATE
