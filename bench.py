@@ -878,19 +878,27 @@ def run_workload(args):
                 qdd.load_gauge(lat, dU)
             return qdd.solve_batch(lats, phis, etas, kap, [CSW] * len(lats), TOL, params)
 
-        def timed(params):
-            for _ in range(args.warmup):
-                run_batch(params)
-            torch.cuda.synchronize()
-            n0 = qdd.kernel_launches()
-            t0 = time.perf_counter()
-            for _ in range(args.steps):
-                infos = run_batch(params)
-            torch.cuda.synchronize()
+        def timed(params, lists=True):
+            prev = qdd.set_batch_lists(lists)
+            try:
+                for _ in range(args.warmup):
+                    run_batch(params)
+                torch.cuda.synchronize()
+                n0 = qdd.kernel_launches()
+                t0 = time.perf_counter()
+                for _ in range(args.steps):
+                    infos = run_batch(params)
+                torch.cuda.synchronize()
+            finally:
+                qdd.set_batch_lists(prev)
             return (time.perf_counter() - t0) / args.steps * 1e3, (qdd.kernel_launches() - n0) // args.steps, infos
 
-        ms_shared, _, _ = timed(shared)
+        # with the work lists (compatible lattices share each launch of an
+        # iteration) and without (every lattice launches its own kernels)
+        ms_shared, launches_shared, _ = timed(shared)
+        ms_shared_own, launches_shared_own, _ = timed(shared, lists=False)
         ms, launches, infos = timed([None] * len(lats))   # per-size tuned parameters from the cache
+        ms_own, launches_own, _ = timed([None] * len(lats), lists=False)
         res = []
         for d, (U, eta), phi in zip(draws, checks, phis):
             op = oracle.Op(d["dims"], BC, U, d["kappa"], CSW, store_clover=False)
@@ -913,6 +921,13 @@ def run_workload(args):
                "tuned_per_shape": {"x".join(map(str, k)): v for k, v in tuned.items()},
                "one_shared_setting_s": round(ms_shared / 1e3, 4),
                "shared_setting": {"block": list(shared.block), "n_dominv": shared.n_dominv, "n_ras": shared.n_ras},
+               "work_lists": {"tuned_s": round(ms / 1e3, 4), "tuned_own_launches_s": round(ms_own / 1e3, 4),
+                              "shared_s": round(ms_shared / 1e3, 4),
+                              "shared_own_launches_s": round(ms_shared_own / 1e3, 4),
+                              "launches_per_step": {"tuned": int(launches), "tuned_own": int(launches_own),
+                                                    "shared": int(launches_shared),
+                                                    "shared_own": int(launches_shared_own)},
+                              "note": "own launches: every lattice launches its own kernels (forked in the graph)"},
                "sum_of_single_tuned_solves_s": round(ms_single / 1e3, 4),
                "gpu_launches_per_step": int(launches), "note": "graph replays count the launches they contain"}
     rec["total_wall_s"] = round(time.perf_counter() - t_all, 1)

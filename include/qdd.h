@@ -260,6 +260,24 @@ qdd_status qdd_solve_batch_each(qdd_lattice *const *lats, double *const *phi, co
                                 const double *kappa, const double *c_sw, double tol,
                                 const qdd_solver_params *const *params, qdd_solve_info *info);
 
+/* Work lists for batches (qdd_solve_batch, qdd_solve_batch_each), on (1) by
+ * default.  While on, the lattices of a batch with FP16 inner storage
+ * (inner_prec QDD_F16) that share n_ras and the number of sites per RAS
+ * domain (128 or 256, overlap 0, x extents divisible by 4), with one
+ * right-hand side each and the RAS Schwarz variant, run each step of their
+ * inner iteration as one launch over all of them, in groups of up to 16
+ * lattices: every sweep of K_RAS is one launch over the (lattice, domain)
+ * items of the group (Alg. 1 lines 4-8 for all domains of all its
+ * lattices), every D one launch over the concatenated site ranges, and the
+ * closing BiCGStab update one launch.  Their blockings, n_dominv, kappa,
+ * tolerances and sizes may differ.  Other lattices, and every lattice while
+ * off, launch their own kernels (forked across their streams in the graph).
+ * The choice changes the launches, not the arithmetic of a site or a
+ * domain; the dot products of a lattice are summed over a different number
+ * of blocks, so its iterates agree to rounding.  Process-wide; the previous
+ * setting is returned in *previous when it is not NULL. */
+qdd_status qdd_set_batch_lists(int on, int *previous);
+
 /* The tuning cache: the parameters the last qdd_autotune in this process
  * chose for a lattice of the same extents, boundary signs and right-hand-side
  * count (the paper's parameter survey of Sec. 5, kept per lattice shape).

@@ -600,6 +600,14 @@ qdd_status qdd_solve_batch(qdd_lattice *const *lats, double *const *phi, const d
     return solve_batch_common(lats, phi, eta, n, kappa, c_sw, tol, ps.data(), info);
 }
 
+qdd_status qdd_set_batch_lists(int on, int *previous)
+{
+    g_err.clear();
+    if (previous) *previous = batch_lists() ? 1 : 0;
+    set_batch_lists(on != 0);
+    return QDD_OK;
+}
+
 qdd_status qdd_solve_batch_each(qdd_lattice *const *lats, double *const *phi, const double *const *eta, int n,
                                 const double *kappa, const double *c_sw, double tol,
                                 const qdd_solver_params *const *params, qdd_solve_info *info)

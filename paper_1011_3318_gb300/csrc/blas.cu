@@ -7,6 +7,8 @@
 // no host round trip is needed inside an iteration).  Kernels of a solver
 // iteration return at once when the status is no longer "running", which
 // lets the host enqueue several iterations ahead of the convergence check.
+#include <cstring>
+
 #include "device.cuh"
 #include "df64.cuh"
 #include "lib.h"
@@ -145,17 +147,14 @@ __global__ void __launch_bounds__(BLAS_NT) blas_kernel(BlasArgs a)
 
 // x += alpha phat + omega shat ; r = s - omega t ; then rho' = <rhat, r>,
 // |r|^2 and beta = (rho'/rho)(alpha/omega).  f = {x, phat, shat, r, s, t, rhat}.
+// Block bid of the nblk blocks of right-hand side r, whose vectors `a`
+// already points at and whose solver runs.
 template <int P>
-__global__ void __launch_bounds__(BLAS_NT) bicg_xr_kernel(BlasArgs a)
+__device__ __forceinline__ void bicg_xr_core(const BlasArgs &a, int r, unsigned bid, unsigned nblk)
 {
     typedef typename RealOf<P>::T T;
-    const int r = blockIdx.x % a.nrhs;
-    const unsigned bid = blockIdx.x / a.nrhs, nblk = gridDim.x / a.nrhs;
     Scalars *sc = a.sc + r;
-    if (sc->status != S_RUN) return;
     const long long V = a.V;
-#pragma unroll
-    for (int i = 0; i < 8; i++) a.f[i] = rhs_view<P>(a.f[i], V, r);
     const C<T> al = {(T)sc->alpha.x, (T)sc->alpha.y};
     const C<T> om = {(T)sc->omega.x, (T)sc->omega.y};
     T part[3] = {0, 0, 0};
@@ -198,6 +197,39 @@ __global__ void __launch_bounds__(BLAS_NT) bicg_xr_kernel(BlasArgs a)
     }
 }
 
+template <int P>
+__global__ void __launch_bounds__(BLAS_NT) bicg_xr_kernel(BlasArgs a)
+{
+    const int r = blockIdx.x % a.nrhs;
+    const unsigned bid = blockIdx.x / a.nrhs, nblk = gridDim.x / a.nrhs;
+    if (a.sc[r].status != S_RUN) return;
+#pragma unroll
+    for (int i = 0; i < 8; i++) a.f[i] = rhs_view<P>(a.f[i], a.V, r);
+    bicg_xr_core<P>(a, r, bid, nblk);
+}
+
+// B_XR on the lattices of a batch in one launch: lattice i owns the blocks
+// first[i] .. first[i+1]-1 and has one right-hand side; one whose solver no
+// longer runs is skipped.
+struct BlasList {
+    int n;
+    int first[LIST_MAX + 1];
+    BlasArgs a[LIST_MAX];
+};
+static_assert(sizeof(BlasList) <= 32000, "kernel parameter size");
+
+template <int P>
+__global__ void __launch_bounds__(BLAS_NT) bicg_xr_list_kernel(const __grid_constant__ BlasList L)
+{
+    __shared__ BlasArgs sa;
+    const int i = list_member(L.first, L.n);
+    const BlasArgs &ga = L.a[i];
+    if (ga.sc->status != S_RUN) return;  // uniform over the block
+    copy_words(&sa, &ga, sizeof(BlasArgs));
+    __syncthreads();
+    bicg_xr_core<P>(sa, 0, blockIdx.x - (unsigned)L.first[i], (unsigned)(L.first[i + 1] - L.first[i]));
+}
+
 static int blas_blocks(long long V, int max_blocks)
 {
     long long nb = (V + BLAS_NT - 1) / BLAS_NT;
@@ -226,6 +258,42 @@ static cudaError_t launch_blas_p(int op, const BlasArgs &a, cudaStream_t st)
     }
     note_launch();
     return cudaGetLastError();
+}
+
+// The resident grid (blas_blocks) shared by the lattices in proportion to
+// their sizes.
+template <int P>
+static cudaError_t launch_xr_list(const BlasArgs *as, int n, cudaStream_t st)
+{
+    if (n < 1 || n > LIST_MAX) return cudaErrorInvalidValue;
+    BlasList L;
+    memset(&L, 0, sizeof(L));
+    L.n = n;
+    long long vtot = 0;
+    for (int i = 0; i < n; i++) {
+        if (as[i].nrhs != 1 || !as[i].sc || as[i].V <= 0) return cudaErrorInvalidValue;
+        vtot += as[i].V;
+    }
+    const long long cap = 152LL * 8;
+    long long total = 0;
+    for (int i = 0; i < n; i++) {
+        L.a[i] = as[i];
+        long long nb = blas_blocks(as[i].V, as[i].rs.max_blocks);
+        const long long share = (cap * as[i].V + vtot - 1) / vtot;
+        if (nb > share) nb = share;
+        L.first[i] = (int)total;
+        total += nb < 1 ? 1 : nb;
+    }
+    L.first[n] = (int)total;
+    bicg_xr_list_kernel<P><<<(unsigned)total, BLAS_NT, 0, st>>>(L);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blas_list(int prec, int op, const BlasArgs *as, int n, cudaStream_t st)
+{
+    if (op != B_XR || prec != P16) return cudaErrorInvalidValue;
+    return launch_xr_list<P16>(as, n, st);
 }
 
 cudaError_t launch_blas(int prec, int op, const BlasArgs &a, cudaStream_t st)

@@ -623,6 +623,22 @@ __device__ __forceinline__ bool grid_sum(T (&t)[N], double (&v)[N], double *part
     return threadIdx.x == 0;
 }
 
+// The lattice of this block in a work-list launch, whose lattice i owns the
+// blocks first[i] .. first[i+1]-1 (n lattices).
+__device__ __forceinline__ int list_member(const int *first, int n)
+{
+    int i = 0;
+    while (i + 1 < n && (int)blockIdx.x >= first[i + 1]) i++;
+    return i;
+}
+
+// dst = src (bytes a multiple of 4), by all threads of the block.
+__device__ __forceinline__ void copy_words(void *dst, const void *src, unsigned bytes)
+{
+    for (unsigned k = threadIdx.x; k < bytes / 4; k += blockDim.x)
+        static_cast<unsigned *>(dst)[k] = static_cast<const unsigned *>(src)[k];
+}
+
 // Reduction scratch of right-hand side r.
 __device__ __forceinline__ double *rs_partials(const ReduceScratch &rs, int r)
 {

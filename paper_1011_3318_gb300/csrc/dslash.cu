@@ -11,6 +11,7 @@
 // spinor out) for HBM.  Epilogues fuse the residual update and the dot
 // products of BiCGStab, so those need no separate pass over memory.
 #include <atomic>
+#include <cstring>
 
 #include "device.cuh"
 #include "lib.h"
@@ -64,21 +65,16 @@ __device__ __forceinline__ void dslash_site(const DslashArgs &a, long long V, lo
     }
 }
 
+// Block bid of the nblk blocks that cover right-hand side r, whose vectors
+// `a` already points at (the caller has checked that its solver runs, where
+// the epilogue reduces).
 template <int P, int EPI, int NT>
-__device__ __forceinline__ void dslash_body(DslashArgs a)
+__device__ __forceinline__ void dslash_core(const DslashArgs &a, int r, unsigned bid, unsigned nblk)
 {
     typedef typename RealOf<P>::T T;
     constexpr int NRED = (EPI == EPI_XMY_NORM) ? 1 : (EPI == EPI_RV || EPI == EPI_TS) ? 3 : 0;
-    const int r = blockIdx.x % a.nrhs;
-    const unsigned bid = blockIdx.x / a.nrhs, nblk = gridDim.x / a.nrhs;
     const long long V = a.g.V;
     Scalars *sc = a.sc ? a.sc + r : nullptr;
-    if constexpr (EPI == EPI_RV || EPI == EPI_TS) {
-        if (sc->status != S_RUN) return;
-    }
-    a.out = rhs_view<P>(a.out, V, r);
-    a.in = rhs_view<P>(a.in, V, r);
-    a.y = rhs_view<P>(a.y, V, r);
     T part[3] = {0, 0, 0};
 
     // one site per thread for the plain epilogues; the reducing ones run on a
@@ -124,6 +120,21 @@ __device__ __forceinline__ void dslash_body(DslashArgs a)
     }
 }
 
+template <int P, int EPI, int NT>
+__device__ __forceinline__ void dslash_body(DslashArgs a)
+{
+    const int r = blockIdx.x % a.nrhs;
+    const unsigned bid = blockIdx.x / a.nrhs, nblk = gridDim.x / a.nrhs;
+    const long long V = a.g.V;
+    if constexpr (EPI == EPI_RV || EPI == EPI_TS) {
+        if (a.sc[r].status != S_RUN) return;
+    }
+    a.out = rhs_view<P>(a.out, V, r);
+    a.in = rhs_view<P>(a.in, V, r);
+    a.y = rhs_view<P>(a.y, V, r);
+    dslash_core<P, EPI, NT>(a, r, bid, nblk);
+}
+
 // FP32 and FP64 keep the compiler's register choice (a register bound there
 // makes them spill heavily).  The FP16 kernel works on packed FP32 pairs
 // (pair.cuh) with up to 128 registers, two blocks of 256 threads per SM: at 3
@@ -141,10 +152,33 @@ __global__ void __launch_bounds__(NT, 2) dslash_f16_kernel(DslashArgs a)
     dslash_body<P16, EPI, NT>(a);
 }
 
+// D on the lattices of a batch in one launch (a concatenated site range),
+// FP16 storage: lattice i owns the blocks first[i] .. first[i+1]-1.  Each
+// lattice has one right-hand side; one whose solver no longer runs is
+// skipped whole.  The arguments are copied to shared memory once per block.
+struct DslashList {
+    int n;
+    int first[LIST_MAX + 1];
+    DslashArgs a[LIST_MAX];
+};
+static_assert(sizeof(DslashList) <= 32000, "kernel parameter size");
+
+template <int P, int EPI, int NT>
+__global__ void __launch_bounds__(NT, 2) dslash_list_kernel(const __grid_constant__ DslashList L)
+{
+    __shared__ DslashArgs sa;
+    const int i = list_member(L.first, L.n);
+    const DslashArgs &ga = L.a[i];
+    if (ga.sc->status != S_RUN) return;  // uniform over the block
+    copy_words(&sa, &ga, sizeof(DslashArgs));
+    __syncthreads();
+    dslash_core<P, EPI, NT>(sa, 0, blockIdx.x - (unsigned)L.first[i], (unsigned)(L.first[i + 1] - L.first[i]));
+}
+
 // SMs x resident blocks per SM of one kernel on the current device, queried
 // once per device (the values are the same for every caller).
-template <int P, int EPI>
-static long long resident_blocks(void (*kernel)(DslashArgs), int nt)
+template <int P, int EPI, typename K>
+static long long resident_blocks(K kernel, int nt)
 {
     static std::atomic<int> cache[64];
     int dev = 0;
@@ -194,6 +228,60 @@ static cudaError_t launch_prec(int epi, const DslashArgs &a, cudaStream_t st)
     case EPI_TS: return launch_one<P, EPI_TS>(a, st);
     }
     return cudaErrorInvalidValue;
+}
+
+// Blocks per lattice: one site per thread for the plain epilogues; for the
+// reducing ones the resident grid shared in proportion to the lattice sizes.
+template <int P, int EPI>
+static cudaError_t launch_list_one(const DslashArgs *as, int n, cudaStream_t st)
+{
+    constexpr int NT = 256;
+    constexpr bool RED = EPI == EPI_XMY_NORM || EPI == EPI_RV || EPI == EPI_TS;
+    auto kernel = dslash_list_kernel<P, EPI, NT>;
+    if (n < 1 || n > LIST_MAX) return cudaErrorInvalidValue;
+    DslashList L;
+    memset(&L, 0, sizeof(L));
+    L.n = n;
+    long long vtot = 0;
+    for (int i = 0; i < n; i++) {
+        if (as[i].nrhs != 1 || !as[i].sc || as[i].g.V <= 0) return cudaErrorInvalidValue;
+        vtot += as[i].g.V;
+    }
+    const long long cap = RED ? resident_blocks<P, EPI>(kernel, NT) : 0;
+    long long total = 0;
+    for (int i = 0; i < n; i++) {
+        L.a[i] = as[i];
+        long long nb = (as[i].g.V + NT - 1) / NT;
+        if (RED && cap > 0) {
+            const long long share = (cap * as[i].g.V + vtot - 1) / vtot;
+            if (nb > share) nb = share;
+        }
+        if (nb > as[i].rs.max_blocks) nb = as[i].rs.max_blocks;
+        L.first[i] = (int)total;
+        total += nb < 1 ? 1 : nb;
+    }
+    L.first[n] = (int)total;
+    if (total >= (1LL << 31)) return cudaErrorInvalidConfiguration;
+    kernel<<<(unsigned)total, NT, 0, st>>>(L);
+    note_launch();
+    return cudaGetLastError();
+}
+
+// (the epilogues of a BiCGStab iteration preconditioned by K_RAS)
+template <int P>
+static cudaError_t launch_list_prec(int epi, const DslashArgs *as, int n, cudaStream_t st)
+{
+    switch (epi) {
+    case EPI_XMY: return launch_list_one<P, EPI_XMY>(as, n, st);
+    case EPI_RV: return launch_list_one<P, EPI_RV>(as, n, st);
+    case EPI_TS: return launch_list_one<P, EPI_TS>(as, n, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_dslash_list(int prec, int epi, const DslashArgs *as, int n, cudaStream_t st)
+{
+    return prec == P16 ? launch_list_prec<P16>(epi, as, n, st) : cudaErrorInvalidValue;
 }
 
 cudaError_t launch_dslash(int prec, int epi, const DslashArgs &a, cudaStream_t st)

@@ -196,6 +196,26 @@ int ras_default_slots();
 
 bool domain_geom(const Geom &g, const int block[4], int s, DomainGeom *dg, std::string *why);
 
+// ---------------------------------------------------------------- work lists
+// One launch over several lattices of a batch: lattice i of a list owns the
+// blocks first[i] .. first[i+1]-1 of the grid, and the per-lattice arguments
+// travel as one kernel parameter.  Every lattice of a list has one
+// right-hand side and a solver status (sc); the blocks of a lattice whose
+// solver no longer runs return at once.
+constexpr int LIST_MAX = 16;
+// Lists exist for FP16 storage only.
+// Whether sweep `a` can be an item of launch_ras_list: FP16 storage, a domain
+// of 128 or 256 sites without overlap, staged by TMA (the same test as the
+// one-lattice launch), one right-hand side.
+bool ras_list_ok(int prec, const RasArgs &a);
+// One RAS sweep (launch_ras_block) of n <= LIST_MAX lattices whose domains
+// all have the same number of sites.
+cudaError_t launch_ras_list(int prec, const RasArgs *a, int n, cudaStream_t st);
+// D with epilogue EPI_XMY, EPI_RV or EPI_TS on n <= LIST_MAX lattices.
+cudaError_t launch_dslash_list(int prec, int epi, const DslashArgs *a, int n, cudaStream_t st);
+// The BiCGStab update B_XR on n <= LIST_MAX lattices.
+cudaError_t launch_blas_list(int prec, int op, const BlasArgs *a, int n, cudaStream_t st);
+
 }  // namespace qdd
 
 struct qdd_field {
@@ -286,6 +306,9 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                             const double *kappa, const double *csw, double tol, const qdd_solver_params *const *ps,
                             qdd_solve_info *const *infos);
 void work_free(qdd_work *w);
+// Whether batches run compatible lattices as work-list groups (process-wide).
+void set_batch_lists(bool on);
+bool batch_lists();
 // The tuning cache: the parameters qdd_autotune chose, per lattice shape
 // (extents, boundary signs, right-hand-side count), for the process.
 void tuned_store(const qdd_lattice *lat, const qdd_solver_params &p);

@@ -603,7 +603,6 @@ __device__ __forceinline__ void ras_mr_domain_x2(const RasArgs &a, const LocSite
     const bool act = s.m & M_ACT;
     float4 *R4 = reinterpret_cast<float4 *>(srho);
     float4 *V4 = reinterpret_cast<float4 *>(sv);
-    const uint4 *Ap = reinterpret_cast<const uint4 *>(sA);
     for (int it = 0; it < a.n_iter; it++) {
         __syncthreads();
         f2 AUR[3], AUI[3], ADR[3], ADI[3];
@@ -820,19 +819,17 @@ struct RasTma {
 // instead of every thread loading its site's 24 values through registers.
 // Input vectors land in the rho/v area as raw FP16 (or FP32) planes and are
 // combined (fused update) and widened there.
+//
+// ras_tma_body is the sweep of one (domain, right-hand side) item, with `a`
+// already pointing at right-hand side rr's vectors; ras_tma_kernel runs it on
+// the domains of one lattice, ras_list_kernel on a work list spanning lattices.
 template <int P, int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) ras_tma_kernel(RasArgs a, const __grid_constant__ RasTma tm)
+__device__ __forceinline__ void ras_tma_body(const RasArgs &a, const RasTma &tm, int rr, int dom)
 {
     constexpr bool SC = P == P16;
     constexpr int RAW = P == P16 ? 52 : 96;      // bytes per site of one staged input vector
     constexpr int LW = P == P16 ? 2 : 4;         // 32-bit words per site of a link plane
     constexpr int INP = P == P16 ? 3 : 6;        // planes of an input vector
-    const int rr = blockIdx.x % a.nrhs, dom = blockIdx.x / a.nrhs;
-    if (a.sc && a.sc[rr].status != S_RUN) return;
-    a.in = rhs_view<P>(a.in, a.g.V, rr);
-    a.vout = rhs_view<P>(a.vout, a.g.V, rr);
-    a.acc = rhs_view<P>(a.acc, a.g.V, rr);
-    if (a.asum) a.asum += (long long)rr * 6 * a.g.V;
     C<float> fb, fc;
     fuse_coefs(a, rr, fb, fc);
     extern __shared__ __align__(128) unsigned char smem_dyn[];
@@ -925,6 +922,46 @@ __global__ void __launch_bounds__(NT, 512 / NT) ras_tma_kernel(RasArgs a, const 
         if (a.fuse != RAS_FUSE_NONE) store_spinor<P>(a.in, a.g.V, s.x, r);
     }
     ras_mr_domain<P, NT, SC, false>(a, s, srho, sv, sA, lU, lA, wpart);
+}
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) ras_tma_kernel(RasArgs a, const __grid_constant__ RasTma tm)
+{
+    const int rr = blockIdx.x % a.nrhs, dom = blockIdx.x / a.nrhs;
+    if (a.sc && a.sc[rr].status != S_RUN) return;
+    a.in = rhs_view<P>(a.in, a.g.V, rr);
+    a.vout = rhs_view<P>(a.vout, a.g.V, rr);
+    a.acc = rhs_view<P>(a.acc, a.g.V, rr);
+    if (a.asum) a.asum += (long long)rr * 6 * a.g.V;
+    ras_tma_body<P, NT>(a, tm, rr, dom);
+}
+
+// The sweeps of several lattices in one launch: a work list of (lattice,
+// domain) items, lattice i owning the blocks first[i] .. first[i+1]-1, one
+// domain each.  Every lattice has one right-hand side and domains of NT
+// sites without overlap; blockings, N_dominv, kappa, fields and the fused
+// update differ freely.  The tensor maps stay in the parameter space (their
+// generic address is what the copies take); the other arguments are copied
+// to shared memory once per CTA, since the lattice index is only known at
+// run time.
+struct RasList {
+    RasTma tm[LIST_MAX];
+    RasArgs a[LIST_MAX];
+    int first[LIST_MAX + 1];
+    int n;
+};
+static_assert(sizeof(RasList) <= 32000, "kernel parameter size");
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) ras_list_kernel(const __grid_constant__ RasList L)
+{
+    __shared__ RasArgs sa;
+    const int i = list_member(L.first, L.n);
+    const RasArgs &ga = L.a[i];
+    if (ga.sc[0].status != S_RUN) return;  // uniform over the CTA
+    copy_words(&sa, &ga, sizeof(RasArgs));
+    __syncthreads();
+    ras_tma_body<P, NT>(sa, L.tm[i], 0, (int)blockIdx.x - L.first[i]);
 }
 
 // ---------------------------------------------------------------- clusters
@@ -1698,6 +1735,57 @@ static cudaError_t launch_tma(const RasArgs &a, const RasTma &tm, cudaStream_t s
     ras_tma_kernel<P, NT><<<a.dg.ndom * a.nrhs, NT, smem, st>>>(a, tm);
     note_launch();
     return cudaGetLastError();
+}
+
+template <int P>
+static bool ras_list_ok_p(const RasArgs &a)
+{
+    const int n = a.dg.nloc;
+    if ((n != 128 && n != 256) || a.nrhs != 1 || !a.sc || a.asum || a.color != 0) return false;
+    RasTma tm;
+    return tma_maps<P>(a, n, &tm);
+}
+
+bool ras_list_ok(int prec, const RasArgs &a) { return prec == P16 && ras_list_ok_p<P16>(a); }
+
+template <int P, int NT>
+static cudaError_t launch_list_nt(const RasArgs *as, int n, cudaStream_t st)
+{
+    const size_t smem = RasSmem<P, false>::bytes(NT, P == P16) + 128;
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || !((done.load() >> dev) & 1ull)) {
+        cudaError_t e =
+            cudaFuncSetAttribute(ras_list_kernel<P, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) done.fetch_or(1ull << dev);
+    }
+    // one parameter block, built on the host per launch (a captured graph
+    // keeps its own copy)
+    static thread_local RasList L;
+    memset(&L, 0, sizeof(L));
+    L.n = n;
+    long long total = 0;
+    for (int i = 0; i < n; i++) {
+        if (as[i].dg.nloc != NT || !ras_list_ok_p<P>(as[i]) || !tma_maps<P>(as[i], NT, &L.tm[i]))
+            return cudaErrorInvalidValue;
+        L.a[i] = as[i];
+        L.first[i] = (int)total;
+        total += as[i].dg.ndom;
+    }
+    L.first[n] = (int)total;
+    if (total >= (1LL << 31)) return cudaErrorInvalidConfiguration;
+    ras_list_kernel<P, NT><<<(unsigned)total, NT, smem, st>>>(L);
+    note_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ras_list(int prec, const RasArgs *as, int n, cudaStream_t st)
+{
+    if (n < 1 || n > LIST_MAX) return cudaErrorInvalidValue;
+    if (prec != P16) return cudaErrorInvalidValue;
+    return as[0].dg.nloc == 256 ? launch_list_nt<P16, 256>(as, n, st) : launch_list_nt<P16, 128>(as, n, st);
 }
 
 // vout = asum, acc = asum (or acc += asum) on every site: the additive

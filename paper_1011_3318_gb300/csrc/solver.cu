@@ -17,9 +17,12 @@
 // iterations between status reads.  Per-kernel profiling records its event
 // pairs as nodes of the graph.  When a lattice uses the legacy default
 // stream, the same work is launched eagerly.
+#include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <memory>
 #include <vector>
 
 #include "lib.h"
@@ -128,8 +131,8 @@ static SpinorView inner(qdd_lattice *lat, int prec, int k)
 
 static SpinorView outer(qdd_lattice *lat, int k) { return SpinorView{lat->work->o_d[k], nullptr}; }
 
-static qdd_status blas(qdd_lattice *lat, int prec, int op, std::initializer_list<SpinorView> fs, int aux_slot = 0,
-                       double tol2 = 0.0, unsigned long long active = ~0ull, Scalars *sc = nullptr)
+static BlasArgs blas_args(qdd_lattice *lat, std::initializer_list<SpinorView> fs, int aux_slot = 0, double tol2 = 0.0,
+                          unsigned long long active = ~0ull, Scalars *sc = nullptr)
 {
     BlasArgs a;
     memset(&a, 0, sizeof(a));
@@ -142,6 +145,13 @@ static qdd_status blas(qdd_lattice *lat, int prec, int op, std::initializer_list
     a.tol2_rel = tol2;
     a.nrhs = lat->nrhs;
     a.active = active;
+    return a;
+}
+
+static qdd_status blas(qdd_lattice *lat, int prec, int op, std::initializer_list<SpinorView> fs, int aux_slot = 0,
+                       double tol2 = 0.0, unsigned long long active = ~0ull, Scalars *sc = nullptr)
+{
+    const BlasArgs a = blas_args(lat, fs, aux_slot, tol2, active, sc);
     ProfScope ps(lat, QDD_K_BLAS);
     cudaError_t e = launch_blas(prec, op, a, lat->stream);
     return e == cudaSuccess ? QDD_OK : cuda_fail(e, "blas kernel");
@@ -166,8 +176,8 @@ static qdd_status read_scalars(const std::vector<qdd_lattice *> &lats, bool oute
     return QDD_OK;
 }
 
-qdd_status run_dslash(qdd_lattice *lat, int prec, int epi, SpinorView out, SpinorView in, SpinorView y, double kappa,
-                      int aux_slot, Scalars *sc)
+static DslashArgs dslash_args(qdd_lattice *lat, int prec, SpinorView out, SpinorView in, SpinorView y, double kappa,
+                              int aux_slot, Scalars *sc)
 {
     DslashArgs a;
     memset(&a, 0, sizeof(a));
@@ -182,6 +192,13 @@ qdd_status run_dslash(qdd_lattice *lat, int prec, int epi, SpinorView out, Spino
     a.sc = sc ? sc : lat->sc;
     a.aux_slot = aux_slot;
     a.nrhs = lat->nrhs;
+    return a;
+}
+
+qdd_status run_dslash(qdd_lattice *lat, int prec, int epi, SpinorView out, SpinorView in, SpinorView y, double kappa,
+                      int aux_slot, Scalars *sc)
+{
+    const DslashArgs a = dslash_args(lat, prec, out, in, y, kappa, aux_slot, sc);
     ProfScope ps(lat, prec == P64 ? QDD_K_DSLASH_F64 : QDD_K_DSLASH);
     cudaError_t e = launch_dslash(prec, epi, a, lat->stream);
     return e == cudaSuccess ? QDD_OK : cuda_fail(e, "dslash kernel");
@@ -346,6 +363,193 @@ qdd_status enqueue_iteration(Member &m)
     return blas(lat, prec, B_XR, {F(W_X), phat, shat, F(W_R), F(W_S), F(W_T), F(W_RHAT)});
 }
 
+// ----------------------------------------------------------- work-list groups
+// Lattices of a batch whose inner iterations share work-list launches: each
+// step of the iteration (every RAS sweep, every D, the closing update) is one
+// launch over the (lattice, domain) or (lattice, site block) items of all
+// members, instead of one launch per lattice.  Members have FP16 inner
+// storage and share NRAS and the number of sites per domain (128 or 256,
+// without overlap, staged by TMA); blockings, N_dominv, kappa, tolerances and
+// lattice sizes are free.  Each has one right-hand side.
+struct Group {
+    std::vector<int> idx;          // members (indices into the batch)
+    std::vector<cudaEvent_t> ev;   // ordering between the first member's stream and the others'
+    Group() = default;
+    Group(const Group &) = delete;  // owns its events
+    Group &operator=(const Group &) = delete;
+    ~Group()
+    {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+    }
+};
+typedef std::vector<std::unique_ptr<Group>> Groups;
+
+std::atomic<int> g_batch_lists{1};
+
+// The arguments of sweep q of the preconditioner application k (0: phat =
+// K p, 1: shat = K s) of one BiCGStab iteration, as ras_apply_fields sets
+// them for the fused updates.
+RasArgs sweep_args(const Member &m, int k, int q)
+{
+    qdd_lattice *lat = m.lat;
+    const int prec = m.prec;
+    auto F = [&](int w) { return inner(lat, prec, w); };
+    RasArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.g = lat->g;
+    ra.dg = m.dg;
+    ra.U = links_of(lat, prec);
+    ra.A = clover_of(lat, prec);
+    ra.kappa = (float)m.kappa;
+    ra.n_iter = m.prm.n_dominv;
+    ra.sc = lat->sc;
+    ra.scratch = lat->ras_scratch;
+    ra.slots = ras_default_slots();
+    ra.nrhs = lat->nrhs;
+    ra.variant = m.prm.ras_kernel;
+    ra.err = lat->ras_err;
+    const bool last = q == m.prm.n_ras - 1;
+    ra.in = q > 0 ? F(W_RHO) : k == 0 ? F(W_P) : F(W_S);
+    ra.vout = last ? SpinorView{nullptr, nullptr} : F(W_VR);
+    ra.acc = k == 0 ? F(W_PHAT) : F(W_SHAT);
+    ra.accumulate = q > 0;
+    ra.fuse = q > 0 ? RAS_FUSE_NONE : k == 0 ? RAS_FUSE_P : RAS_FUSE_S;
+    ra.fr = F(W_R);
+    ra.fz = F(W_V);
+    return ra;
+}
+
+bool list_eligible(const Member &m)
+{
+    if (!m.use_ras || m.prec != P16 || m.lat->nrhs != 1) return false;
+    const SchwarzPlan sp = schwarz_plan(m.prm.schwarz, m.dg);
+    if (sp.variant != QDD_SCHWARZ_RAS || sp.colors != 1 || sp.sum) return false;
+    if (!ras_can_fuse(m.prec, m.dg, RAS_FUSE_P, m.prm.schwarz) ||
+        !ras_can_fuse(m.prec, m.dg, RAS_FUSE_S, m.prm.schwarz))
+        return false;
+    for (int k = 0; k < 2; k++)
+        for (int q = 0; q < m.prm.n_ras; q++)
+            if (!ras_list_ok(m.prec, sweep_args(m, k, q))) return false;
+    return true;
+}
+
+// Splits the batch into groups of at most LIST_MAX compatible lattices;
+// lattices without a partner keep their own launches (solo).
+qdd_status form_groups(const std::vector<Member> &ms, bool enable, Groups &groups, std::vector<int> &solo)
+{
+    std::vector<int> cand;
+    for (size_t i = 0; i < ms.size(); i++) {
+        if (enable && list_eligible(ms[i])) cand.push_back((int)i);
+        else solo.push_back((int)i);
+    }
+    std::vector<int> used(ms.size(), 0);
+    for (size_t a = 0; a < cand.size(); a++) {
+        const int i = cand[a];
+        if (used[i]) continue;
+        std::vector<int> idx{i};
+        used[i] = 1;
+        for (size_t b = a + 1; b < cand.size() && (int)idx.size() < LIST_MAX; b++) {
+            const int j = cand[b];
+            if (used[j] || ms[j].prec != ms[i].prec || ms[j].prm.n_ras != ms[i].prm.n_ras ||
+                ms[j].dg.nloc != ms[i].dg.nloc)
+                continue;
+            idx.push_back(j);
+            used[j] = 1;
+        }
+        if (idx.size() == 1) {
+            solo.push_back(i);
+            continue;
+        }
+        groups.emplace_back(new Group());
+        Group &g = *groups.back();
+        g.idx = idx;
+        g.ev.assign(idx.size(), nullptr);
+        for (auto &e : g.ev)
+            if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+                return cuda_fail(cudaGetLastError(), "event");
+    }
+    std::sort(solo.begin(), solo.end());
+    return QDD_OK;
+}
+
+// One BiCGStab iteration (as enqueue_iteration, with both fused updates) of
+// every member of a group, on the first member's stream, ordered after the
+// work queued on the other members' streams and before their next work.
+qdd_status enqueue_group(Group &g, std::vector<Member> &ms)
+{
+    const int n = (int)g.idx.size();
+    Member &m0 = ms[g.idx[0]];
+    qdd_lattice *lat0 = m0.lat;
+    cudaStream_t st = lat0->stream;
+    const int prec = m0.prec, nras = m0.prm.n_ras;
+    for (int i = 1; i < n; i++) {
+        cudaEventRecord(g.ev[i], ms[g.idx[i]].lat->stream);
+        cudaStreamWaitEvent(st, g.ev[i], 0);
+    }
+    RasArgs ra[LIST_MAX];
+    DslashArgs da[LIST_MAX];
+    BlasArgs ba[LIST_MAX];
+    auto F = [&](int i, int w) { return inner(ms[g.idx[i]].lat, prec, w); };
+    for (int k = 0; k < 2; k++) {
+        for (int q = 0; q < nras; q++) {
+            for (int i = 0; i < n; i++) ra[i] = sweep_args(ms[g.idx[i]], k, q);
+            cudaError_t e;
+            {
+                ProfScope ps(lat0, QDD_K_RAS);
+                e = launch_ras_list(prec, ra, n, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "RAS work-list kernel");
+            if (q == nras - 1) break;
+            // rho = in - D v
+            for (int i = 0; i < n; i++)
+                da[i] = dslash_args(ms[g.idx[i]].lat, prec, F(i, W_RHO), F(i, W_VR), ra[i].in, ms[g.idx[i]].kappa, 0,
+                                    nullptr);
+            {
+                ProfScope ps(lat0, QDD_K_DSLASH);
+                e = launch_dslash_list(prec, EPI_XMY, da, n, st);
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "dslash work-list kernel");
+        }
+        // v = D phat with alpha, or t = D shat with omega
+        for (int i = 0; i < n; i++)
+            da[i] = k == 0 ? dslash_args(ms[g.idx[i]].lat, prec, F(i, W_V), F(i, W_PHAT), F(i, W_RHAT),
+                                         ms[g.idx[i]].kappa, 0, nullptr)
+                           : dslash_args(ms[g.idx[i]].lat, prec, F(i, W_T), F(i, W_SHAT), F(i, W_S),
+                                         ms[g.idx[i]].kappa, 0, nullptr);
+        cudaError_t e;
+        {
+            ProfScope ps(lat0, QDD_K_DSLASH);
+            e = launch_dslash_list(prec, k == 0 ? EPI_RV : EPI_TS, da, n, st);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "dslash work-list kernel");
+    }
+    for (int i = 0; i < n; i++)
+        ba[i] = blas_args(ms[g.idx[i]].lat, {F(i, W_X), F(i, W_PHAT), F(i, W_SHAT), F(i, W_R), F(i, W_S), F(i, W_T),
+                                             F(i, W_RHAT)});
+    cudaError_t e;
+    {
+        ProfScope ps(lat0, QDD_K_BLAS);
+        e = launch_blas_list(prec, B_XR, ba, n, st);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "update work-list kernel");
+    cudaEventRecord(g.ev[0], st);
+    for (int i = 1; i < n; i++) cudaStreamWaitEvent(ms[g.idx[i]].lat->stream, g.ev[0], 0);
+    return QDD_OK;
+}
+
+// One iteration of every lattice: the groups' list launches and the solo
+// lattices' own launches.
+qdd_status enqueue_all(std::vector<Member> &ms, Groups &groups, const std::vector<int> &solo)
+{
+    qdd_status st;
+    for (auto &g : groups)
+        if ((st = enqueue_group(*g, ms)) != QDD_OK) return st;
+    for (int i : solo)
+        if ((st = enqueue_iteration(ms[i])) != QDD_OK) return st;
+    return QDD_OK;
+}
+
 bool graph_capable(const std::vector<Member> &ms)
 {
     for (size_t i = 0; i < ms.size(); i++) {
@@ -375,7 +579,7 @@ struct IterGraph {
     }
 };
 
-qdd_status build_graph(std::vector<Member> &ms, int chunk, IterGraph &g)
+qdd_status build_graph(std::vector<Member> &ms, Groups &groups, const std::vector<int> &solo, int chunk, IterGraph &g)
 {
     cudaStream_t s0 = ms[0].lat->stream;
     g.events.resize(ms.size() + 1, nullptr);
@@ -397,9 +601,7 @@ qdd_status build_graph(std::vector<Member> &ms, int chunk, IterGraph &g)
     qdd_status st = QDD_OK;
     cudaEventRecord(g.events[0], s0);
     for (size_t i = 1; i < ms.size(); i++) cudaStreamWaitEvent(ms[i].lat->stream, g.events[0], 0);
-    for (int c = 0; c < chunk && st == QDD_OK; c++)
-        for (Member &m : ms)
-            if (st == QDD_OK) st = enqueue_iteration(m);
+    for (int c = 0; c < chunk && st == QDD_OK; c++) st = enqueue_all(ms, groups, solo);
     for (size_t i = 1; i < ms.size(); i++) {
         cudaEventRecord(g.events[i], ms[i].lat->stream);
         cudaStreamWaitEvent(s0, g.events[i], 0);
@@ -422,6 +624,9 @@ qdd_status build_graph(std::vector<Member> &ms, int chunk, IterGraph &g)
 }
 
 }  // namespace
+
+void set_batch_lists(bool on) { g_batch_lists.store(on ? 1 : 0); }
+bool batch_lists() { return g_batch_lists.load() != 0; }
 
 qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, const double *const *eta_dev, int n,
                             const double *kappa, const double *csw, double tol, const qdd_solver_params *const *ps,
@@ -507,6 +712,11 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
     long long vmax = 0;
     for (Member &m : ms) vmax = std::max(vmax, m.lat->g.V);
     const int chunk = vmax >= (1 << 18) ? 2 : 4;
+    // work-list groups need the lattices on distinct streams (as the graph
+    // does) and their inner fields, allocated above
+    Groups groups;
+    std::vector<int> solo;
+    if ((st = form_groups(ms, graphs && !plain && g_batch_lists.load() != 0, groups, solo)) != QDD_OK) return st;
     IterGraph graph;
     bool have_graph = false;
     const bool nested_outer = !plain && ps[0]->outer_mode == 1;
@@ -547,9 +757,8 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                 if (!have_graph) {
                     // one eager iteration first: it sets kernel attributes and
                     // allocates scratch outside the capture
-                    for (Member &m : ms)
-                        if ((st = enqueue_iteration(m)) != QDD_OK) return st;
-                    if ((st = build_graph(ms, chunk, graph)) != QDD_OK) return st;
+                    if ((st = enqueue_all(ms, groups, solo)) != QDD_OK) return st;
+                    if ((st = build_graph(ms, groups, solo, chunk, graph)) != QDD_OK) return st;
                     have_graph = true;
                 } else {
                     // the graph runs on the first lattice's stream: order it after
@@ -570,8 +779,7 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                 }
             } else {
                 for (int c = 0; c < chunk; c++)
-                    for (Member &m : ms)
-                        if ((st = enqueue_iteration(m)) != QDD_OK) return st;
+                    if ((st = enqueue_all(ms, groups, solo)) != QDD_OK) return st;
             }
             if ((st = read_scalars(L)) != QDD_OK) return st;
             bool running = false;

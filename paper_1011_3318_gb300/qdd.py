@@ -45,7 +45,8 @@ ABI = ("qdd_version", "qdd_last_error", "qdd_default_params", "qdd_create_lattic
        "qdd_load_gauge", "qdd_dslash", "qdd_ras_apply", "qdd_solve", "qdd_field_create", "qdd_field_destroy",
        "qdd_field_import", "qdd_field_export", "qdd_dslash_field", "qdd_kernel_launches", "qdd_set_profiling",
        "qdd_profile_read", "qdd_measure_fma_peak", "qdd_ras_field_noalloc", "qdd_autotune", "qdd_solve_batch",
-       "qdd_solve_batch_each", "qdd_tuned_params", "qdd_load_gauge_clover", "qdd_test_ras_wait")
+       "qdd_solve_batch_each", "qdd_tuned_params", "qdd_load_gauge_clover", "qdd_set_batch_lists",
+       "qdd_test_ras_wait")
 
 # Kernel classes of the per-class GPU timers (qdd_profile).
 KCLASS = ("dslash", "dslash_f64", "ras", "blas", "convert", "clover")
@@ -112,6 +113,7 @@ def _load():
                                          ctypes.c_double, ctypes.POINTER(ctypes.POINTER(SolverParams)),
                                          ctypes.POINTER(SolveInfo)]
     lib.qdd_tuned_params.argtypes = [P, ctypes.POINTER(SolverParams)]
+    lib.qdd_set_batch_lists.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     lib.qdd_autotune.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                  ctypes.POINTER(SolverParams), ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     lib.qdd_ras_field_noalloc.argtypes = [P, P, P, P, P, ctypes.c_double, ctypes.c_double,
@@ -324,6 +326,14 @@ def tuned_params(lat: Lattice):
         return None
     _check(st, "qdd_tuned_params")
     return p
+
+
+def set_batch_lists(on: bool) -> bool:
+    """Turns the batch work lists (qdd_set_batch_lists) on or off; returns
+    the previous setting."""
+    prev = ctypes.c_int(0)
+    _check(_lib.qdd_set_batch_lists(1 if on else 0, ctypes.byref(prev)), "qdd_set_batch_lists")
+    return bool(prev.value)
 
 
 class Field:

@@ -167,3 +167,82 @@ def test_tuning_cache_feeds_the_batch(qdd, oracle_mod):
     assert oracle_mod.Op(dims, BC, U, kappa, 1.0).true_residual(eta.cpu().numpy(), phi.cpu().numpy()) <= 1e-10
     assert oracle_mod.Op((4, 4, 4, 8), BC, U2, kappa, 1.0).true_residual(eta2, phi2) <= 1e-10
     assert infos[0][0]["ras_sweeps"] == 2 * infos[0][0]["inner_iters"] * p.n_ras
+
+
+def _solve_batch_counted(qdd, lats, phis, etas, kappas, params, lists):
+    prev = qdd.set_batch_lists(lists)
+    try:
+        torch.cuda.synchronize()
+        n0 = qdd.kernel_launches()
+        infos = qdd.solve_batch(lats, phis, etas, kappas, [1.0] * len(lats), 1e-10, params)
+        torch.cuda.synchronize()
+        return infos, qdd.kernel_launches() - n0
+    finally:
+        qdd.set_batch_lists(prev)
+
+
+def test_batch_work_lists(qdd, oracle_mod):
+    """Work lists (qdd_set_batch_lists): lattices with FP16 inner storage that
+    share NRAS and the domain size run each step of their iteration as one
+    launch over all of them -- every RAS sweep over all (lattice, domain)
+    items, every D over the concatenated site ranges, the update.  Here two
+    groups (256-site and 128-site domains, different shapes, blockings,
+    N_dominv and kappa, so they converge after different iteration counts)
+    and one lattice that keeps its own launches (FP32 storage).  Every
+    system meets the oracle's FP64 residual with the lists on and off; the
+    two give the same solution to about cond * tol, and the lists need
+    fewer launches."""
+    draws = [((8, 8, 8, 8), 0.3, 0.12, dict(block=(4, 4, 4, 4), n_dominv=3)),
+             ((8, 8, 8, 16), 0.25, 0.118, dict(block=(4, 4, 4, 4), n_dominv=4)),
+             ((12, 8, 8, 8), 0.35, 0.124, dict(block=(4, 4, 4, 4), n_dominv=2)),
+             ((4, 4, 4, 12), 0.2, 0.11, dict(block=(4, 4, 4, 4), n_dominv=3)),
+             ((8, 8, 4, 8), 0.3, 0.122, dict(block=(4, 4, 4, 2), n_dominv=3)),
+             ((8, 4, 8, 8), 0.3, 0.12, dict(block=(4, 4, 2, 4), n_dominv=2)),
+             ((8, 8, 8, 8), 0.3, 0.12, dict(block=(4, 4, 4, 4), n_dominv=3, inner_prec="f32"))]
+    lats, etas, ops, params = [], [], [], []
+    for k, (dims, eps, kappa, kw) in enumerate(draws):
+        U = synth.gauge_field(dims, eps, 500 + k)
+        eta = synth.gaussian_source(dims, 600 + k)
+        lat = qdd.create_lattice(dims, BC, stream=torch.cuda.Stream())
+        qdd.load_gauge(lat, torch.from_numpy(U).cuda())
+        lats.append(lat)
+        etas.append(torch.from_numpy(eta).cuda())
+        ops.append((oracle_mod.Op(dims, BC, U, kappa, 1.0), eta))
+        params.append(qdd.default_params(**{"n_ras": 2, "inner_prec": "f16", **kw}))
+    kappas = [d[2] for d in draws]
+    out = {}
+    for lists in (True, False):
+        phis = [torch.zeros_like(e) for e in etas]
+        infos, launches = _solve_batch_counted(qdd, lats, phis, etas, kappas, params, lists)
+        for k, ((op, eta), phi, info) in enumerate(zip(ops, phis, infos)):
+            assert info[0]["status"] == 0, (lists, k)
+            assert op.true_residual(eta, phi.cpu().numpy()) <= 1e-10, (lists, k)
+            assert info[0]["ras_sweeps"] == 2 * info[0]["inner_iters"] * 2
+        out[lists] = ([p.cpu().numpy() for p in phis], launches, [i[0]["inner_iters"] for i in infos])
+    for a, b in zip(out[True][0], out[False][0]):
+        assert rel(a, b) < 1e-8
+    assert len(set(out[True][2])) > 1          # the members stop at different iterations
+    assert out[True][1] < 0.6 * out[False][1], (out[True][1], out[False][1])
+
+
+def test_batch_work_lists_split_at_sixteen(qdd, oracle_mod):
+    """17 compatible lattices: the first 16 share one group's launches (the
+    largest list), the 17th keeps its own; every system meets the oracle's
+    FP64 residual."""
+    dims, n = (8, 8, 8, 8), 17
+    lats, phis, etas, ops = [], [], [], []
+    for k in range(n):
+        U = synth.gauge_field(dims, 0.2 + 0.01 * k, 700 + k)
+        eta = synth.gaussian_source(dims, 800 + k)
+        kappa = 0.11 + 0.0008 * k
+        lat = qdd.create_lattice(dims, BC, stream=torch.cuda.Stream())
+        qdd.load_gauge(lat, torch.from_numpy(U).cuda())
+        lats.append(lat)
+        etas.append(torch.from_numpy(eta).cuda())
+        phis.append(torch.zeros_like(etas[-1]))
+        ops.append((oracle_mod.Op(dims, BC, U, kappa, 1.0), eta, kappa))
+    p = qdd.default_params(block=(4, 4, 4, 4), n_ras=2, n_dominv=3, inner_prec="f16")
+    infos, _ = _solve_batch_counted(qdd, lats, phis, etas, [o[2] for o in ops], [p] * n, True)
+    for (op, eta, _), phi, info in zip(ops, phis, infos):
+        assert info[0]["status"] == 0
+        assert op.true_residual(eta, phi.cpu().numpy()) <= 1e-10
