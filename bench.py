@@ -487,6 +487,21 @@ def run_ours(args, rank, world):
     e2e_s = (time.perf_counter() - t0) / args.steps
     e_ok = all(i["status"] == 0 for i in e_infos)
 
+    # the box's pinned-copy bandwidth, which sets the end-to-end overhead
+    # (it has varied between boxes of this pool): one copy of the links each way
+    dev = torch.empty(hU.shape, dtype=hU.dtype, device="cuda")
+    xfer = {}
+    for name, dst, src in (("h2d_GBps", dev, hU), ("d2h_GBps", hU, dev)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        dst.copy_(src, non_blocking=True)
+        ev1.record()
+        torch.cuda.synchronize()
+        xfer[name] = round(hU.numel() * hU.element_size() / (ev0.elapsed_time(ev1) * 1e-3) / 1e9, 1)
+    del dev
+
     # the oracle's check of the last answer (FP64 true residual with the oracle's D)
     oracle_res = None
     cb = None
@@ -530,7 +545,7 @@ def run_ours(args, rank, world):
             "roofline": roof, "roofline_dslash": roof_dslash, "dslash_alone": dsl,
             "e2e": {"value": round(e2e_s, 5), "unit": "s",
                     "h2d_bytes_per_step": int(U.nbytes + eta.nbytes), "d2h_bytes_per_step": int(eta.nbytes),
-                    "converged": e_ok},
+                    "converged": e_ok, "pinned_copy": xfer},
             "gpu_launches": int(launches),
             "clocks": clocks,
             "cpu_baseline": cb,

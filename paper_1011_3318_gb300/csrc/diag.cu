@@ -35,7 +35,7 @@ void Profiler::release_graph()
         pool.push_back(p.b);
     }
     graph_pairs.clear();
-    graph_replays = 0;
+    graph_replays[0] = graph_replays[1] = 0;
 }
 
 cudaEvent_t Profiler::get()
@@ -57,18 +57,18 @@ void Profiler::drain()
 {
     // each replay of a captured graph re-records its pairs; one replay runs
     // between two reads, so the pairs hold the last replay's times
-    if (graph_replays > 0) {
-        for (auto &p : graph_pairs) {
-            float ms_ = 0.f;
-            if (cudaEventElapsedTime(&ms_, p.a, p.b) == cudaSuccess) {
-                ms[p.cls] += ms_ * graph_replays;
-                n[p.cls] += graph_replays;
-            } else {
-                cudaGetLastError();
-            }
+    for (auto &p : graph_pairs) {
+        const int reps = graph_replays[p.graph];
+        if (reps <= 0) continue;
+        float ms_ = 0.f;
+        if (cudaEventElapsedTime(&ms_, p.a, p.b) == cudaSuccess) {
+            ms[p.cls] += ms_ * reps;
+            n[p.cls] += reps;
+        } else {
+            cudaGetLastError();
         }
-        graph_replays = 0;
     }
+    graph_replays[0] = graph_replays[1] = 0;
     for (auto &p : pending) {
         float ms_ = 0.f;
         if (cudaEventElapsedTime(&ms_, p.a, p.b) == cudaSuccess) {
@@ -102,10 +102,10 @@ ProfScope::~ProfScope()
     }
     cudaEventRecordWithFlags(b, st, prof->capturing ? cudaEventRecordExternal : cudaEventRecordDefault);
     if (prof->capturing) {  // the records are nodes of the graph being captured
-        prof->graph_pairs.push_back(Profiler::Pair{cls, a, b});
+        prof->graph_pairs.push_back(Profiler::Pair{cls, a, b, prof->capture_graph});
         return;
     }
-    prof->pending.push_back(Profiler::Pair{cls, a, b});
+    prof->pending.push_back(Profiler::Pair{cls, a, b, 0});
     // bound the number of outstanding pairs: drain (which waits) when many
     if (prof->pending.size() >= 4096) {
         cudaEventSynchronize(b);

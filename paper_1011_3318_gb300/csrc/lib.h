@@ -22,6 +22,7 @@ struct Profiler {
     struct Pair {
         int cls;
         cudaEvent_t a, b;
+        int graph;  // which captured graph holds the pair (0 or 1)
     };
     bool on = false;
     std::vector<cudaEvent_t> pool;
@@ -29,8 +30,9 @@ struct Profiler {
     // pairs recorded while a CUDA graph is captured: event-record nodes of
     // the graph, read after each replay and kept until the graph is released
     bool capturing = false;
+    int capture_graph = 0;  // the id given to the pairs of the graph being captured
     std::vector<Pair> graph_pairs;
-    int graph_replays = 0;  // replays since the graph pairs were last read
+    int graph_replays[2] = {0, 0};  // replays of each graph since its pairs were last read
     double ms[QDD_NKCLASS] = {};
     long long n[QDD_NKCLASS] = {};
     ~Profiler();

@@ -43,6 +43,7 @@
 #include "lib.h"
 #include "pair.cuh"
 #include "tma.cuh"
+#include "tmem.cuh"
 
 namespace qdd {
 
@@ -422,10 +423,10 @@ __device__ __forceinline__ void ras_mr_domain(const RasArgs &a, const LocSite &s
                                               unsigned char *sA, const LinkView &lU, const CloverView &lA,
                                               float (&wpart)[3][NT / 32]);
 
-template <int NT>
+template <int NT, bool TM = false>
 __device__ __forceinline__ void ras_mr_domain_x2(const RasArgs &a, const LocSite &s, float2 *srho, float2 *sv,
                                                  const unsigned char *sA, const float *sAn, const LinkView &lU,
-                                                 float (&wpart)[3][NT / 32]);
+                                                 float (&wpart)[3][NT / 32], unsigned tv = 0);
 
 template <int P, int NT, bool SC, bool EXP>
 __device__ __forceinline__ void ras_mr_domain(const RasArgs &a, const LocSite &s, float2 *srho, float2 *sv,
@@ -536,11 +537,43 @@ template <int P, bool SC, bool EXP> struct SplitRho {
     static constexpr bool value = P == P16 && SC && !EXP;
 };
 
+// Row 2 of the staged FP16 links, rebuilt once per sweep instead of in
+// every MR iteration: entry k of link mu of site i at r2[(3 mu + k) v + i]
+// (FP32 complex).  Rebuilding it in every hop cost 10% of the sweep.
+__device__ __forceinline__ void stage_row2(const LinkView &u, float2 *r2, unsigned v, unsigned i)
+{
+#pragma unroll
+    for (int mu = 0; mu < 4; mu++) {
+        C<float> U[9];
+        load_link16(u, v, mu, i, U);
+#pragma unroll
+        for (int k = 0; k < 3; k++) r2[(3 * mu + k) * v + i] = make_float2(U[6 + k].r, U[6 + k].i);
+    }
+}
+
+// The staged FP16 link U_mu of site i (rows 0 and 1) with its staged row 2.
+__device__ __forceinline__ void load_link16_r2(const LinkView &u, const float2 *r2, unsigned v, int mu, unsigned i,
+                                               C<float> (&U)[9])
+{
+    const uint2 *p = (const uint2 *)u.d + mu * 3 * v;
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        const uint2 w = p[q * v + i];
+        U[2 * q] = {hre(w.x), him(w.x)};
+        U[2 * q + 1] = {hre(w.y), him(w.y)};
+    }
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const float2 w = r2[(3 * mu + k) * v + i];
+        U[6 + k] = {w.x, w.y};
+    }
+}
+
 // Both hops of direction MU on the split residual in shared memory (float4
-// groups), links from the staged FP16 planes.
-template <int MU>
+// groups), links from the staged FP16 planes (row 2 from r2 when R2).
+template <int MU, bool R2>
 __device__ __forceinline__ void smem_hops_x2(const LocSite &s, int l, const float4 *R4, const LinkView &sU,
-                                             float kappa, int NT, f2 (&AUR)[3], f2 (&AUI)[3],
+                                             const float2 *r2, float kappa, int NT, f2 (&AUR)[3], f2 (&AUI)[3],
                                              f2 (&ADR)[3], f2 (&ADI)[3])
 {
     const int ls = s.ls[MU], e = s.e[MU];
@@ -572,7 +605,8 @@ __device__ __forceinline__ void smem_hops_x2(const LocSite &s, int l, const floa
         f2 UR[3], UI[3], DA[3], DB[3];
         C<float> U[9];
         pairs(nf, UR, UI, DA, DB);
-        load_link16(sU, (unsigned)NT, MU, (unsigned)l, U);
+        if constexpr (R2) load_link16_r2(sU, r2, (unsigned)NT, MU, (unsigned)l, U);
+        else load_link16(sU, (unsigned)NT, MU, (unsigned)l, U);
         const float c = !kf ? 0.f : (s.m & (1u << (8 + MU))) ? kappa : -kappa;
         hop_core<MU, true>(UR, UI, DA, DB, U, c, AUR, AUI, ADR, ADI);
     }
@@ -581,7 +615,8 @@ __device__ __forceinline__ void smem_hops_x2(const LocSite &s, int l, const floa
         f2 UR[3], UI[3], DA[3], DB[3];
         C<float> U[9];
         pairs(nb, UR, UI, DA, DB);
-        load_link16(sU, (unsigned)NT, MU, (unsigned)nb, U);
+        if constexpr (R2) load_link16_r2(sU, r2, (unsigned)NT, MU, (unsigned)nb, U);
+        else load_link16(sU, (unsigned)NT, MU, (unsigned)nb, U);
         const float c = !kb ? 0.f : (s.m & (1u << (12 + MU))) ? kappa : -kappa;
         hop_core<MU, false>(UR, UI, DA, DB, U, c, AUR, AUI, ADR, ADI);
     }
@@ -594,10 +629,14 @@ __device__ __forceinline__ void smem_hops_x2(const LocSite &s, int l, const floa
 // The clover term stays scalar (see below).  Measured at 32^4 against the
 // all-scalar solve: 4x4x4x2 domains, N_dominv 3: 240.5 -> 215.7 us; 4^4
 // domains, N_dominv 4: 328 -> 304 us.
-template <int NT>
+//
+// With TM (the TMA-staged sweep): v lives in tensor memory at this thread's
+// lane (24 columns from tv, the split layout's 6 float4 groups), and sv holds
+// the links' row 2 (stage_row2) instead of v.
+template <int NT, bool TM>
 __device__ __forceinline__ void ras_mr_domain_x2(const RasArgs &a, const LocSite &s, float2 *srho, float2 *sv,
                                                  const unsigned char *sA, const float *sAn, const LinkView &lU,
-                                                 float (&wpart)[3][NT / 32])
+                                                 float (&wpart)[3][NT / 32], unsigned tv)
 {
     const int l = threadIdx.x;
     const bool act = s.m & M_ACT;
@@ -625,10 +664,10 @@ __device__ __forceinline__ void ras_mr_domain_x2(const RasArgs &a, const LocSite
                     ADR[c] = make_float2(na * o[6 + c].r, na * o[9 + c].r); ADI[c] = make_float2(na * o[6 + c].i, na * o[9 + c].i);
                 }
             }
-            smem_hops_x2<0>(s, l, R4, lU, a.kappa, NT, AUR, AUI, ADR, ADI);
-            smem_hops_x2<1>(s, l, R4, lU, a.kappa, NT, AUR, AUI, ADR, ADI);
-            smem_hops_x2<2>(s, l, R4, lU, a.kappa, NT, AUR, AUI, ADR, ADI);
-            smem_hops_x2<3>(s, l, R4, lU, a.kappa, NT, AUR, AUI, ADR, ADI);
+            smem_hops_x2<0, TM>(s, l, R4, lU, sv, a.kappa, NT, AUR, AUI, ADR, ADI);
+            smem_hops_x2<1, TM>(s, l, R4, lU, sv, a.kappa, NT, AUR, AUI, ADR, ADI);
+            smem_hops_x2<2, TM>(s, l, R4, lU, sv, a.kappa, NT, AUR, AUI, ADR, ADI);
+            smem_hops_x2<3, TM>(s, l, R4, lU, sv, a.kappa, NT, AUR, AUI, ADR, ADI);
         }
         // <q, rho> = sum conj(q) rho and |q|^2 on pairs, then over the domain
         // in FP32 (warp sums, per-warp partials read by every thread)
@@ -671,14 +710,25 @@ __device__ __forceinline__ void ras_mr_domain_x2(const RasArgs &a, const LocSite
             }
         }
         // every thread is past the barrier: rho can be updated in place
-        if (red[2] > 0.f) {
+        if (red[2] > 0.f) {  // uniform over the CTA (the warp-wide TMEM accesses need that)
             const float inv = 1.0f / red[2];
             const f2 ar = bc2(red[0] * inv), ai = bc2(red[1] * inv), an = bc2(-red[1] * inv);
+            float vt[TM ? 24 : 1];
+            if constexpr (TM) {
+                tm_ld24(tv, vt);
+            }
 #pragma unroll
             for (int g = 0; g < 6; g++) {
                 const f2 QR = g < 3 ? AUR[g] : ADR[g - 3], QI = g < 3 ? AUI[g] : ADI[g - 3];
-                const float4 vq = V4[g * NT + l];
-                f2 VR = make_float2(vq.x, vq.y), VI = make_float2(vq.z, vq.w);
+                f2 VR, VI;
+                if constexpr (TM) {
+                    VR = make_float2(vt[4 * g], vt[4 * g + 1]);
+                    VI = make_float2(vt[4 * g + 2], vt[4 * g + 3]);
+                } else {
+                    const float4 vq = V4[g * NT + l];
+                    VR = make_float2(vq.x, vq.y);
+                    VI = make_float2(vq.z, vq.w);
+                }
                 // v += alpha rho
                 VR = pfma(ar, RR[g], VR);
                 VR = pfma(an, RI[g], VR);
@@ -689,12 +739,39 @@ __device__ __forceinline__ void ras_mr_domain_x2(const RasArgs &a, const LocSite
                 NR = pfma(ai, QI, NR);
                 f2 NI = pfma(pneg(ar), QI, RI[g]);
                 NI = pfma(an, QR, NI);
-                V4[g * NT + l] = make_float4(VR.x, VR.y, VI.x, VI.y);
+                if constexpr (TM) {
+                    vt[4 * g] = VR.x;
+                    vt[4 * g + 1] = VR.y;
+                    vt[4 * g + 2] = VI.x;
+                    vt[4 * g + 3] = VI.y;
+                } else {
+                    V4[g * NT + l] = make_float4(VR.x, VR.y, VI.x, VI.y);
+                }
                 R4[g * NT + l] = make_float4(NR.x, NR.y, NI.x, NI.y);
+            }
+            if constexpr (TM) {
+                tm_st8(tv, vt);
+                tm_st8(tv + 8, vt + 8);
+                tm_st8(tv + 16, vt + 16);
             }
         }
     }
-    if (a.asum) {  // additive Schwarz: no restriction, overlaps summed
+    if constexpr (TM) {  // (the TMA-staged sweeps never sum overlaps: no asum)
+        float vt[24];
+        tm_ld24(tv, vt);  // by every thread: the warp-wide load precedes the branch
+        if (s.m & M_BULK) {  // restriction R_{Omega}
+            C<float> vv[12];
+#pragma unroll
+            for (int h = 0; h < 2; h++)
+#pragma unroll
+                for (int c = 0; c < 3; c++) {
+                    const int g = 3 * h + c;
+                    vv[6 * h + c] = {vt[4 * g], vt[4 * g + 2]};
+                    vv[6 * h + 3 + c] = {vt[4 * g + 1], vt[4 * g + 3]};
+                }
+            write_outputs<P16>(a, s.x, vv);
+        }
+    } else if (a.asum) {  // additive Schwarz: no restriction, overlaps summed
         if (act) {
             C<float> vv[12];
             ld_split(sv, NT, l, vv);
@@ -839,6 +916,12 @@ __device__ __forceinline__ void ras_tma_body(const RasArgs &a, const RasTma &tm,
     unsigned char *smem = smem_dyn + ((128u - (smem_addr(smem_dyn) & 127u)) & 127u);
     __shared__ float wpart[3][NT / 32];
     __shared__ __align__(8) unsigned long long bar;
+    // FP16 storage: the domain solve keeps v in tensor memory (24 columns per
+    // thread; warps 4-7 of a 256-thread CTA share lanes with warps 0-3 and
+    // take columns 32-55) and the links' row 2 in v's shared-memory area
+    constexpr bool TMV = P == P16;
+    constexpr unsigned TM_COLS = NT <= 128 ? 32u : 64u;
+    __shared__ unsigned tm_base;
     float2 *srho = reinterpret_cast<float2 *>(smem);
     float2 *sv = srho + 12 * NT;
     unsigned char *sU = reinterpret_cast<unsigned char *>(sv + 12 * NT);
@@ -855,6 +938,16 @@ __device__ __forceinline__ void ras_tma_body(const RasArgs &a, const RasTma &tm,
         return;
     }
 
+    // the tensor-memory columns first, so that the allocation overlaps the
+    // copies (allocated after the copies had landed, the 128-site sweep ran
+    // 14% slower); every path below frees them
+    if constexpr (TMV) {
+        if (l < 32) {
+            __syncwarp();  // the allocation is a warp-wide (aligned) instruction
+            tm_alloc(&tm_base, TM_COLS);
+        }
+        tm_fence_before();
+    }
     if (l == 0) mbar_init(&bar, 1);
     __syncthreads();
     if (l == 0) {
@@ -884,6 +977,13 @@ __device__ __forceinline__ void ras_tma_body(const RasArgs &a, const RasTma &tm,
             else if (a.err) atomicOr(a.err, 1u);
         }
         mbar_wait_bounded(&bar, 0, tm.max_polls);  // give the copies in flight a last chance to land
+        if constexpr (TMV) {
+            if (l < 32) {
+                __syncwarp();  // reconverge after the bounded waits
+                tm_fence_after();
+                tm_dealloc(tm_base, TM_COLS);
+            }
+        }
         return;
     }
 
@@ -908,20 +1008,36 @@ __device__ __forceinline__ void ras_tma_body(const RasArgs &a, const RasTma &tm,
         }
     }
     __syncthreads();  // all raw inputs read before rho and v overwrite them
-    {
-        C<float> z[12];
+    if constexpr (TMV) {
+        tm_fence_after();
+        const unsigned tv = tm_lane_addr(tm_base, (unsigned)(l >> 7) * 32u);
+        st_split(srho, NT, l, r);
+        const float z[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        tm_st8(tv, z);
+        tm_st8(tv + 8, z);
+        tm_st8(tv + 16, z);
+        stage_row2(lU, sv, (unsigned)NT, (unsigned)l);
+        if (a.fuse != RAS_FUSE_NONE) store_spinor<P>(a.in, a.g.V, s.x, r);
+        ras_mr_domain_x2<NT, true>(a, s, srho, sv, sA, sAn, lU, wpart, tv);
+        // every warp's tensor-memory accesses are done before the release
+        tm_fence_before();
+        __syncthreads();
+        if (l < 32) {
+            __syncwarp();
+            tm_fence_after();
+            tm_dealloc(tm_base, TM_COLS);
+        }
+    } else {
+        {
+            C<float> z[12];
 #pragma unroll
-        for (int q = 0; q < 12; q++) z[q] = {0.f, 0.f};
-        if constexpr (SplitRho<P, SC, false>::value) {
-            st_split(srho, NT, l, r);
-            st_split(sv, NT, l, z);
-        } else {
+            for (int q = 0; q < 12; q++) z[q] = {0.f, 0.f};
             st_local(srho, NT, l, r);
             st_local(sv, NT, l, z);
+            if (a.fuse != RAS_FUSE_NONE) store_spinor<P>(a.in, a.g.V, s.x, r);
         }
-        if (a.fuse != RAS_FUSE_NONE) store_spinor<P>(a.in, a.g.V, s.x, r);
+        ras_mr_domain<P, NT, SC, false>(a, s, srho, sv, sA, lU, lA, wpart);
     }
-    ras_mr_domain<P, NT, SC, false>(a, s, srho, sv, sA, lU, lA, wpart);
 }
 
 template <int P, int NT>

@@ -331,7 +331,28 @@ struct Member {
     std::vector<double> eta2, rr, best;
     std::vector<int> stalls, restarted, done, result;
     std::vector<int> oit;  // outer BiCGStab iterations (outer_mode 1)
+    // the last |r|^2 and iteration count seen by the host, per right-hand
+    // side, to estimate how many iterations an inner solve still needs
+    std::vector<double> seen_rr;
+    std::vector<int> seen_it;
 };
+
+// Whether one more iteration is likely to end right-hand side r of m: the
+// reduction of |r|^2 per iteration since the host last looked, extrapolated
+// to the tolerance (BiCGStab's residual is not monotonic, so this is only an
+// estimate: a wrong guess costs one more replay, not a wrong result).  Then
+// records what it saw.
+bool one_more_suffices(Member &m, int r, const Scalars &h)
+{
+    bool one = false;
+    if (m.seen_it[r] >= 0 && h.iter > m.seen_it[r] && h.rr > 0.0 && m.seen_rr[r] > h.rr && h.tol2 > 0.0) {
+        const double per = std::log(h.rr / m.seen_rr[r]) / (h.iter - m.seen_it[r]);  // < 0
+        one = std::log(h.tol2 / h.rr) >= per;  // the next iteration reaches tol2
+    }
+    m.seen_rr[r] = h.rr;
+    m.seen_it[r] = h.iter;
+    return one;
+}
 
 // One BiCGStab iteration (van der Vorst) of every right-hand side of a
 // lattice, right-preconditioned by K_RAS when use_ras: D K chi = b,
@@ -562,6 +583,7 @@ bool graph_capable(const std::vector<Member> &ms)
 
 // Enqueues `chunk` iterations of every member, eagerly or as one graph launch.
 struct IterGraph {
+    int id = 0;  // 0: the chunk graph, 1: the one-iteration graph (per-kernel profiling tells them apart)
     cudaGraphExec_t exec = nullptr;
     unsigned long long launches = 0;
     std::vector<cudaEvent_t> events;  // fork/join inside the capture
@@ -597,7 +619,10 @@ qdd_status build_graph(std::vector<Member> &ms, Groups &groups, const std::vecto
     cudaError_t e = cudaStreamBeginCapture(s0, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "graph capture");
     for (Member &m : ms)
-        if (m.lat->prof && m.lat->prof->on) m.lat->prof->capturing = true;
+        if (m.lat->prof && m.lat->prof->on) {
+            m.lat->prof->capturing = true;
+            m.lat->prof->capture_graph = g.id;
+        }
     qdd_status st = QDD_OK;
     cudaEventRecord(g.events[0], s0);
     for (size_t i = 1; i < ms.size(); i++) cudaStreamWaitEvent(ms[i].lat->stream, g.events[0], 0);
@@ -673,6 +698,8 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
         m.done.assign(R, 0);
         m.result.assign(R, QDD_ERR_NOT_CONVERGED);
         m.oit.assign(R, 0);
+        m.seen_rr.assign(R, 0.0);
+        m.seen_it.assign(R, -1);
         if (m.info) memset(m.info, 0, sizeof(qdd_solve_info) * R);
         for (int j = 0; j < i; j++)
             if (L[j] == L[i]) {
@@ -717,8 +744,12 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
     Groups groups;
     std::vector<int> solo;
     if ((st = form_groups(ms, graphs && !plain && g_batch_lists.load() != 0, groups, solo)) != QDD_OK) return st;
-    IterGraph graph;
-    bool have_graph = false;
+    // the graph of `chunk` iterations, and one of a single iteration for the
+    // replay that the residuals say ends the inner solve (a chunk there would
+    // run iterations whose kernels return at once)
+    IterGraph graph, graph1;
+    graph1.id = 1;
+    bool have_graph = false, have_graph1 = false;
     const bool nested_outer = !plain && ps[0]->outer_mode == 1;
 
     // One inner solve of every lattice: right-hand side r of lattice m is
@@ -750,8 +781,10 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
             if ((st = blas(lat, prec, B_INIT, {F(W_B), F(W_R), F(W_RHAT), F(W_X), F(W_P), F(W_V)}, 0, -1.0,
                            active[i])) != QDD_OK)
                 return st;
+            for (int r = 0; r < R; r++) m.seen_it[r] = -1;
         }
         // inner iterations of every lattice until no right-hand side runs
+        bool one = false;  // the next replay runs a single iteration
         for (;;) {
             if (graphs) {
                 if (!have_graph) {
@@ -761,33 +794,40 @@ qdd_status solve_batch_impl(qdd_lattice *const *lats, double *const *phi_dev, co
                     if ((st = build_graph(ms, groups, solo, chunk, graph)) != QDD_OK) return st;
                     have_graph = true;
                 } else {
+                    if (one && !have_graph1) {
+                        if ((st = build_graph(ms, groups, solo, 1, graph1)) != QDD_OK) return st;
+                        have_graph1 = true;
+                    }
+                    IterGraph &g = one ? graph1 : graph;
                     // the graph runs on the first lattice's stream: order it after
                     // the work already queued on the other lattices' streams, and
                     // their next work after it
                     cudaStream_t s0 = ms[0].lat->stream;
                     for (size_t i = 1; i < ms.size(); i++) {
-                        cudaEventRecord(graph.pre[i], ms[i].lat->stream);
-                        cudaStreamWaitEvent(s0, graph.pre[i], 0);
+                        cudaEventRecord(g.pre[i], ms[i].lat->stream);
+                        cudaStreamWaitEvent(s0, g.pre[i], 0);
                     }
-                    cudaError_t e = cudaGraphLaunch(graph.exec, s0);
+                    cudaError_t e = cudaGraphLaunch(g.exec, s0);
                     if (e != cudaSuccess) return cuda_fail(e, "graph launch");
-                    note_launch_adjust((long long)graph.launches);
+                    note_launch_adjust((long long)g.launches);
                     for (Member &m : ms)
-                        if (m.lat->prof && !m.lat->prof->graph_pairs.empty()) m.lat->prof->graph_replays++;
-                    cudaEventRecord(graph.post, s0);
-                    for (size_t i = 1; i < ms.size(); i++) cudaStreamWaitEvent(ms[i].lat->stream, graph.post, 0);
+                        if (m.lat->prof && !m.lat->prof->graph_pairs.empty()) m.lat->prof->graph_replays[g.id]++;
+                    cudaEventRecord(g.post, s0);
+                    for (size_t i = 1; i < ms.size(); i++) cudaStreamWaitEvent(ms[i].lat->stream, g.post, 0);
                 }
             } else {
-                for (int c = 0; c < chunk; c++)
+                for (int c = 0; c < (one ? 1 : chunk); c++)
                     if ((st = enqueue_all(ms, groups, solo)) != QDD_OK) return st;
             }
             if ((st = read_scalars(L)) != QDD_OK) return st;
             bool running = false;
+            one = true;
             for (Member &m : ms) {
                 qdd_lattice *lat = m.lat;
                 bool restart = false;
                 for (int r = 0; r < lat->nrhs; r++) {
                     const Scalars &h = lat->sc_host[r];
+                    if (h.status == S_RUN && !one_more_suffices(m, r, h)) one = false;
                     if (h.status == S_RUN) {
                         if (h.iter >= m.prm.max_inner) {
                             // out of inner iterations: stop this right-hand side
