@@ -111,8 +111,8 @@ class ClockSampler:
 # ------------------------------------------------------------------ helpers
 # the files that define device code: a change to any of them invalidates the
 # committed ncu traffic figures
-KERNEL_SOURCES = ("device.cuh", "pair.cuh", "df64.cuh", "qdd_internal.h", "lib.h", "dslash.cu", "ras.cu", "blas.cu",
-                  "lattice.cu")
+KERNEL_SOURCES = ("device.cuh", "pair.cuh", "df64.cuh", "tma.cuh", "tmem.cuh", "qdd_internal.h", "lib.h", "dslash.cu",
+                  "ras.cu", "blas.cu", "lattice.cu")
 
 
 def kernel_source_hash():
