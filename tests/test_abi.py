@@ -90,6 +90,17 @@ def test_host_side_calls_without_gpu(libpath):
     assert lib.qdd_create_lattice(ctypes.byref(h), big, bc, 1, None) == qdd.QDD_ERR_ARG
     assert "119304647" in qdd.last_error()
     assert lib.qdd_destroy_lattice(None) == qdd.QDD_OK
+    # the batch work-list switch is process-wide host state: on by default,
+    # and each call reports the setting it replaces
+    prev = qdd.set_batch_lists(False)
+    try:
+        assert prev is True
+        assert qdd.set_batch_lists(False) is False
+        assert qdd.set_batch_lists(True) is False
+        assert qdd.set_batch_lists(True) is True
+    finally:
+        qdd.set_batch_lists(prev)
+    assert lib.qdd_set_batch_lists(1, None) == qdd.QDD_OK
 
 
 def test_oracle_and_library_share_no_code():
