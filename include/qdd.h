@@ -261,7 +261,8 @@ qdd_status qdd_solve_batch_each(qdd_lattice *const *lats, double *const *phi, co
                                 const qdd_solver_params *const *params, qdd_solve_info *info);
 
 /* Work lists for batches (qdd_solve_batch, qdd_solve_batch_each), on (1) by
- * default.  While on, the lattices of a batch with FP16 inner storage
+ * default.  The paper has no counterpart (it solves one system at a time);
+ * this is an execution choice.  While on, the lattices of a batch with FP16 inner storage
  * (inner_prec QDD_F16) that share n_ras and the number of sites per RAS
  * domain (128 or 256, overlap 0, x extents divisible by 4), with one
  * right-hand side each and the RAS Schwarz variant, run each step of their
